@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the rank-k Cholesky up/downdate on GB300.
+
+Workload (the paper's headline shape, Sec. 5): n = 5000, k = 16, float64,
+L = upper Cholesky factor of B^T B / n + I (B ~ N(0, 1)), V ~ N(0, 1/n); one
+step is a rank-16 update followed by the rank-16 downdate with the same V,
+which returns L to its starting value up to rounding.
+
+Metric: effective HBM GB/s = algorithmic bytes / time, where the algorithmic
+bytes of one modification are elt*n*(n+1) (read and write of the upper
+triangle) + elt*n*k (one read of V).  The L factor (100 MB upper triangle)
+fits in the 126 MB L2, so L2 is flushed (a 512 MB write) between timed steps,
+outside the timed events.
+
+Arms:
+  default          the CUDA library through its C ABI (this repository)
+  --impl reference the serial CPU oracle on the host cores, same workload and metric
+Multi-GPU (torchrun): the factor does not shard, so every rank runs an
+independent replica (weak scaling) and ``value`` sums the ranks' bytes over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N, K, DTYPE = 5000, 16, "f64"
+METRIC = "rank-k up/downdate effective HBM GB/s"
+UNIT = "GB/s"
+# Nominal FP64 rate of the part: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# dram read+write bytes per launch of the dominant kernel from the last ncu
+# capture of the current kernel version (None until one is taken).
+NCU_TRAFFIC = {}
+
+
+def alg_bytes(n, k, elt=8):
+    return elt * n * (n + 1) + elt * n * k
+
+
+def alg_flops(n, k):
+    # Apply: 4 flops (2 multiplies, 2 adds) per element per vector; Compute: ~6 per row and vector.
+    return k * (2 * n * (n - 1) + 6 * n)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chm", choices=["chm", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n, k, budget_s=12.0, max_steps=None):
+    """Time the oracle (serial C, one core) on whole steps of the workload."""
+    import numpy as np
+
+    import oracle
+    from paper_1011_1173_gb300 import inputs
+
+    L0 = inputs.spd_factor(n, inputs.config_seed(1)).numpy()
+    V = inputs.update_block(n, k, inputs.config_seed(1)).numpy()
+    L = L0.copy()
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        st1, _ = oracle.modify_b(L, V, 1)
+        st2, _ = oracle.modify_b(L, V, -1)
+        times.append(time.perf_counter() - t0)
+        assert st1 == 0 and st2 == 0
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if max_steps is None and time.perf_counter() - t_start >= budget_s:
+            break
+    per_step = sum(times) / len(times)
+    value = 2 * alg_bytes(n, k) / per_step / 1e9
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d whole step(s) (rank-%d update + downdate, n=%d, float64), serial C "
+                      "oracle CholeskyModifyB, %.2f s/step" % (len(times), k, n, per_step)}, per_step
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    # warm-up steps, then timed steps of the oracle
+    cb, _ = cpu_baseline(N, K, max_steps=args.warmup)
+    cb, per_step = cpu_baseline(N, K, max_steps=args.steps)
+    value = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
+            "data": "synthetic",
+            "config": {"workload": "rank-%d update+downdate n=%d float64" % (K, N), "n": N, "k": K,
+                       "l2": "n/a (host)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1011_1173_gb300 import chm, inputs
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    chm.load(build_if_missing=True)
+
+    n, k = N, K
+    seed = inputs.config_seed(1)
+    L0 = inputs.spd_factor(n, seed, device=dev)
+    V = inputs.update_block(n, k, seed, device=dev)
+    L = L0.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    launch_ev = []
+
+    def step(record=False):
+        for sg in (1, -1):
+            if record:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            rc = chm.modify(L, V, sg, stream=stream)
+            if rc != chm.CHM_OK:
+                raise chm.ChmError(rc, "launch")
+            if record:
+                b.record(stream)
+                launch_ev.append((a, b))
+
+    for _ in range(args.warmup):
+        step()
+    st, info = chm.status_sync(stream)
+    chm.check(st, "warm-up status (info %d)" % info)
+
+    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    sampler = ClockSampler(smi_index if smi_index.strip().isdigit() else local)
+    step_ev = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for s in range(args.steps):
+        if s % 10 == 0:
+            L.copy_(L0)  # bound drift; outside the timed events
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(record=True)
+        b.record(stream)
+        step_ev.append((a, b))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    st, info = chm.status_sync(stream)
+    chm.check(st, "timed status (info %d)" % info)
+
+    ms = sum(a.elapsed_time(b) for a, b in step_ev) / len(step_ev)
+    launch_ms = sum(a.elapsed_time(b) for a, b in launch_ev) / len(launch_ev)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    bytes_step = 2 * alg_bytes(n, k)
+    value = world * bytes_step / (ms_max / 1e3) / 1e9
+
+    # End to end through the public API with host buffers: pinned host L and
+    # V copied in, update + downdate, the modified factor copied back.
+    e2e = None
+    if not args.no_e2e:
+        Lh0 = L0.cpu().pin_memory()
+        Vh = V.cpu().pin_memory()
+        Lh_out = torch.empty_like(Lh0).pin_memory()
+        Ld = torch.empty_like(L0)
+        Vd = torch.empty_like(V)
+
+        def e2e_step():
+            Ld.copy_(Lh0, non_blocking=True)
+            Vd.copy_(Vh, non_blocking=True)
+            for sg in (1, -1):
+                chm.check(chm.modify(Ld, Vd, sg, stream=stream), "e2e launch")
+            Lh_out.copy_(Ld, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        chm.check(chm.status_sync(stream)[0], "e2e status")
+        e2e_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = Lh0.numel() * Lh0.element_size() + Vh.numel() * Vh.element_size()
+        e2e = {"value": world * bytes_step / (float(te.item()) / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Lh_out.numel() * Lh_out.element_size(),
+               "ms_per_step": float(te.item())}
+
+    kernel = "modify_wavefront_kernel<double>"
+    achieved = alg_flops(n, k) / (launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64)",
+                "launch_ms": launch_ms,
+                "hbm_gbs": alg_bytes(n, k) / (launch_ms / 1e3) / 1e9,
+                "traffic": NCU_TRAFFIC.get(kernel)}
+
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(n, k)
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
+                "config": {"workload": "rank-%d update+downdate n=%d float64 (paper headline shape)"
+                                       % (k, n), "n": n, "k": k, "ld": n,
+                           "l2": "flushed between timed steps (512 MB write outside the events)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": 2 * args.steps * ((k + 15) // 16),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

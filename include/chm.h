@@ -1,0 +1,137 @@
+/*
+ * chm.h - C ABI of the GB300 rank-k Cholesky up/downdate library.
+ *
+ * Operation (Walder 2010, Sec. 1): given an upper-triangular factor L of
+ * order n with positive diagonal, A = L^T L, and V in R^{n x k}, overwrite L
+ * with the factor Lt such that
+ *
+ *     Lt^T Lt = A + V diag(sigma) V^T,      sigma_p in {+1 (update), -1 (downdate)}
+ *
+ * by the hyperbolic rotations of Algorithm 1 (Compute / Apply), in O(k n^2)
+ * work.  The k columns of V are processed in ascending order, which yields
+ * the same factor as k successive rank-1 modifications.
+ *
+ * Conventions shared by every entry point:
+ *   - Layout.  L is column-major upper triangular with leading dimension ld
+ *     (LAPACK uplo = 'U', Matlab's chol convention): element (i, j), i <= j,
+ *     is at L[i + j*ld].  Only the upper triangle including the diagonal is
+ *     read or written; the strictly lower part and the rows n..ld-1 of each
+ *     column are left bit-for-bit unchanged.  V is column-major n x k with
+ *     leading dimension ldv (ldv = n in the short forms); column p is the
+ *     p-th update vector.  V is read only.
+ *   - Pointers.  L, V and d_info are DEVICE pointers owned by the caller
+ *     (the library never frees them).  L and V must be aligned to their
+ *     element size.  sigma arrays are HOST pointers.
+ *   - Precision.  CHM_F64: L and V are double; all arithmetic in double.
+ *     CHM_F32_MIXED: L and V are float; the Apply sweep runs in float while
+ *     every Compute step (the square root and the c, s ratios) runs in
+ *     double on the promoted float values, the new diagonal being rounded to
+ *     float after each vector.
+ *   - Streams.  Work is enqueued on `stream` (a cudaStream_t; NULL means the
+ *     legacy default stream of the current device) and the call returns
+ *     without synchronising.  L is modified in place in stream order.
+ *   - Errors.  A call returns synchronously only argument errors
+ *     (CHM_ERR_ARG), allocation failures (CHM_ERR_NOMEM) and launch errors
+ *     (CHM_ERR_CUDA).  Conditions found on the device are recorded in a
+ *     per-(device, stream) status word that stays set until read by
+ *     chm_status_sync: CHM_ERR_NOT_PD (a Compute step found L_ii <= 0 or
+ *     L_ii^2 + sigma V_i^2 <= 0 or a non-finite value; info = the 0-based
+ *     row) and CHM_ERR_TIMEOUT (a wait between thread blocks exceeded its
+ *     bound; info = the column block).  After either, L is unspecified.
+ *   - Memory.  The library keeps a small workspace per (device, stream):
+ *     rotation panels (n * 512 bytes), flags and the status word.  It is
+ *     allocated on the first call that needs a larger one; later calls of
+ *     the same or smaller size allocate nothing.
+ *
+ * Thread safety: entry points may be called from several host threads; calls
+ * on the same stream from different threads must be ordered by the caller.
+ */
+#ifndef CHM_H
+#define CHM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so that this header needs no CUDA header. */
+typedef struct CUstream_st *chm_stream_t;
+
+typedef enum {
+    CHM_F64 = 0,       /* double storage, double arithmetic */
+    CHM_F32_MIXED = 1  /* float storage and Apply, double Compute */
+} chm_dtype;
+
+typedef enum {
+    CHM_OK = 0,
+    CHM_ERR_ARG = -1,
+    CHM_ERR_NOT_PD = -2,
+    CHM_ERR_TIMEOUT = -3,
+    CHM_ERR_CUDA = -4,
+    CHM_ERR_NOMEM = -5,
+    CHM_ERR_BUDGET = -6,
+    CHM_ERR_STATE = -7
+} chm_status;
+
+/*
+ * Rank-k update (sigma = +1 for every column): L <- Lt with
+ * Lt^T Lt = L^T L + V V^T.  Algorithm 1 with sigma = +1 (Sec. 2); the
+ * k-column blocking follows Sec. 4.1.
+ *   L      device, n x n upper factor, leading dimension ld (in/out)
+ *   n      order, n >= 0 (n == 0 is a no-op)
+ *   ld     leading dimension of L, ld >= max(1, n)
+ *   V      device, n x k, leading dimension n (read only)
+ *   k      number of update vectors, k >= 0 (k == 0 is a no-op)
+ *   dtype  CHM_F64 or CHM_F32_MIXED (element type of L and V)
+ *   stream CUDA stream
+ * Returns CHM_OK or CHM_ERR_ARG / CHM_ERR_NOMEM / CHM_ERR_CUDA.
+ */
+int chm_update(void *L, int64_t n, int64_t ld, const void *V, int64_t k, int dtype,
+               chm_stream_t stream);
+
+/*
+ * Rank-k downdate (sigma = -1 for every column): Lt^T Lt = L^T L - V V^T.
+ * Same arguments and errors as chm_update.  If L^T L - V V^T is not
+ * positive definite, the stream's status word records CHM_ERR_NOT_PD.
+ */
+int chm_downdate(void *L, int64_t n, int64_t ld, const void *V, int64_t k, int dtype,
+                 chm_stream_t stream);
+
+/*
+ * General form: per-column signs and an explicit leading dimension for V.
+ *   ldv    leading dimension of V, ldv >= max(1, n)
+ *   sigma  HOST array of k entries, each +1 or -1; if NULL every column uses `sign`
+ *   sign   +1 or -1, used when sigma == NULL
+ *   d_info optional DEVICE int64[2]; if non-NULL the library sets it to
+ *          {CHM_OK, -1} on the stream before the work and the device writes
+ *          {status, info} there if this call hits CHM_ERR_NOT_PD or
+ *          CHM_ERR_TIMEOUT (the per-stream status word is written as well)
+ * Each column uses its own sign in both Compute and Apply (a generalisation
+ * of Algorithm 1, where sigma is one scalar).
+ */
+int chm_modify_ex(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k,
+                  const int8_t *sigma, int sign, int dtype, chm_stream_t stream,
+                  int64_t *d_info);
+
+/*
+ * Synchronises `stream`, then reads and clears the status word of the
+ * current device and that stream.
+ *   info   optional HOST int64[2] receiving {status, info}
+ * Returns the recorded status (CHM_OK if no call since the last read hit a
+ * device-side error), or CHM_ERR_CUDA if the synchronisation failed.
+ */
+int chm_status_sync(chm_stream_t stream, int64_t *info);
+
+/* Human-readable name of a status code (static string). */
+const char *chm_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int chm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHM_H */

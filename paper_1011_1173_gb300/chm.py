@@ -1,0 +1,171 @@
+"""Python binding of the C ABI in ``include/chm.h`` (argument marshalling only).
+
+Every function here forwards to the CUDA library ``libchm.so``; none of them
+computes anything.  The library is loaded on first use and there is no
+fallback: if it has not been built, or cannot be loaded, the call raises.
+
+Tensor helpers take torch tensors in the storage convention of the C ABI:
+an order-n upper factor is a C-contiguous (n, ld) tensor whose row j is
+column j of L, and V is a C-contiguous (k, ldv) tensor whose row p is column
+p of V (see ``inputs.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+CHM_F64 = 0
+CHM_F32_MIXED = 1
+
+CHM_OK = 0
+CHM_ERR_ARG = -1
+CHM_ERR_NOT_PD = -2
+CHM_ERR_TIMEOUT = -3
+CHM_ERR_CUDA = -4
+CHM_ERR_NOMEM = -5
+CHM_ERR_BUDGET = -6
+CHM_ERR_STATE = -7
+
+_lib = None
+
+
+class ChmError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s%s" % (what + ": " if what else "", chm_status_string(status)))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libchm.so (optionally building it first).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libchm.so is not built (run paper_1011_1173_gb300.build.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    i64, vp, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    sig = {
+        "chm_update": ([vp, i64, i64, vp, i64, i32, vp], i32),
+        "chm_downdate": ([vp, i64, i64, vp, i64, i32, vp], i32),
+        "chm_modify_ex": ([vp, i64, i64, vp, i64, i64, vp, i32, i32, vp, vp], i32),
+        "chm_status_sync": ([vp, vp], i32),
+        "chm_status_string": ([i32], ctypes.c_char_p),
+        "chm_version": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- raw C ABI
+
+def chm_update(L, n, ld, V, k, dtype, stream):
+    return load().chm_update(L, n, ld, V, k, dtype, stream)
+
+
+def chm_downdate(L, n, ld, V, k, dtype, stream):
+    return load().chm_downdate(L, n, ld, V, k, dtype, stream)
+
+
+def chm_modify_ex(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info):
+    return load().chm_modify_ex(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info)
+
+
+def chm_status_sync(stream, info):
+    return load().chm_status_sync(stream, info)
+
+
+def chm_status_string(status) -> str:
+    return load().chm_status_string(int(status)).decode()
+
+
+def chm_version() -> int:
+    return load().chm_version()
+
+
+# ---------------------------------------------------------------- tensor helpers
+
+def dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return CHM_F64
+    if t.dtype == torch.float32:
+        return CHM_F32_MIXED
+    raise TypeError("L and V must be float64 or float32")
+
+
+def _check_layout(L: torch.Tensor, V: torch.Tensor, n):
+    if not (L.is_cuda and V.is_cuda):
+        raise ValueError("L and V must be CUDA tensors")
+    if L.dtype != V.dtype:
+        raise TypeError("L and V must have the same dtype")
+    if L.dim() != 2 or V.dim() != 2 or not L.is_contiguous() or not V.is_contiguous():
+        raise ValueError("L must be a contiguous (n, ld) tensor and V a contiguous (k, ldv) tensor")
+    n = L.shape[0] if n is None else int(n)
+    return n
+
+
+def modify(L: torch.Tensor, V: torch.Tensor, sigma=1, n=None, stream=None, d_info=None) -> int:
+    """Enqueue L <- modified factor (chm_modify_ex); returns the call's status.
+
+    ``sigma`` is +1, -1, or a sequence of k signs."""
+    n = _check_layout(L, V, n)
+    k = V.shape[0]
+    if isinstance(sigma, int):
+        sig_ptr, sign = None, int(sigma)
+        keep = None
+    else:
+        keep = (ctypes.c_int8 * k)(*[int(s) for s in sigma])
+        sig_ptr, sign = ctypes.cast(keep, ctypes.c_void_p), 1
+    info_ptr = None if d_info is None else d_info.data_ptr()
+    return chm_modify_ex(L.data_ptr(), n, L.shape[1], V.data_ptr(), V.shape[1], k, sig_ptr, sign,
+                         dtype_code(L), _stream_handle(stream), info_ptr)
+
+
+def update(L, V, n=None, stream=None) -> int:
+    n = _check_layout(L, V, n)
+    if V.shape[1] != n:
+        return modify(L, V, 1, n=n, stream=stream)
+    return chm_update(L.data_ptr(), n, L.shape[1], V.data_ptr(), V.shape[0], dtype_code(L),
+                      _stream_handle(stream))
+
+
+def downdate(L, V, n=None, stream=None) -> int:
+    n = _check_layout(L, V, n)
+    if V.shape[1] != n:
+        return modify(L, V, -1, n=n, stream=stream)
+    return chm_downdate(L.data_ptr(), n, L.shape[1], V.data_ptr(), V.shape[0], dtype_code(L),
+                        _stream_handle(stream))
+
+
+def status_sync(stream=None):
+    """Synchronise the stream and return (status, info) of its status word."""
+    info = (ctypes.c_int64 * 2)()
+    st = chm_status_sync(_stream_handle(stream), ctypes.cast(info, ctypes.c_void_p))
+    return st, int(info[1])
+
+
+def check(status, what=""):
+    if status != CHM_OK:
+        raise ChmError(status, what)

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1011_1173_gb300 import build as chm_build
+from paper_1011_1173_gb300 import chm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_ \*]*?)\b(chm_[A-Za-z0-9_]+)\s*\(", text):
+            names.append(m.group(2))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    chm_build.build()
+    return ctypes.CDLL(chm_build.LIB)
+
+
+def test_header_declares_core_calls():
+    names = declared_functions()
+    for required in ("chm_update", "chm_downdate", "chm_modify_ex", "chm_status_sync"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    for n in declared_functions():
+        assert hasattr(chm, n), "binding lacks %s" % n
+
+
+def test_host_only_calls_without_gpu():
+    assert chm.chm_version() >= 100
+    assert "NOT_PD" in chm.chm_status_string(chm.CHM_ERR_NOT_PD)
+
+
+def test_argument_errors_return_synchronously_without_gpu():
+    E = chm.CHM_ERR_ARG
+    assert chm.chm_update(None, -1, 1, None, 1, chm.CHM_F64, None) == E
+    assert chm.chm_update(None, 4, 3, None, 1, chm.CHM_F64, None) == E       # ld < n
+    assert chm.chm_update(None, 4, 4, None, 1, 7, None) == E                 # bad dtype
+    assert chm.chm_update(None, 4, 4, None, 1, chm.CHM_F64, None) == E       # NULL L
+    assert chm.chm_modify_ex(8, 4, 4, 8, 4, 1, None, 0, chm.CHM_F64, None, None) == E  # sign 0
+    assert chm.chm_update(12, 4, 4, 16, 1, chm.CHM_F64, None) == E           # misaligned L
+    # n == 0 or k == 0 with no per-call info word: nothing to do, no CUDA call
+    assert chm.chm_update(None, 0, 1, None, 3, chm.CHM_F64, None) == chm.CHM_OK
+    assert chm.chm_update(8, 5, 5, None, 0, chm.CHM_F64, None) == chm.CHM_OK
