@@ -25,146 +25,260 @@
 
 namespace chm {
 
+// Sweep coefficients of one row for one wave, in the Apply type T:
+//   S' = S + a*u,  u' = u - b*S'  (scaled mixed rotation), e1 = new row scale.
 template <typename T>
-struct ModifyParams {
+struct CoefRow {
+    T a, b, e1, pad;
+};
+
+// Chain data of one row for one wave (always double): ep = e*p (old row
+// scale times the forward-substitution value), e1 = new row scale, d1 = new
+// diagonal, tn = T after this row.
+struct ChainRow {
+    double ep, e1, d1, tn;
+};
+
+template <typename T>
+struct WaveParams {
     T *L;
     long long n, ld;
     const T *V;
     long long ldv;
-    int kb;              // vectors in this launch (<= kKB)
-    unsigned sign_mask;  // bit q set: vector q is a downdate
-    int nblocks;         // column blocks
-    T *coef;             // [nblocks][kW][kKB] Coef<T> (row-major)
+    int nwaves;                   // update vectors in this launch (<= kMaxWaves)
+    int nblocks;                  // column blocks of kW columns
+    unsigned long long down_mask; // bit q set: wave q is a downdate
+    CoefRow<T> *coef;             // [nwaves][nblocks][kW]
+    ChainRow *chain;              // [nwaves][nblocks][kW]
+    int *pflag;                   // [nwaves][nblocks]: panel published when == epoch
+    long long *progress;          // [nwaves][nblocks]: (epoch << 32) + tiles done
     SyncArgs sync;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kW) modify_wavefront_kernel(ModifyParams<T> prm)
+__device__ __forceinline__ CoefRow<double> ld_coef(const CoefRow<double> *p)
 {
-    __shared__ __align__(16) Coef<T> pan[kW][kKB];
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 x = __ldcg(q), y = __ldcg(q + 1);
+    return CoefRow<double>{x.x, x.y, y.x, y.y};
+}
+__device__ __forceinline__ CoefRow<float> ld_coef(const CoefRow<float> *p)
+{
+    const float4 x = __ldcg(reinterpret_cast<const float4 *>(p));
+    return CoefRow<float>{x.x, x.y, x.z, x.w};
+}
+__device__ __forceinline__ void st_coef(CoefRow<double> *p, const CoefRow<double> &c)
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+    __stcg(q, make_double2(c.a, c.b));
+    __stcg(q + 1, make_double2(c.e1, c.pad));
+}
+__device__ __forceinline__ void st_coef(CoefRow<float> *p, const CoefRow<float> &c)
+{
+    __stcg(reinterpret_cast<float4 *>(p), make_float4(c.a, c.b, c.e1, c.pad));
+}
+
+// One task = (wave q, column block b), one warp, lane = column.  Tasks are
+// taken in ticket order t = b * nwaves + q, so a task only waits on tasks
+// with smaller tickets: (q, p < b) for rotation panels and (q - 1, b) for
+// the factor as the previous wave left it.
+//
+// Storage between waves: the diagonal holds the true L_ii; an off-diagonal
+// L_ij (i < j) is stored as S_ij = L_ij / e_i, with e_i the row scale that the
+// last wave's panel published (1 at the start).  The last wave of the
+// launch stores true values again.
+//
+// Per wave (rank-1 modification of the current factor F by v, sign sigma):
+//   chain:  p = F^{-T} v by forward substitution, T_0 = 1,
+//           T_{i+1} = T_i + sigma p_i^2;
+//   these give Algorithm 1's c_i = sqrt(T_{i+1}/T_i) and s_i = p_i/sqrt(T_i);
+//   sweep:  with u = sqrt(T_i) u_hat, the mixed Apply L' = (L + sigma s u)/c,
+//           u' = c u - s L' becomes S' = S + a_i u_hat, u_hat' = u_hat - b_i S'
+//           with a_i = sigma p_i / e_i and b_i = p_i e_i / T_{i+1}.
+template <typename T>
+__global__ void __launch_bounds__(kW) wave_kernel(WaveParams<T> P)
+{
+    __shared__ T tile[kW][kW + 1];  // [column][row]
+    __shared__ CoefRow<T> cf[kW];
+    __shared__ double sep[kW];
     const int lane = threadIdx.x;
     const unsigned FULL = 0xffffffffu;
-    const SyncArgs &sy = prm.sync;
-    const long long n = prm.n, ld = prm.ld;
-    const int kb = prm.kb;
+    const SyncArgs &sy = P.sync;
+    const long long n = P.n, ld = P.ld;
+    const int nw = P.nwaves, nb = P.nblocks;
+    const long long ep64 = (long long)sy.epoch << 32;
 
     for (;;) {
-        int b = 0;
-        if (lane == 0) b = atomicAdd(sy.ticket, 1);
-        b = __shfl_sync(FULL, b, 0);
-        if (b >= prm.nblocks) return;
+        int t = 0;
+        if (lane == 0) t = atomicAdd(sy.ticket, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= nw * nb) return;
         if (aborted(sy)) return;
+        const int b = t / nw, q = t % nw;
+        const int sg = ((P.down_mask >> q) & 1ull) ? -1 : 1;
+        const bool last = (q == nw - 1);
+        const long long c0 = (long long)b * kW;
+        const int ncols = (int)min((long long)kW, n - c0);
+        const bool active = lane < ncols;
+        const long long j = c0 + lane;
+        T uh = active ? P.V[j + (long long)q * P.ldv] : T(0);
+        double z = (double)uh;
+        const long long *prog_prev = q > 0 ? P.progress + (size_t)(q - 1) * nb + b : nullptr;
+        long long *prog_me = P.progress + (size_t)q * nb + b;
 
-        const long long j = (long long)b * kW + lane;
-        const bool active = j < n;
-        T u[kKB];
-#pragma unroll
-        for (int q = 0; q < kKB; ++q)
-            u[q] = (active && q < kb) ? prm.V[j + (long long)q * prm.ldv] : T(0);
-
-        // Trailing sweep: rotations of every earlier row panel.
+        // ---- off-diagonal tiles (p, b), p < b
         for (int p = 0; p < b; ++p) {
             int ok = 1;
-            if (lane == 0) ok = wait_panel(sy, p, b) ? 1 : 0;
+            if (lane == 0) {
+                const int *pf = P.pflag + (size_t)q * nb + p;
+                const int epoch = sy.epoch;
+                ok = bounded_wait(sy, [&] { return ld_acquire_gpu(pf) == epoch; }, t);
+                if (ok && prog_prev) {
+                    const long long want = ep64 + p + 1;
+                    ok = bounded_wait(sy, [&] { return ld_acquire_gpu(prog_prev) >= want; }, t);
+                }
+            }
             ok = __shfl_sync(FULL, ok, 0);
             if (!ok) return;
             __syncwarp();
+            const bool lastTile = (p == b - 1);
+            const size_t prow = ((size_t)q * nb + p) * kW;
+            cf[lane] = ld_coef(P.coef + prow + lane);
+            double tstart = 1.0;
+            if (lastTile) {
+                sep[lane] = __ldcg(&P.chain[prow + lane].ep);
+                if (p > 0) tstart = __ldcg(&P.chain[prow - 1].tn);
+            }
             {
-                constexpr int kWords = (int)(sizeof(Coef<T>) * kW * kKB / 16);
-                const int4 *src = reinterpret_cast<const int4 *>(prm.coef + (size_t)p * kW * kKB * 4);
-                int4 *dst = reinterpret_cast<int4 *>(&pan[0][0]);
-                for (int e = lane; e < kWords; e += 32) dst[e] = __ldcg(src + e);
+                const T *src = P.L + (long long)p * kW + lane;
+                for (int c = 0; c < ncols; ++c) tile[c][lane] = __ldcg(src + (c0 + c) * ld);
             }
             __syncwarp();
             if (active) {
-                T *col = prm.L + j * ld + (long long)p * kW;
+                if (lastTile) {
+                    // z = T u (the forward-substitution carry) after the rows
+                    // above this tile, then the rows of this tile.
+                    double z0 = tstart * (double)uh, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+#pragma unroll
+                    for (int r = 0; r < kW; r += 4) {
+                        z0 = fma(-sep[r], (double)tile[lane][r], z0);
+                        z1 = fma(-sep[r + 1], (double)tile[lane][r + 1], z1);
+                        z2 = fma(-sep[r + 2], (double)tile[lane][r + 2], z2);
+                        z3 = fma(-sep[r + 3], (double)tile[lane][r + 3], z3);
+                    }
+                    z = (z0 + z1) + (z2 + z3);
+                }
+#pragma unroll 8
                 for (int r = 0; r < kW; ++r) {
-                    T x = col[r];
-#pragma unroll
-                    for (int q = 0; q < kKB; ++q) {
-                        if (q < kb) {
-                            const Coef<T> cf = pan[r][q];
-                            apply_rotation(x, u[q], cf.c, cf.s, cf.a, cf.b);
-                        }
-                    }
-                    col[r] = x;
+                    const CoefRow<T> c = cf[r];
+                    const T s = fma(c.a, uh, tile[lane][r]);
+                    uh = fma(-c.b, s, uh);
+                    tile[lane][r] = last ? s * c.e1 : s;
                 }
             }
             __syncwarp();
-        }
-
-        // Diagonal triangle of block b.
-        const int rows = (int)min((long long)kW, n - (long long)b * kW);
-        for (int r = 0; r < rows; ++r) {
-            const long long i = (long long)b * kW + r;
-            if (lane == r) {
-                T *dg = prm.L + i + i * ld;
-                double l = (double)*dg;
-                bool okc = true;
-#pragma unroll
-                for (int q = 0; q < kKB; ++q) {
-                    if (q < kb && okc) {
-                        const int sg = ((prm.sign_mask >> q) & 1u) ? -1 : 1;
-                        double c, s, a, bb;
-                        if (compute_rotation(l, (double)u[q], sg, c, s, a, bb)) {
-                            l = (double)(T)l;  // the stored precision of the new diagonal
-                            pan[r][q] = Coef<T>{(T)c, (T)s, (T)a, (T)bb};
-                        } else {
-                            okc = false;
-                            record_error(sy, kStatusNotPD, i);
-                        }
-                    }
-                }
-                if (okc) *dg = (T)l;
+            {
+                T *dst = P.L + (long long)p * kW + lane;
+                for (int c = 0; c < ncols; ++c) __stcg(dst + (c0 + c) * ld, tile[c][lane]);
             }
-            __syncwarp();
-            if (aborted(sy)) return;
-            if (active && lane > r) {
-                T *e = prm.L + i + j * ld;
-                T x = *e;
-#pragma unroll
-                for (int q = 0; q < kKB; ++q) {
-                    if (q < kb) {
-                        const Coef<T> cf = pan[r][q];
-                        apply_rotation(x, u[q], cf.c, cf.s, cf.a, cf.b);
-                    }
-                }
-                *e = x;
-            }
-            __syncwarp();
-        }
-
-        // Publish this block's panel for the blocks to its right.
-        if (b + 1 < prm.nblocks) {
-            constexpr int kWords = (int)(sizeof(Coef<T>) * kW * kKB / 16);
-            int4 *dst = reinterpret_cast<int4 *>(prm.coef + (size_t)b * kW * kKB * 4);
-            const int4 *src = reinterpret_cast<const int4 *>(&pan[0][0]);
-            for (int e = lane; e < kWords; e += 32) __stcg(dst + e, src[e]);
             __threadfence();
             __syncwarp();
-            if (lane == 0) st_release_gpu(sy.flags + b, sy.epoch);
+            if (lane == 0) st_release_gpu(prog_me, ep64 + p + 1);
         }
+
+        // ---- diagonal block b
+        {
+            int ok = 1;
+            if (lane == 0 && prog_prev) {
+                const long long want = ep64 + b + 1;
+                ok = bounded_wait(sy, [&] { return ld_acquire_gpu(prog_prev) >= want; }, t);
+            }
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) return;
+            __syncwarp();
+        }
+        const int rows = ncols;
+        if (lane < rows) {
+            const T *src = P.L + c0 + lane;
+            for (int c = lane; c < ncols; ++c) tile[c][lane] = __ldcg(src + (c0 + c) * ld);
+        }
+        const size_t drow = ((size_t)q * nb + b) * kW;
+        double e = 1.0;
+        if (q > 0 && lane < rows) e = __ldcg(&P.chain[((size_t)(q - 1) * nb + b) * kW + lane].e1);
+        const double T0 = b > 0 ? __ldcg(&P.chain[drow - 1].tn) : 1.0;
         __syncwarp();
+        const double D = lane < rows ? (double)tile[lane][lane] : 1.0;
+        const double g = e / D;
+        // forward substitution through the diagonal block
+        for (int r = 0; r < rows; ++r) {
+            const double qr = __shfl_sync(FULL, z * g, r);
+            if (lane > r && lane < rows) z = fma(-(double)tile[lane][r], qr, z);
+        }
+        const double pv = lane < rows ? z / D : 0.0;
+        double x = lane < rows ? (double)sg * pv * pv : 0.0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x += y;
+        }
+        const double Tn = T0 + x;
+        double Tp = __shfl_up_sync(FULL, Tn, 1);
+        if (lane == 0) Tp = T0;
+        const bool bad = lane < rows && !(D > 0.0 && D <= DBL_MAX && Tn > 0.0 && Tn <= DBL_MAX);
+        const unsigned badm = __ballot_sync(FULL, bad);
+        if (badm && lane == 0) record_error(sy, kStatusNotPD, c0 + (__ffs(badm) - 1));
+        const double av = (double)sg * pv / e;
+        const double bv = pv * e / Tn;
+        const double cc = sqrt(Tn / Tp);
+        const double e1 = e / cc;
+        const double d1 = D * cc;
+        if (lane < rows) {
+            st_coef(P.coef + drow + lane, CoefRow<T>{(T)av, (T)bv, (T)e1, T(0)});
+            double2 *ch = reinterpret_cast<double2 *>(P.chain + drow + lane);
+            __stcg(ch, make_double2(e * pv, e1));
+            __stcg(ch + 1, make_double2(d1, Tn));
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_gpu(P.pflag + (size_t)q * nb + b, sy.epoch);
+
+        // the wave's rotations inside the diagonal block
+        const T at = (T)av, bt = (T)bv, et = (T)e1;
+        for (int r = 0; r < rows; ++r) {
+            const T ar = __shfl_sync(FULL, at, r);
+            const T br = __shfl_sync(FULL, bt, r);
+            const T er = __shfl_sync(FULL, et, r);
+            if (lane > r && lane < ncols) {
+                const T s = fma(ar, uh, tile[lane][r]);
+                uh = fma(-br, s, uh);
+                tile[lane][r] = last ? s * er : s;
+            }
+        }
+        if (lane < rows) tile[lane][lane] = (T)d1;
+        __syncwarp();
+        if (lane < rows) {
+            T *dst = P.L + c0 + lane;
+            for (int c = lane; c < ncols; ++c) __stcg(dst + (c0 + c) * ld, tile[c][lane]);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_gpu(prog_me, ep64 + b + 1);
     }
 }
 
-__global__ void info_init_kernel(long long *info)
-{
-    info[0] = 0;
-    info[1] = -1;
-}
 
 // ---------------------------------------------------------------- host side
 
 struct Workspace {
     int device = -1;
     cudaStream_t stream = nullptr;
-    void *coef = nullptr;
-    size_t coef_bytes = 0;
-    int *flags = nullptr;
-    int nflags = 0;
-    int *misc = nullptr;         // [0] ticket, [32] abort (separate cache lines)
-    long long *status = nullptr; // {status, info}
+    void *coef = nullptr;          // CoefRow panels
+    void *chain = nullptr;         // ChainRow panels
+    size_t panel_rows = 0;         // capacity of coef/chain in rows
+    int *pflag = nullptr;          // panel flags
+    long long *progress = nullptr; // progress counters
+    size_t nflags = 0;
+    int *misc = nullptr;           // [0] ticket, [32] abort (separate cache lines)
+    long long *status = nullptr;   // {status, info}
     int epoch = 0;
 };
 
@@ -189,33 +303,41 @@ static int sm_count(int dev)
     return cache[dev];
 }
 
-static int alloc_workspace(Workspace *w, size_t coef_bytes, int nflags)
+static const long long kStatusInit[2] = {0, -1};
+
+static int alloc_workspace(Workspace *w, size_t rows, size_t nflags)
 {
-    if (w->coef_bytes >= coef_bytes && w->nflags >= nflags && w->misc) return CHM_OK;
+    if (w->panel_rows >= rows && w->nflags >= nflags && w->misc) return CHM_OK;
     // Queued work on this stream may still use the old buffers.
     if (cudaStreamSynchronize(w->stream) != cudaSuccess) return CHM_ERR_CUDA;
-    if (w->coef_bytes < coef_bytes) {
+    if (w->panel_rows < rows) {
         cudaFree(w->coef);
-        w->coef = nullptr;
-        w->coef_bytes = 0;
-        if (cudaMalloc(&w->coef, coef_bytes) != cudaSuccess) return CHM_ERR_NOMEM;
-        w->coef_bytes = coef_bytes;
+        cudaFree(w->chain);
+        w->coef = w->chain = nullptr;
+        w->panel_rows = 0;
+        if (cudaMalloc(&w->coef, rows * sizeof(CoefRow<double>)) != cudaSuccess) return CHM_ERR_NOMEM;
+        if (cudaMalloc(&w->chain, rows * sizeof(ChainRow)) != cudaSuccess) return CHM_ERR_NOMEM;
+        w->panel_rows = rows;
     }
     if (w->nflags < nflags) {
-        cudaFree(w->flags);
-        w->flags = nullptr;
+        cudaFree(w->pflag);
+        cudaFree(w->progress);
+        w->pflag = nullptr;
+        w->progress = nullptr;
         w->nflags = 0;
-        if (cudaMalloc(&w->flags, sizeof(int) * (size_t)nflags) != cudaSuccess) return CHM_ERR_NOMEM;
-        if (cudaMemset(w->flags, 0, sizeof(int) * (size_t)nflags) != cudaSuccess) return CHM_ERR_CUDA;
+        if (cudaMalloc(&w->pflag, sizeof(int) * nflags) != cudaSuccess) return CHM_ERR_NOMEM;
+        if (cudaMalloc(&w->progress, sizeof(long long) * nflags) != cudaSuccess) return CHM_ERR_NOMEM;
+        if (cudaMemset(w->pflag, 0, sizeof(int) * nflags) != cudaSuccess) return CHM_ERR_CUDA;
+        if (cudaMemset(w->progress, 0, sizeof(long long) * nflags) != cudaSuccess) return CHM_ERR_CUDA;
         w->nflags = nflags;
         w->epoch = 0;
     }
     if (!w->misc) {
         if (cudaMalloc(&w->misc, 64 * sizeof(int)) != cudaSuccess) return CHM_ERR_NOMEM;
         if (cudaMalloc(&w->status, 2 * sizeof(long long)) != cudaSuccess) return CHM_ERR_NOMEM;
-        const long long init[2] = {0, -1};
         if (cudaMemset(w->misc, 0, 64 * sizeof(int)) != cudaSuccess) return CHM_ERR_CUDA;
-        if (cudaMemcpy(w->status, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpy(w->status, kStatusInit, sizeof(kStatusInit), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
             return CHM_ERR_CUDA;
     }
     return CHM_OK;
@@ -233,6 +355,12 @@ static Workspace *find_workspace(int dev, cudaStream_t s, bool create)
     return w;
 }
 
+__global__ void info_init_kernel(long long *info)
+{
+    info[0] = 0;
+    info[1] = -1;
+}
+
 template <typename T>
 static int launch_modify(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
                          const int8_t *sigma, int sign, cudaStream_t stream, long long *d_info)
@@ -240,47 +368,52 @@ static int launch_modify(T *L, long long n, long long ld, const T *V, long long 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
     const int nblocks = (int)((n + kW - 1) / kW);
+    const int wmax = (int)std::min<long long>(k, kMaxWaves);
     std::lock_guard<std::mutex> lock(g_mu);
     Workspace *w = find_workspace(dev, stream, true);
-    int rc = alloc_workspace(w, sizeof(T) * 4 * (size_t)kW * kKB * (size_t)nblocks, nblocks);
+    int rc = alloc_workspace(w, (size_t)wmax * nblocks * kW, (size_t)wmax * nblocks);
     if (rc != CHM_OK) return rc;
-    if (d_info) info_init_kernel<<<1, 1, 0, stream>>>(d_info);
-
+    if (d_info) {
+        info_init_kernel<<<1, 1, 0, stream>>>(d_info);
+        if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
+    }
     static int occ[2][64] = {{0}};
     int &bps = occ[sizeof(T) == 8 ? 0 : 1][dev & 63];
     if (!bps) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, modify_wavefront_kernel<T>, kW, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wave_kernel<T>, kW, 0);
         if (bps < 1) bps = 1;
     }
-    const int grid = std::max(1, std::min(nblocks, sm_count(dev) * bps));
-
-    for (long long q0 = 0; q0 < k; q0 += kKB) {
-        const int kb = (int)std::min<long long>(kKB, k - q0);
-        unsigned mask = 0;
-        for (int q = 0; q < kb; ++q) {
+    for (long long q0 = 0; q0 < k; q0 += kMaxWaves) {
+        const int nw = (int)std::min<long long>(kMaxWaves, k - q0);
+        unsigned long long mask = 0;
+        for (int q = 0; q < nw; ++q) {
             const int sg = sigma ? sigma[q0 + q] : sign;
-            if (sg < 0) mask |= 1u << q;
+            if (sg < 0) mask |= 1ull << q;
         }
         // ticket and abort flag start at zero for every launch
         if (cudaMemsetAsync(w->misc, 0, 64 * sizeof(int), stream) != cudaSuccess) return CHM_ERR_CUDA;
-        ModifyParams<T> prm;
+        WaveParams<T> prm;
         prm.L = L;
         prm.n = n;
         prm.ld = ld;
         prm.V = V + q0 * ldv;
         prm.ldv = ldv;
-        prm.kb = kb;
-        prm.sign_mask = mask;
+        prm.nwaves = nw;
         prm.nblocks = nblocks;
-        prm.coef = static_cast<T *>(w->coef);
-        prm.sync.flags = w->flags;
+        prm.down_mask = mask;
+        prm.coef = static_cast<CoefRow<T> *>(w->coef);
+        prm.chain = static_cast<ChainRow *>(w->chain);
+        prm.pflag = w->pflag;
+        prm.progress = w->progress;
         prm.sync.ticket = w->misc;
         prm.sync.abort_flag = w->misc + 32;
         prm.sync.status = w->status;
         prm.sync.user_info = d_info;
         prm.sync.epoch = ++w->epoch;
         prm.sync.timeout_ns = timeout_ns();
-        modify_wavefront_kernel<T><<<grid, kW, 0, stream>>>(prm);
+        const long long tasks = (long long)nw * nblocks;
+        const int grid = (int)std::max(1ll, std::min<long long>(tasks, (long long)sm_count(dev) * bps));
+        wave_kernel<T><<<grid, kW, 0, stream>>>(prm);
         if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
     }
     return CHM_OK;
@@ -292,7 +425,7 @@ static int check_args(const void *L, long long n, long long ld, const void *V, l
     if (n < 0 || k < 0) return CHM_ERR_ARG;
     if (dtype != CHM_F64 && dtype != CHM_F32_MIXED) return CHM_ERR_ARG;
     if (ld < std::max(1ll, n) || ldv < std::max(1ll, n)) return CHM_ERR_ARG;
-    if (n > (1ll << 31) - kW) return CHM_ERR_ARG;
+    if (n > (1ll << 26)) return CHM_ERR_ARG;
     const size_t elt = dtype == CHM_F64 ? 8 : 4;
     if (n > 0 && (!L || ((uintptr_t)L % elt))) return CHM_ERR_ARG;
     if (n > 0 && k > 0 && (!V || ((uintptr_t)V % elt))) return CHM_ERR_ARG;
@@ -362,8 +495,8 @@ int chm_status_sync(chm_stream_t stream, int64_t *info)
         if (w && w->status) {
             if (cudaMemcpy(h, w->status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
                 return CHM_ERR_CUDA;
-            const long long init[2] = {0, -1};
-            if (cudaMemcpy(w->status, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess)
+            if (cudaMemcpy(w->status, chm::kStatusInit, sizeof(chm::kStatusInit),
+                           cudaMemcpyHostToDevice) != cudaSuccess)
                 return CHM_ERR_CUDA;
         }
     }
