@@ -130,6 +130,17 @@ const char *chm_status_string(int status);
 /* Library version as major*10000 + minor*100 + patch. */
 int chm_version(void);
 
+/*
+ * Diagnostics.  When the environment variable CHM_TRACE is set to 1 before
+ * the first call, every launch records, per task, 16 int64 stamps of the
+ * device's %globaltimer (ns) at fixed points of the task (slot 15 holds the
+ * SM id).  chm_trace_dump synchronises the device and writes the last
+ * launch's records (tasks x 16 int64, native endianness) to the file `path`.
+ * Returns CHM_OK, CHM_ERR_STATE if tracing is off, CHM_ERR_ARG if the file
+ * cannot be written, or CHM_ERR_CUDA.  Not for production use.
+ */
+int chm_trace_dump(const char *path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ def load(build_if_missing: bool = False):
         "chm_status_sync": ([vp, vp], i32),
         "chm_status_string": ([i32], ctypes.c_char_p),
         "chm_version": ([], i32),
+        "chm_trace_dump": ([ctypes.c_char_p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -103,6 +104,10 @@ def chm_status_string(status) -> str:
 
 def chm_version() -> int:
     return load().chm_version()
+
+
+def chm_trace_dump(path) -> int:
+    return load().chm_trace_dump(path.encode() if isinstance(path, str) else path)
 
 
 # ---------------------------------------------------------------- tensor helpers

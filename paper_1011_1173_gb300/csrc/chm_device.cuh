@@ -58,6 +58,13 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int *p)
     return v;
 }
 
+__device__ __forceinline__ long long ld_relaxed_gpu(const long long *p)
+{
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ long long global_ns()
 {
     long long t;
@@ -89,20 +96,30 @@ __device__ __forceinline__ void record_error(const SyncArgs &s, long long code, 
     if (code == kStatusTimeout) atomicExch(s.abort_flag, 1);
 }
 
-// One thread waits until *p == want (an int flag) or, for a 64-bit counter,
-// until *p >= want.  Returns false if the launch is being aborted or the wait
-// ran out of time (then recorded as CHM_ERR_TIMEOUT with info = who).
-template <typename F>
-__device__ __forceinline__ bool bounded_wait(const SyncArgs &s, F ready, long long who)
+// One thread waits until ready() holds.  ready() polls with relaxed loads
+// (cheap, no ordering) under exponential backoff; once it holds, acquire()
+// performs the single acquiring load that orders this thread's later reads
+// after the writer's release.  Returns false if the launch is being aborted
+// or the wait ran out of time (then recorded as CHM_ERR_TIMEOUT, info = who).
+template <typename F, typename A>
+__device__ __forceinline__ bool bounded_wait(const SyncArgs &s, F ready, A acquire, long long who)
 {
-    if (ready()) return true;
+    if (ready()) {
+        acquire();
+        return true;
+    }
     const long long t0 = global_ns();
+    unsigned ns = 16;
     for (unsigned it = 1;; ++it) {
-        __nanosleep(32);
-        if (ready()) return true;
-        if ((it & 31u) == 0u) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        if (ready()) {
+            acquire();
+            return true;
+        }
+        if ((it & 15u) == 0u) {
             if (aborted(s)) return false;
-            if (global_ns() - t0 > s.timeout_ns || it > (1u << 27)) {
+            if (global_ns() - t0 > s.timeout_ns || it > (1u << 26)) {
                 record_error(s, kStatusTimeout, who);
                 return false;
             }
