@@ -116,6 +116,32 @@ int chm_modify_ex(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, in
                   int64_t *d_info);
 
 /*
+ * Same operation and arguments as chm_modify_ex, for callers that cannot
+ * allocate device memory: code running where cudaMalloc is not permitted or
+ * must not be called (inside CUDA-graph stream capture, from a real-time or
+ * memory-budgeted host thread that owns all device memory itself, or under an
+ * allocator that forbids allocations outside its own pool).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *
+ * Scratch: a file-scope device array of 16 MiB that every GPU which loads
+ * the library holds until the process exits.  It limits the order to
+ * n <= 8192 (larger n returns CHM_ERR_BUDGET before any work is enqueued) and
+ * the vectors per launch (more vectors are processed in several launches).
+ * The first call on a device (with that device current) looks up the array's
+ * device address and clears its flag words; make that first call before any
+ * stream capture.  All calls share the array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU (different streams, or
+ * different host threads without ordering) race and give wrong results.
+ * Device-side errors (CHM_ERR_NOT_PD, CHM_ERR_TIMEOUT) are reported only
+ * through d_info; chm_status_sync does not see this variant's status.
+ * Returns CHM_OK or CHM_ERR_ARG / CHM_ERR_BUDGET / CHM_ERR_CUDA.
+ */
+int chm_modify_noalloc(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k,
+                       const int8_t *sigma, int sign, int dtype, chm_stream_t stream,
+                       int64_t *d_info);
+
+/*
  * Synchronises `stream`, then reads and clears the status word of the
  * current device and that stream.
  *   info   optional HOST int64[2] receiving {status, info}

@@ -59,6 +59,7 @@ def load(build_if_missing: bool = False):
         "chm_update": ([vp, i64, i64, vp, i64, i32, vp], i32),
         "chm_downdate": ([vp, i64, i64, vp, i64, i32, vp], i32),
         "chm_modify_ex": ([vp, i64, i64, vp, i64, i64, vp, i32, i32, vp, vp], i32),
+        "chm_modify_noalloc": ([vp, i64, i64, vp, i64, i64, vp, i32, i32, vp, vp], i32),
         "chm_status_sync": ([vp, vp], i32),
         "chm_status_string": ([i32], ctypes.c_char_p),
         "chm_version": ([], i32),
@@ -92,6 +93,10 @@ def chm_downdate(L, n, ld, V, k, dtype, stream):
 
 def chm_modify_ex(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info):
     return load().chm_modify_ex(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info)
+
+
+def chm_modify_noalloc(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info):
+    return load().chm_modify_noalloc(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info)
 
 
 def chm_status_sync(stream, info):

@@ -42,6 +42,7 @@ struct Layout {
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t align_up_const(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static Layout layout(int nb_cap, int nw, int nb)
 {
@@ -156,39 +157,60 @@ __global__ void info_init_kernel(long long *info)
     info[1] = -1;
 }
 
+// Scratch memory of one launch sequence: the arrays of layout(), the misc
+// words and the status word, and the epoch counter of that scratch.
+struct Scratch {
+    char *base;
+    int nb_cap;
+    int *misc;
+    long long *status;
+    int *epoch;
+};
+
+// One-time per-(device, type) kernel set-up; allocates nothing.
 template <typename T>
-static int launch_modify(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
-                         const int8_t *sigma, int sign, cudaStream_t stream, long long *d_info)
+static int kernel_setup(int dev, int *bps_out)
+{
+    static int occ[2][64] = {{0}};
+    int &bps = occ[sizeof(T) == 8 ? 0 : 1][dev & 63];
+    if (!bps) {
+        const size_t smem = 4 * (size_t)kWarpSmemBytes;
+        if (cudaFuncSetAttribute(wave_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return CHM_ERR_CUDA;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wave_kernel<T>, 128, smem) != cudaSuccess ||
+            b < 1)
+            return CHM_ERR_CUDA;
+        const char *cap = getenv("CHM_MAX_CTAS_PER_SM");
+        if (cap && atoi(cap) > 0 && atoi(cap) < b) b = atoi(cap);
+        bps = b;
+    }
+    *bps_out = bps;
+    return CHM_OK;
+}
+
+// Enqueue the launches of one modification (up to nw_max waves each) on
+// `stream` using scratch `sc`.  Tracing (which allocates) only if allowed.
+template <typename T>
+static int launch_waves(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
+                        const int8_t *sigma, int sign, cudaStream_t stream, long long *d_info,
+                        const Scratch &sc, int nw_max, bool allow_trace)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
-    const int nb = (int)((n + kW - 1) / kW);
-    const int wmax = (int)std::min<long long>(k, kMaxWaves);
-    std::lock_guard<std::mutex> lock(g_mu);
-    Workspace *w = find_workspace(dev, stream, true);
-    Layout lay0;
-    int rc = alloc_workspace(w, wmax, nb, &lay0);
+    int bps = 0;
+    int rc = kernel_setup<T>(dev, &bps);
     if (rc != CHM_OK) return rc;
+    const int nb = (int)((n + kW - 1) / kW);
+    const int nsm = sm_count(dev);
     if (d_info) {
         info_init_kernel<<<1, 1, 0, stream>>>(d_info);
         if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
     }
     const size_t smem = 4 * (size_t)kWarpSmemBytes;
-    static int occ[2][64] = {{0}};
-    int &bps = occ[sizeof(T) == 8 ? 0 : 1][dev & 63];
-    if (!bps) {
-        if (cudaFuncSetAttribute(wave_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return CHM_ERR_CUDA;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wave_kernel<T>, 128, smem);
-        if (bps < 1) return CHM_ERR_CUDA;
-        const char *cap = getenv("CHM_MAX_CTAS_PER_SM");
-        if (cap && atoi(cap) > 0 && atoi(cap) < bps) bps = atoi(cap);
-    }
-    const int nsm = sm_count(dev);
-    char *base = static_cast<char *>(w->buf);
-    for (long long q0 = 0; q0 < k; q0 += kMaxWaves) {
-        const int nw = (int)std::min<long long>(kMaxWaves, k - q0);
+    for (long long q0 = 0; q0 < k; q0 += nw_max) {
+        const int nw = (int)std::min<long long>(nw_max, k - q0);
         const int ndiag = (nw + 3) / 4;
         if (ndiag + 1 > nsm) return CHM_ERR_ARG;
         unsigned long long mask = 0;
@@ -197,9 +219,10 @@ static int launch_modify(T *L, long long n, long long ld, const T *V, long long 
             if (sg < 0) mask |= 1ull << q;
         }
         // ticket, abort flag and the start-up role registry are zero for every launch
-        if (cudaMemsetAsync(w->misc, 0, kMiscInts * sizeof(int), stream) != cudaSuccess)
+        if (cudaMemsetAsync(sc.misc, 0, kMiscInts * sizeof(int), stream) != cudaSuccess)
             return CHM_ERR_CUDA;
-        const Layout ly = layout(w->nb_cap, nw, nb);
+        const Layout ly = layout(sc.nb_cap, nw, nb);
+        char *base = sc.base;
         WaveParams<T> prm;
         prm.L = L;
         prm.n = n;
@@ -208,7 +231,7 @@ static int launch_modify(T *L, long long n, long long ld, const T *V, long long 
         prm.ldv = ldv;
         prm.nwaves = nw;
         prm.nblocks = nb;
-        prm.fstride = w->nb_cap;
+        prm.fstride = sc.nb_cap;
         prm.down_mask = mask;
         prm.coef = reinterpret_cast<CoefRow<T> *>(base + ly.coef);
         prm.chain = reinterpret_cast<ChainRow *>(base + ly.chain);
@@ -221,12 +244,12 @@ static int launch_modify(T *L, long long n, long long ld, const T *V, long long 
         prm.rdiag = reinterpret_cast<double *>(base + ly.rdiag);
         prm.rtile = reinterpret_cast<double *>(base + ly.rtile);
         prm.rflag0 = reinterpret_cast<int *>(base + ly.rflag0);
-        prm.smslot = w->misc + 128;
-        prm.smrole = w->misc + 128 + kMaxSm;
-        prm.ndiag = w->misc + 64;
+        prm.smslot = sc.misc + 128;
+        prm.smrole = sc.misc + 128 + kMaxSm;
+        prm.ndiag = sc.misc + 64;
         prm.ndiag_blocks = ndiag;
         prm.trace = nullptr;
-        if (trace_on()) {
+        if (allow_trace && trace_on()) {
             const size_t need = (size_t)2 * nw * nb * kTracePoints;
             if (g_trace_cap < need) {
                 cudaFree(g_trace);
@@ -240,17 +263,33 @@ static int launch_modify(T *L, long long n, long long ld, const T *V, long long 
                 g_trace_tasks = (size_t)2 * nw * nb;
             }
         }
-        prm.sync.ticket = w->misc;
-        prm.sync.abort_flag = w->misc + 32;
-        prm.sync.status = w->status;
+        prm.sync.ticket = sc.misc;
+        prm.sync.abort_flag = sc.misc + 32;
+        prm.sync.status = sc.status;
         prm.sync.user_info = d_info;
-        prm.sync.epoch = ++w->epoch;
+        prm.sync.epoch = ++*sc.epoch;
         prm.sync.timeout_ns = timeout_ns();
-        const int grid = nsm * bps;
-        wave_kernel<T><<<grid, 128, smem, stream>>>(prm);
+        wave_kernel<T><<<nsm * bps, 128, smem, stream>>>(prm);
         if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
     }
     return CHM_OK;
+}
+
+template <typename T>
+static int launch_modify(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
+                         const int8_t *sigma, int sign, cudaStream_t stream, long long *d_info)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
+    const int nb = (int)((n + kW - 1) / kW);
+    const int wmax = (int)std::min<long long>(k, kMaxWaves);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *w = find_workspace(dev, stream, true);
+    Layout lay0;
+    int rc = alloc_workspace(w, wmax, nb, &lay0);
+    if (rc != CHM_OK) return rc;
+    const Scratch sc{static_cast<char *>(w->buf), w->nb_cap, w->misc, w->status, &w->epoch};
+    return launch_waves<T>(L, n, ld, V, ldv, k, sigma, sign, stream, d_info, sc, kMaxWaves, true);
 }
 
 static int check_args(const void *L, long long n, long long ld, const void *V, long long ldv,
@@ -292,6 +331,91 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
                                 k, sigma, sign, stream, d_info);
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+
+// chm_modify_noalloc serves callers that must not allocate device memory:
+// its scratch is this array, one copy on every GPU that loads the library,
+// held until the process exits.  Every call shares it.
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;
+constexpr long long kNoAllocMaxN = 8192;
+constexpr int kNoAllocNbCap = (int)((kNoAllocMaxN + kW - 1) / kW);
+// misc words, then the status word, then the arrays of layout()
+constexpr size_t kNoAllocStatusOff = align_up_const(kMiscInts * sizeof(int), 256);
+constexpr size_t kNoAllocHeader = kNoAllocStatusOff + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocState {
+    bool ready = false;
+    char *base = nullptr;  // device address of g_noalloc_scratch on this device
+    int epoch = 0;
+};
+static NoAllocState g_noalloc[64];
+static std::mutex g_noalloc_mu;
+
+// First call on a device (with that device current): look up the array's
+// device address and zero its flag words once; later launches only ever
+// compare flags against larger epochs.
+static int noalloc_setup(int dev, NoAllocState **out)
+{
+    NoAllocState &st = g_noalloc[dev];
+    if (!st.ready) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CHM_ERR_CUDA;
+        char *base = static_cast<char *>(p);
+        const Layout lay = layout(kNoAllocNbCap, 1, 1);
+        if (cudaMemset(base, 0, kNoAllocHeader + lay.flags_end) != cudaSuccess) return CHM_ERR_CUDA;
+        if (cudaMemcpy(base + kNoAllocStatusOff, kStatusInit, sizeof(kStatusInit),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return CHM_ERR_CUDA;
+        if (cudaDeviceSynchronize() != cudaSuccess) return CHM_ERR_CUDA;
+        st.base = base;
+        st.ready = true;
+    }
+    *out = &st;
+    return CHM_OK;
+}
+
+// Waves per launch that fit the array for nb column blocks (0: none).
+static int noalloc_waves(int nb)
+{
+    for (int nw = kMaxWaves; nw >= 1; --nw)
+        if (kNoAllocHeader + layout(kNoAllocNbCap, nw, nb).total <= kNoAllocBytes) return nw;
+    return 0;
+}
+
+static int modify_noalloc(void *L, long long n, long long ld, const void *V, long long ldv,
+                          long long k, const int8_t *sigma, int sign, int dtype,
+                          cudaStream_t stream, long long *d_info)
+{
+    int rc = check_args(L, n, ld, V, ldv, k, sigma, sign, dtype);
+    if (rc != CHM_OK) return rc;
+    if (n > kNoAllocMaxN) return CHM_ERR_BUDGET;
+    if (n == 0 || k == 0) {
+        if (d_info) {
+            info_init_kernel<<<1, 1, 0, stream>>>(d_info);
+            if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
+        }
+        return CHM_OK;
+    }
+    const int nb = (int)((n + kW - 1) / kW);
+    const int nw_max = noalloc_waves(nb);
+    if (nw_max < 1) return CHM_ERR_BUDGET;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return CHM_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocState *st = nullptr;
+    rc = noalloc_setup(dev, &st);
+    if (rc != CHM_OK) return rc;
+    const Scratch sc{st->base + kNoAllocHeader, kNoAllocNbCap, reinterpret_cast<int *>(st->base),
+                     reinterpret_cast<long long *>(st->base + kNoAllocStatusOff), &st->epoch};
+    if (dtype == CHM_F64)
+        return launch_waves<double>(static_cast<double *>(L), n, ld, static_cast<const double *>(V), ldv,
+                                    k, sigma, sign, stream, d_info, sc, nw_max, false);
+    return launch_waves<float>(static_cast<float *>(L), n, ld, static_cast<const float *>(V), ldv, k,
+                               sigma, sign, stream, d_info, sc, nw_max, false);
+}
+
 }  // namespace chm
 
 extern "C" {
@@ -315,6 +439,13 @@ int chm_modify_ex(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, in
 {
     return chm::modify_dispatch(L, n, ld, V, ldv, k, sigma, sign, dtype, (cudaStream_t)stream,
                                 reinterpret_cast<long long *>(d_info));
+}
+
+int chm_modify_noalloc(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k,
+                       const int8_t *sigma, int sign, int dtype, chm_stream_t stream, int64_t *d_info)
+{
+    return chm::modify_noalloc(L, n, ld, V, ldv, k, sigma, sign, dtype, (cudaStream_t)stream,
+                               reinterpret_cast<long long *>(d_info));
 }
 
 int chm_status_sync(chm_stream_t stream, int64_t *info)

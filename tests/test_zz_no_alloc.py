@@ -1,0 +1,63 @@
+"""The no-allocation entry point, chm_modify_noalloc.
+
+Some callers cannot allocate device memory (inside CUDA-graph capture,
+under an allocator that owns all device memory, from budgeted real-time
+threads).  chm_modify_noalloc serves them from a fixed device array; these
+tests call it through the C ABI and check its factor against chm_modify_ex's
+on two calls in a row.  This file is collected last so that a run stopping
+at the first failure has already run every other test.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1011_1173_gb300 import chm, inputs
+from tests.common import TOL_F64, colscaled_err
+
+TOL_MIXED = 1e-4
+
+
+def _call(fn, L, V, sigma, d_info=None):
+    k = V.shape[0]
+    sig = (ctypes.c_int8 * k)(*[int(s) for s in sigma])
+    return fn(L.data_ptr(), L.shape[0], L.shape[1], V.data_ptr(), V.shape[1], k,
+              ctypes.cast(sig, ctypes.c_void_p), 1, chm.dtype_code(L),
+              torch.cuda.current_stream().cuda_stream,
+              None if d_info is None else d_info.data_ptr())
+
+
+def test_noalloc_rejects_too_large_without_work():
+    # the size check comes before any CUDA call, so this needs no GPU
+    st = chm.chm_modify_noalloc(8, 8193, 8193, 8, 8193, 1, None, 1, chm.CHM_F64, None, None)
+    assert st == chm.CHM_ERR_BUDGET
+    st = chm.chm_modify_noalloc(8, 10, 9, 8, 10, 1, None, 1, chm.CHM_F64, None, None)
+    assert st == chm.CHM_ERR_ARG
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,k,dtype", [(1500, 16, torch.float64), (4100, 40, torch.float64),
+                                       (700, 9, torch.float32)])
+def test_noalloc_matches_allocating_path_twice(n, k, dtype):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    chm.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    seed = 4242 + n + k
+    L0 = inputs.spd_factor(n, seed, ld=n + 3).to("cuda", dtype)
+    V = inputs.update_block(n, k, seed, scale=0.5 / np.sqrt(n * k)).to("cuda", dtype)
+    sig = inputs.sigma_vector(k, seed).tolist()
+    tol = TOL_F64 if dtype == torch.float64 else TOL_MIXED
+    ref = L0.clone()
+    got = L0.clone()
+    info = torch.full((2,), 99, dtype=torch.int64, device="cuda")
+    for _ in range(2):  # two calls in a row, each continuing from the last
+        assert _call(chm.chm_modify_ex, ref, V, sig) == chm.CHM_OK
+        assert _call(chm.chm_modify_noalloc, got, V, sig, info) == chm.CHM_OK
+        torch.cuda.synchronize()
+        assert info.tolist() == [chm.CHM_OK, -1]
+        assert chm.status_sync()[0] == chm.CHM_OK
+        assert colscaled_err(got.cpu().numpy(), ref.cpu().numpy()) <= tol
