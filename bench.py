@@ -39,9 +39,22 @@ METRIC = "rank-k up/downdate effective HBM GB/s"
 UNIT = "GB/s"
 # Nominal FP64 rate of the part: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# dram read+write bytes per launch of the dominant kernel from the last ncu
-# capture of the current kernel version (None until one is taken).
-NCU_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from an ncu capture of this workload (profiles/), keyed by the
+# sha256 (first 16 hex digits) of the kernel sources it was taken with; a
+# capture of an older kernel version reads as null.
+NCU_TRAFFIC = {("wave_kernel<double>", "859a14c4a7d3e184"): 279.7e6}
+KERNEL_SOURCES = ("paper_1011_1173_gb300/csrc/chm_wave.cuh", "paper_1011_1173_gb300/csrc/chm_device.cuh",
+                  "paper_1011_1173_gb300/csrc/chm_modify.cu")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def alg_bytes(n, k, elt=8):
@@ -293,7 +306,8 @@ def main():
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64)",
                 "launch_ms": launch_ms,
                 "hbm_gbs": alg_bytes(n, k) / (launch_ms / 1e3) / 1e9,
-                "traffic": NCU_TRAFFIC.get(kernel)}
+                "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash())),
+                "kernel_source_hash": kernel_source_hash()}
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:

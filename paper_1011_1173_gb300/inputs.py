@@ -60,8 +60,12 @@ def spd_factor(n: int, seed: int, ld: int | None = None, device="cpu",
     A.div_(n)
     A.diagonal().add_(1.0)
     # torch's lower factor G (A = G G^T) in row-major order has exactly the
-    # memory image of the column-major upper factor L = G^T.
-    G = torch.linalg.cholesky(A)
+    # memory image of the column-major upper factor L = G^T.  Orders up to
+    # 8192 are factored on the host (LAPACK), larger ones on the device.
+    if n <= 8192:
+        G = torch.linalg.cholesky(A.cpu())
+    else:
+        G = torch.linalg.cholesky(A)
     del A
     out[:, :n].copy_(G)
     return out
