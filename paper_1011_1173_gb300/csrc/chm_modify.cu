@@ -37,8 +37,8 @@ struct Workspace {
 // are read in every launch.
 struct Layout {
     int nb_cap;
-    size_t pflag, progress, zflag, rflag0, flags_end;
-    size_t coef, chain, chain0, tend, zbuf, rdiag, rtile, total;
+    size_t pflag, progress, zflag, cflag, dflag, rflag0, flags_end;
+    size_t coef, chain, chain0, tend, zbuf, carry, rdiag, rtile, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -54,6 +54,8 @@ static Layout layout(int nb_cap, int nw, int nb)
     L.pflag = o;    o = align256(o + sizeof(int) * nflag);
     L.progress = o; o = align256(o + sizeof(long long) * nflag);
     L.zflag = o;    o = align256(o + sizeof(int) * nflag);
+    L.cflag = o;    o = align256(o + sizeof(int) * nflag);
+    L.dflag = o;    o = align256(o + sizeof(int) * nflag);
     L.rflag0 = o;   o = align256(o + sizeof(int) * (size_t)nb_cap);
     L.flags_end = o;
     L.coef = o;     o = align256(o + sizeof(CoefRow<double>) * rows);
@@ -61,6 +63,7 @@ static Layout layout(int nb_cap, int nw, int nb)
     L.chain0 = o;   o = align256(o + sizeof(ChainRow) * (size_t)nb * kW);
     L.tend = o;     o = align256(o + sizeof(double) * (size_t)nw * nb);
     L.zbuf = o;     o = align256(o + sizeof(double) * rows);
+    L.carry = o;    o = align256(o + sizeof(double) * rows);
     L.rdiag = o;    o = align256(o + sizeof(double) * rows * kW);
     L.rtile = o;    o = align256(o + sizeof(double) * rows * kW);
     L.total = o;
@@ -102,6 +105,8 @@ static int sm_count(int dev)
 }
 
 static const long long kStatusInit[2] = {0, -1};
+// Waves per launch: each takes one SM for its diagonal work.
+constexpr int kWavesPerLaunch = 16;
 // misc ints: [0] ticket, [32] abort, [64] ndiag, [128..] smslot, [128+kMaxSm..] smrole
 constexpr int kMiscInts = 128 + 2 * kMaxSm;
 
@@ -174,7 +179,7 @@ static int kernel_setup(int dev, int *bps_out)
     static int occ[2][64] = {{0}};
     int &bps = occ[sizeof(T) == 8 ? 0 : 1][dev & 63];
     if (!bps) {
-        const size_t smem = 4 * (size_t)kWarpSmemBytes;
+        const size_t smem = kBlockSmemBytes;
         if (cudaFuncSetAttribute(wave_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return CHM_ERR_CUDA;
@@ -208,11 +213,12 @@ static int launch_waves(T *L, long long n, long long ld, const T *V, long long l
         info_init_kernel<<<1, 1, 0, stream>>>(d_info);
         if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
     }
-    const size_t smem = 4 * (size_t)kWarpSmemBytes;
+    const size_t smem = kBlockSmemBytes;
+    // one SM per wave: keep most SMs for the sweep
+    nw_max = std::max(1, std::min(nw_max, std::min(kWavesPerLaunch, nsm / 8)));
     for (long long q0 = 0; q0 < k; q0 += nw_max) {
         const int nw = (int)std::min<long long>(nw_max, k - q0);
-        const int ndiag = (nw + 3) / 4;
-        if (ndiag + 1 > nsm) return CHM_ERR_ARG;
+        if (nw + 1 > nsm) return CHM_ERR_ARG;
         unsigned long long mask = 0;
         for (int q = 0; q < nw; ++q) {
             const int sg = sigma ? sigma[q0 + q] : sign;
@@ -241,13 +247,15 @@ static int launch_waves(T *L, long long n, long long ld, const T *V, long long l
         prm.progress = reinterpret_cast<long long *>(base + ly.progress);
         prm.zbuf = reinterpret_cast<double *>(base + ly.zbuf);
         prm.zflag = reinterpret_cast<int *>(base + ly.zflag);
+        prm.cflag = reinterpret_cast<int *>(base + ly.cflag);
+        prm.dflag = reinterpret_cast<int *>(base + ly.dflag);
+        prm.carry = reinterpret_cast<double *>(base + ly.carry);
         prm.rdiag = reinterpret_cast<double *>(base + ly.rdiag);
         prm.rtile = reinterpret_cast<double *>(base + ly.rtile);
         prm.rflag0 = reinterpret_cast<int *>(base + ly.rflag0);
         prm.smslot = sc.misc + 128;
         prm.smrole = sc.misc + 128 + kMaxSm;
         prm.ndiag = sc.misc + 64;
-        prm.ndiag_blocks = ndiag;
         prm.trace = nullptr;
         if (allow_trace && trace_on()) {
             const size_t need = (size_t)2 * nw * nb * kTracePoints;

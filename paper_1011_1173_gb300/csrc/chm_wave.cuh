@@ -16,18 +16,25 @@
 // element and vector.
 //
 // Work split (one launch):
-//   * wave workers: one warp per wave, on a few SMs that run nothing else
-//     (claimed at start-up through %smid).  Wave q walks the diagonal blocks
-//     in order, forms z for the block from the sweep's carry and a 32-row dot
-//     product, runs the forward substitution through the block with ratios
-//     precomputed by the sweep, and publishes the block's rotation panel.
+//   * wave blocks: one thread block per wave, each on an SM of its own
+//     (claimed at start-up through %smid), walks the diagonal blocks in
+//     order with four specialised warps that hand work to each other through
+//     shared memory:
+//       A  the forward substitution through the diagonal block, with ratio
+//          matrices prepared in advance;
+//       B  the 32-row dot product that carries the previous block's p into
+//          this block, then p, T and the rotation coefficients, and the
+//          publication of the block's panel;
+//       C  the wave's rotations inside the diagonal block, the next wave's
+//          ratio matrix of that block, and its store;
+//       D  prefetch of the next block's inputs (cp.async).
 //   * sweep workers: every other warp takes tasks (wave q, column block b)
-//     in ticket order t = b * nwaves + q and rotates the block's tiles with
-//     wave q's panels, the update vector held in registers.  It also hands
-//     the wave worker what it needs next: the carry z for the block, and the
-//     ratio matrices of the next wave.
-// Every wait is bounded (%globaltimer), and a task only waits on events of
-// tasks with smaller tickets or on wave workers, which always run.
+//     in ticket order t = b * nwaves + q and rotates the block's off-diagonal
+//     tiles with wave q's panels, the update vector held in registers.  It
+//     also publishes what the wave block needs: the carry z for the block,
+//     the carry u_hat at the diagonal, and the next wave's dot-product matrix.
+// Every wait is bounded (%globaltimer); a sweep task only waits on events of
+// tasks with smaller tickets or on wave blocks, which always run.
 //
 // Storage between waves of one launch: the diagonal holds true values, an
 // off-diagonal L_ij is held as S_ij = L_ij / e_i; the last wave of the launch
@@ -69,24 +76,42 @@ struct WaveParams {
     ChainRow *chain;               // [nw][nb][kW]
     ChainRow *chain0;              // [nb][kW]      original diagonal data
     double *tend;                  // [nw][nb]      T after the block's last row
-    int *pflag;                    // [nw][fstride] panel published (== epoch)
-    long long *progress;           // [nw][fstride] (epoch << 32) + tiles done (b + 1 = all)
     double *zbuf;                  // [nw][nb][kW]  T u_hat before the block's last tile
-    int *zflag;                    // [nw][fstride]
+    double *carry;                 // [nw][nb][kW]  u_hat at the diagonal block
     double *rdiag;                 // [nw][nb][kW][kW] -S_rc e_r / D_r, r < c (diagonal block)
     double *rtile;                 // [nw][nb][kW][kW] -S_rc e_r (tile: rows of block b, cols of b+1)
+    int *pflag;                    // [nw][fstride] panel published (== epoch)
+    long long *progress;           // [nw][fstride] (epoch << 32) + off-diagonal tiles done
+    int *zflag;                    // [nw][fstride] zbuf ready
+    int *cflag;                    // [nw][fstride] carry ready
+    int *dflag;                    // [nw][fstride] diagonal block done, next wave's rdiag ready
     int *rflag0;                   // [nb]          wave-0 data of block b ready
     int *smslot;                   // [kMaxSm]      arrivals per SM (zero at launch)
     int *smrole;                   // [kMaxSm]      role decided by the SM's first block
-    int *ndiag;                    // diag-role blocks claimed so far
-    int ndiag_blocks;              // blocks of 4 wave workers needed
+    int *ndiag;                    // wave blocks claimed so far
     long long *trace;              // optional per-task timestamps
     SyncArgs sync;
 };
 
-// Per-warp shared memory: the larger of the wave worker's two ratio
-// matrices and the sweep worker's tile and row data.
-constexpr int kWarpSmemBytes = 2 * kW * kW * 8 + 2 * kW * 32;
+// Dynamic shared memory per thread block: four warps' worth.
+constexpr int kWarpSmemBytes = 18432;
+constexpr int kBlockSmemBytes = 4 * kWarpSmemBytes;
+
+// Shared memory of a wave block.
+template <typename T>
+struct WaveSmem {
+    double R[2][kW][kW];   // chain ratios of the block, [r][c]
+    double Rt[2][kW][kW];  // dot-product matrix of the tile above, [r][c]
+    ChainRow rowd[2][kW];  // row data of the block before this wave
+    double zpart[2][kW];   // carry z before the tile above
+    double zbox[kW];       // B -> A: z entering the chain
+    double cbox[kW];       // A -> B: z after the chain
+    CoefRow<T> cf[2][kW];  // B -> C: sweep coefficients of the block
+    ChainRow cnew[2][kW];  // B -> C: row data after this wave
+    T DT[kW][kW + 1];      // C: the diagonal tile, [c][r]
+    int dseq, zseq, cseq, bseq, fseq, bail;
+};
+static_assert(sizeof(WaveSmem<double>) <= kBlockSmemBytes, "wave block shared memory");
 
 // ---------------------------------------------------------------- small helpers
 
@@ -157,6 +182,42 @@ __device__ __forceinline__ bool wait_ge(const SyncArgs &s, const long long *p, l
     return bounded_wait(s, [&] { return ld_acquire_gpu(p) >= want; }, [] {}, who);
 }
 
+// Shared-memory sequence counters between the warps of a wave block.  The
+// writer stores its data, fences the block and raises the counter; the
+// reader waits for the counter (bounded) and fences before reading.  `bail`
+// is raised by a warp that stops early, so that the others stop waiting.
+__device__ __forceinline__ void seq_post(int *seq, int v)
+{
+    __threadfence_block();
+    *reinterpret_cast<volatile int *>(seq) = v;
+}
+__device__ __forceinline__ bool seq_wait(const SyncArgs &s, int *seq, int want, int *bail,
+                                         long long who)
+{
+    volatile int *vs = reinterpret_cast<volatile int *>(seq);
+    volatile int *vb = reinterpret_cast<volatile int *>(bail);
+    if (*vs >= want) {
+        __threadfence_block();
+        return true;
+    }
+    const long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(8);
+        if (*vs >= want) {
+            __threadfence_block();
+            return true;
+        }
+        if ((it & 255u) == 0u) {
+            if (*vb || aborted(s)) return false;
+            if (global_ns() - t0 > s.timeout_ns || it > (1u << 28)) {
+                record_error(s, kStatusTimeout, who);
+                *vb = 1;
+                return false;
+            }
+        }
+    }
+}
+
 // Asynchronous 16-byte global -> shared copies (L2 only), completed by cp_async_wait.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -166,29 +227,31 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Copy one kW x kW double matrix (8 KB, row-major) into shared memory with
-// the 32 lanes of a warp.
-__device__ __forceinline__ void fetch_matrix(double (*dst)[kW], const double *src, int lane)
+// Copy `bytes` (a multiple of 16) from global to shared memory with the 32
+// lanes of a warp.
+__device__ __forceinline__ void fetch_bytes(void *dst, const void *src, int bytes, int lane)
 {
     const char *g = reinterpret_cast<const char *>(src);
-    char *d = reinterpret_cast<char *>(&dst[0][0]);
-#pragma unroll
-    for (int i = 0; i < kW * kW * 8 / (16 * 32); ++i) {
-        const int off = (i * 32 + lane) * 16;
-        cp_async16(d + off, g + off);
-    }
+    char *d = reinterpret_cast<char *>(dst);
+    for (int off = lane * 16; off < bytes; off += 32 * 16) cp_async16(d + off, g + off);
 }
 
-// Warp-wide: lane 0 waits, every lane gets the verdict; the __syncwarp
-// orders the other lanes' later loads after lane 0's acquire.
+// Warp-wide wait: all 32 lanes poll together and lane 0's verdict is the
+// warp's.  The poll loop is warp-uniform on purpose: a loop taken by lane 0
+// alone leaves the warp split, and on this part every later shfl.sync of the
+// warp then pays a resynchronisation (measured: a 32-deep dependent shuffle
+// chain 8.6 times slower), which is exactly the latency-bound path of the
+// chain and of the sweep tasks.
 #define CHM_WARP_WAIT(expr)                                   \
     do {                                                      \
-        int ok_ = 1;                                          \
-        if (lane == 0) ok_ = (expr) ? 1 : 0;                  \
+        int ok_ = (expr) ? 1 : 0;                             \
         ok_ = __shfl_sync(0xffffffffu, ok_, 0);               \
         if (!ok_) return;                                     \
         __syncwarp();                                         \
     } while (0)
+
+// The same for a shared-memory sequence counter of the wave block.
+#define CHM_SEQ_WAIT(seqp, want) CHM_WARP_WAIT(seq_wait(sy, (seqp), (want), &S.bail, who))
 
 #define CHM_TRACE(pt)                                                                            \
     do {                                                                                         \
@@ -224,8 +287,8 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
 
     if (q == 0) {
         // Original-factor data of block b for wave 0: the diagonal and its
-        // inverse, the diagonal block's chain ratios, and (b >= 1) a copy of
-        // the tile above the block, taken before any wave rotates it.
+        // inverse, the diagonal block's chain ratios, and (b >= 1) the dot
+        // product matrix of the tile above, taken before any wave rotates it.
         T x[kW];
 #pragma unroll
         for (int c = 0; c < kW; ++c)
@@ -273,7 +336,6 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
 #pragma unroll
         for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         __syncwarp();
-        if (p == b - 2) CHM_TRACE(4);
         T S[kW];
 #pragma unroll
         for (int r = 0; r < kW; ++r) S[r] = tile[lane][r];
@@ -286,11 +348,17 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
             }
         }
         if (p == b - 2) {
-            // the wave worker's carry for block b: z = T u_hat after rows < (b-1) kW
+            // the wave block's carry for block b: z = T u_hat after rows < (b-1) kW
             __stcg(P.zbuf + ((size_t)q * nb + b) * kW + lane, active ? tnext * (double)uh : 0.0);
             __syncwarp();
             if (lane == 0) st_release_gpu(P.zflag + (size_t)q * P.fstride + b, epoch);
-            CHM_TRACE(5);
+        }
+        if (lastTile) {
+            // u_hat entering the diagonal block, for the wave block's rotations there
+            __stcg(P.carry + ((size_t)q * nb + b) * kW + lane, active ? (double)uh : 0.0);
+            __syncwarp();
+            if (lane == 0) st_release_gpu(P.cflag + (size_t)q * P.fstride + b, epoch);
+            CHM_TRACE(2);
         }
         if (lastTile && has_next) {
             // next wave's dot-product matrix for tile (b-1, b): -S' e'
@@ -316,171 +384,140 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
         }
         __syncwarp();
         if (lane == 0) st_release_gpu(prog_me, ep64 + p + 1);
-        if (p == b - 2) CHM_TRACE(6);
     }
-
-    // Diagonal block: wave q's rotations inside it.  The diagonal tile as
-    // the previous wave left it is fetched while the panel is pending.
-    if (prog_prev) CHM_WARP_WAIT(wait_ge(sy, prog_prev, ep64 + b + 1, who));
-    {
-        T x[kW];
-#pragma unroll
-        for (int c = 0; c < kW; ++c)
-            x[c] = (lane <= c && c < ncols) ? __ldcg(P.L + c0 + lane + (c0 + c) * ld) : T(0);
-        CHM_WARP_WAIT(wait_eq(sy, P.pflag + (size_t)q * P.fstride + b, epoch, who));
-        CHM_TRACE(2);
-        const size_t drow = ((size_t)q * nb + b) * kW;
-        cf[lane] = ld_coef(P.coef + drow + lane);
-        ch[lane] = ld_chain(P.chain + drow + lane);
-#pragma unroll
-        for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
-    }
-    __syncwarp();
-    {
-        T S[kW];
-#pragma unroll
-        for (int r = 0; r < kW; ++r) S[r] = tile[lane][r];
-#pragma unroll
-        for (int r = 0; r < kW; ++r) {
-            if (r < lane) {
-                const CoefRow<T> c = cf[r];
-                S[r] = fma(c.a, uh, S[r]);
-                uh = fma(-c.b, S[r], uh);
-            }
-        }
-        if (has_next) {
-            // next wave's chain ratios for this block: -S'_rc e'_r / D'_r (r < c)
-            double *rd = P.rdiag + (((size_t)(q + 1) * nb) + b) * kW * kW;
-#pragma unroll
-            for (int r = 0; r < kW; ++r) {
-                const double v = (r < lane && active) ? -(double)S[r] * ch[r].e1 * ch[r].id1 : 0.0;
-                __stcg(rd + (size_t)r * kW + lane, v);
-            }
-        }
-        if (last) {
-#pragma unroll
-            for (int r = 0; r < kW; ++r)
-                if (r < lane) S[r] *= cf[r].e1;
-        }
-#pragma unroll
-        for (int r = 0; r < kW; ++r)
-            if (r < lane) tile[lane][r] = S[r];
-        if (active) tile[lane][lane] = (T)ch[lane].d1;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int c = 0; c < kW; ++c)
-        if (lane <= c && c < ncols) __stcg(P.L + c0 + lane + (c0 + c) * ld, tile[c][lane]);
-    __syncwarp();
     CHM_TRACE(3);
-    if (lane == 0) st_release_gpu(prog_me, ep64 + b + 1);
 }
 
-// ---------------------------------------------------------------- wave worker
+// ---------------------------------------------------------------- wave block
 
+#define CHM_WTRACE(b, pt)                                                                      \
+    do {                                                                                       \
+        if (P.trace && lane == 0)                                                              \
+            P.trace[((size_t)P.nwaves * P.nblocks + (size_t)q * P.nblocks + (b)) * kTracePoints + \
+                    (pt)] = global_ns();                                                       \
+    } while (0)
+
+// Warp D: the inputs of each block for warps A and B, one block ahead.
 template <typename T>
-__device__ void wave_worker(const WaveParams<T> &P, int q, unsigned char *sm)
+__device__ void wave_prefetch(const WaveParams<T> &P, int q, WaveSmem<T> &S)
 {
-    double(*R)[kW] = reinterpret_cast<double(*)[kW]>(sm);                 // chain ratios [r][c]
-    double(*Rt)[kW] = reinterpret_cast<double(*)[kW]>(sm + kW * kW * 8);  // tile above [r][c]
+    const int lane = threadIdx.x & 31;
+    const SyncArgs &sy = P.sync;
+    const long long n = P.n;
+    const int nb = P.nblocks;
+    const int epoch = sy.epoch;
+    const long long ep64 = (long long)epoch << 32;
+    const long long who = -1 - q;
+    const long long *prog_prev = q > 0 ? P.progress + (size_t)(q - 1) * P.fstride : nullptr;
+    for (int b = 0; b < nb; ++b) {
+        const int s = b & 1;
+        const long long c0 = (long long)b * kW;
+        // the slot's previous block (b - 2) must be finished by warps A, B, C
+        if (b >= 2) CHM_SEQ_WAIT(&S.fseq, b - 1);
+        CHM_WTRACE(b, 0);
+        if (q == 0) {
+            CHM_WARP_WAIT(wait_eq(sy, P.rflag0 + b, epoch, who));
+        } else {
+            CHM_WARP_WAIT(wait_eq(sy, P.dflag + (size_t)(q - 1) * P.fstride + b, epoch, who) &&
+                          (b == 0 || wait_ge(sy, prog_prev + b, ep64 + b, who)));
+        }
+        CHM_WTRACE(b, 1);
+        if (b >= 2) CHM_WARP_WAIT(wait_eq(sy, P.zflag + (size_t)q * P.fstride + b, epoch, who));
+        CHM_WTRACE(b, 2);
+        fetch_bytes(&S.R[s][0][0], P.rdiag + ((size_t)q * nb + b) * kW * kW, kW * kW * 8, lane);
+        if (b >= 1) fetch_bytes(&S.Rt[s][0][0], P.rtile + ((size_t)q * nb + (b - 1)) * kW * kW, kW * kW * 8, lane);
+        fetch_bytes(&S.rowd[s][0], (q == 0 ? P.chain0 + (size_t)b * kW : P.chain + ((size_t)(q - 1) * nb + b) * kW),
+                    kW * (int)sizeof(ChainRow), lane);
+        if (b >= 2) {
+            fetch_bytes(&S.zpart[s][0], P.zbuf + ((size_t)q * nb + b) * kW, kW * 8, lane);
+        } else {
+            S.zpart[s][lane] = (c0 + lane < n) ? (double)P.V[c0 + lane + (long long)q * P.ldv] : 0.0;
+        }
+        cp_async_commit();
+        cp_async_wait();
+        __syncwarp();
+        CHM_WTRACE(b, 3);
+        if (lane == 0) seq_post(&S.dseq, b + 1);
+    }
+}
+
+// Warp A: the forward substitution through each diagonal block.
+template <typename T>
+__device__ void wave_chain(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+{
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const SyncArgs &sy = P.sync;
-    const long long n = P.n;
-    const int nw = P.nwaves, nb = P.nblocks;
-    const int epoch = sy.epoch;
-    const long long ep64 = (long long)epoch << 32;
-    const int sg = ((P.down_mask >> q) & 1ull) ? -1 : 1;
-    const double sgd = (double)sg;
     const long long who = -1 - q;
-    const long long *prog_prev = q > 0 ? P.progress + (size_t)(q - 1) * P.fstride : nullptr;
-
-    // Inputs of block b: row data, ratio matrices, carry z.
-    auto rowdata = [&](int b) -> ChainRow {
-        const int rows = (int)min((long long)kW, n - (long long)b * kW);
-        if (lane >= rows) return ChainRow{1.0, 1.0, 1.0, 1.0};
-        return ld_chain((q == 0 ? P.chain0 + (size_t)b * kW : P.chain + ((size_t)(q - 1) * nb + b) * kW) +
-                        lane);
-    };
-    auto carry = [&](int b) -> double {
-        const long long c0 = (long long)b * kW;
-        if (b >= 2) return __ldcg(P.zbuf + ((size_t)q * nb + b) * kW + lane);
-        return (c0 + lane < n) ? (double)P.V[c0 + lane + (long long)q * P.ldv] : 0.0;
-    };
-    auto fetch = [&](int b) {
-        fetch_matrix(R, P.rdiag + ((size_t)q * nb + b) * kW * kW, lane);
-        if (b >= 1) fetch_matrix(Rt, P.rtile + ((size_t)q * nb + (b - 1)) * kW * kW, lane);
-        cp_async_commit();
-    };
-
-    double pprev = 0.0;  // p of the previous block's row `lane`
-    double Tend = 1.0;   // T before the current block
-    double iTend = 1.0;  // 1 / Tend
-    bool have = false;   // block b's inputs already requested
-    ChainRow rowd{1.0, 1.0, 1.0, 1.0};
-    double z = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        const long long c0 = (long long)b * kW;
-        const int rows = (int)min((long long)kW, n - c0);
-        const bool active = lane < rows;
-        const size_t trace_row = (size_t)nw * nb + (size_t)q * nb + b;
-        CHM_TRACE(0);
-        if (!have) {
-            if (q == 0) {
-                CHM_WARP_WAIT(wait_eq(sy, P.rflag0 + b, epoch, who));
-            } else {
-                CHM_WARP_WAIT(wait_ge(sy, prog_prev + b, ep64 + b + 1, who));
-            }
-            if (b >= 2) CHM_WARP_WAIT(wait_eq(sy, P.zflag + (size_t)q * P.fstride + b, epoch, who));
-            fetch(b);
-            rowd = rowdata(b);
-            z = carry(b);
-        }
-        cp_async_wait();
-        __syncwarp();
-        CHM_TRACE(1);
-        // early look at the next block's flags: every lane issues the same
-        // acquiring loads now and compares after the arithmetic below, so
-        // the loads are in flight meanwhile
-        int fz = epoch;
-        long long fr = 0;
-        if (b + 1 < nb) {
-            if (b + 1 >= 2) fz = ld_acquire_gpu(P.zflag + (size_t)q * P.fstride + b + 1);
-            fr = q == 0 ? (long long)ld_acquire_gpu(P.rflag0 + b + 1) : ld_acquire_gpu(prog_prev + b + 1);
-        }
-        if (b >= 1) {
-            // rows of the block above: z_c += sum_r (-S_rc e_r) p_r
-            double z1 = 0.0, z2 = 0.0, z3 = 0.0;
-#pragma unroll
-            for (int r = 0; r < kW; r += 4) {
-                z = fma(Rt[r][lane], __shfl_sync(FULL, pprev, r), z);
-                z1 = fma(Rt[r + 1][lane], __shfl_sync(FULL, pprev, r + 1), z1);
-                z2 = fma(Rt[r + 2][lane], __shfl_sync(FULL, pprev, r + 2), z2);
-                z3 = fma(Rt[r + 3][lane], __shfl_sync(FULL, pprev, r + 3), z3);
-            }
-            z = (z + z1) + (z2 + z3);
-        }
-        // forward substitution through the block
+    for (int b = 0; b < P.nblocks; ++b) {
+        CHM_SEQ_WAIT(&S.zseq, b + 1);
+        CHM_WTRACE(b, 8);
+        double(*R)[kW] = S.R[b & 1];
+        double z = S.zbox[lane];
 #pragma unroll
         for (int r = 0; r < kW; ++r) {
             const double zr = __shfl_sync(FULL, z, r);
             z = fma(R[r][lane], zr, z);
         }
+        S.cbox[lane] = z;
         __syncwarp();
-        // the ratio buffers are free again: request the next block's inputs
-        const bool rr = q == 0 ? fr == (long long)epoch : fr >= ep64 + b + 2;
-        const int nready = __all_sync(FULL, b + 1 < nb && fz == epoch && rr);
-        ChainRow rowd_next{1.0, 1.0, 1.0, 1.0};
-        double z_next = 0.0;
-        have = false;
-        if (nready) {
-            fetch(b + 1);
-            rowd_next = rowdata(b + 1);
-            z_next = carry(b + 1);
-            have = true;
+        CHM_WTRACE(b, 9);
+        if (lane == 0) seq_post(&S.cseq, b + 1);
+    }
+}
+
+// Warp B: the dot product into each block, then p, T and the coefficients
+// of the block just chained, and the panel's publication.  The next chain
+// is started before a panel is published whenever its inputs are already in.
+template <typename T>
+__device__ void wave_coef(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const SyncArgs &sy = P.sync;
+    const long long n = P.n;
+    const int nb = P.nblocks;
+    const int epoch = sy.epoch;
+    const double sgd = ((P.down_mask >> q) & 1ull) ? -1.0 : 1.0;
+    const long long who = -1 - q;
+    double pprev = 0.0;  // p of the block last chained, row `lane`
+    double Tend = 1.0, iTend = 1.0;
+    int pending = -1;    // block chained (or being chained) but not yet published
+    int next = 0;        // next block whose chain input is to be formed
+    bool ok = true;
+    auto wait_seq = [&](int *seq, int want) -> bool {
+        int v = seq_wait(sy, seq, want, &S.bail, who) ? 1 : 0;  // all lanes: see CHM_WARP_WAIT
+        v = __shfl_sync(FULL, v, 0);
+        __syncwarp();
+        return v != 0;
+    };
+    auto form_input = [&](int b) {
+        // z entering block b's chain: the carry plus the rows of the block above
+        const int s = b & 1;
+        double z = S.zpart[s][lane];
+        if (b >= 1) {
+            double z1 = 0.0, z2 = 0.0, z3 = 0.0;
+#pragma unroll
+            for (int r = 0; r < kW; r += 4) {
+                z = fma(S.Rt[s][r][lane], __shfl_sync(FULL, pprev, r), z);
+                z1 = fma(S.Rt[s][r + 1][lane], __shfl_sync(FULL, pprev, r + 1), z1);
+                z2 = fma(S.Rt[s][r + 2][lane], __shfl_sync(FULL, pprev, r + 2), z2);
+                z3 = fma(S.Rt[s][r + 3][lane], __shfl_sync(FULL, pprev, r + 3), z3);
+            }
+            z = (z + z1) + (z2 + z3);
         }
-        CHM_TRACE(2);
-        const double p = active ? z * rowd.id1 : 0.0;
+        S.zbox[lane] = z;
+        __syncwarp();
+        CHM_WTRACE(b, 4);
+        if (lane == 0) seq_post(&S.zseq, b + 1);
+    };
+    auto publish = [&](int b, double p) {
+        // T and the coefficients of block b (already chained), given its p
+        const int s = b & 1;
+        const long long c0 = (long long)b * kW;
+        const int rows = (int)min((long long)kW, n - c0);
+        const bool active = lane < rows;
+        const ChainRow rowd = S.rowd[s][lane];
         double x = sgd * p * p;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -498,23 +535,130 @@ __device__ void wave_worker(const WaveParams<T> &P, int q, unsigned char *sm)
         const double ratio = Tn * iTp;           // c^2
         const double rc = rsqrt_refined(ratio);  // 1/c
         const double c = ratio * rc;
-        const double a = sgd * p * rowd.ie1;
-        const double bb = p * rowd.e1 * iTn;
+        const CoefRow<T> cr{(T)(sgd * p * rowd.ie1), (T)(p * rowd.e1 * iTn), (T)(rowd.e1 * rc), T(0)};
         const ChainRow nrow{rowd.e1 * rc, rowd.ie1 * c, rowd.d1 * c, rowd.id1 * rc};
+        S.cf[s][lane] = cr;
+        S.cnew[s][lane] = nrow;
+        __syncwarp();
+        if (lane == 0) seq_post(&S.bseq, b + 1);
         if (active) {
             const size_t prow = ((size_t)q * nb + b) * kW + lane;
-            st_coef(P.coef + prow, CoefRow<T>{(T)a, (T)bb, (T)nrow.e1, T(0)});
+            st_coef(P.coef + prow, cr);
             st_chain(P.chain + prow, nrow);
         }
         if (lane == 0) __stcg(P.tend + (size_t)q * nb + b, Tlast);
         __syncwarp();
         if (lane == 0) st_release_gpu(P.pflag + (size_t)q * P.fstride + b, epoch);
-        CHM_TRACE(3);
-        pprev = p;
+        CHM_WTRACE(b, 5);
         Tend = Tlast;
         iTend = __shfl_sync(FULL, iTn, rows - 1);
-        rowd = rowd_next;
-        z = z_next;
+    };
+
+    while (ok && (next < nb || pending >= 0)) {
+        if (pending < 0) {
+            // nothing is being chained: form the next input (waiting for it)
+            if (!wait_seq(&S.dseq, next + 1)) return;
+            form_input(next);
+            pending = next++;
+        }
+        // collect the chain of `pending`; its p feeds the next dot product
+        if (!wait_seq(&S.cseq, pending + 1)) return;
+        const int done = pending;
+        pending = -1;
+        {
+            const long long c0 = (long long)done * kW;
+            pprev = (c0 + lane < n) ? S.cbox[lane] * S.rowd[done & 1][lane].id1 : 0.0;
+        }
+        if (next < nb) {
+            const int ready = __shfl_sync(FULL, *reinterpret_cast<volatile int *>(&S.dseq) >= next + 1 ? 1 : 0, 0);
+            if (ready) {
+                __threadfence_block();
+                form_input(next);
+                pending = next++;
+            }
+        }
+        publish(done, pprev);
+    }
+}
+
+// Warp C: the wave's rotations inside each diagonal block.
+template <typename T>
+__device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+{
+    const int lane = threadIdx.x & 31;
+    const SyncArgs &sy = P.sync;
+    const long long n = P.n, ld = P.ld;
+    const int nw = P.nwaves, nb = P.nblocks;
+    const int epoch = sy.epoch;
+    const bool last = q == nw - 1;
+    const bool has_next = q + 1 < nw;
+    const long long who = -1 - q;
+    for (int b = 0; b < nb; ++b) {
+        const int s = b & 1;
+        const long long c0 = (long long)b * kW;
+        const int ncols = (int)min((long long)kW, n - c0);
+        const bool active = lane < ncols;
+        // u_hat entering the block (from the sweep of its last off-diagonal tile)
+        T uh = T(0);
+        if (b == 0) {
+            uh = active ? P.V[c0 + lane + (long long)q * P.ldv] : T(0);
+        } else {
+            CHM_WARP_WAIT(wait_eq(sy, P.cflag + (size_t)q * P.fstride + b, epoch, who));
+            uh = (T)__ldcg(P.carry + ((size_t)q * nb + b) * kW + lane);
+        }
+        CHM_WTRACE(b, 10);
+        // the tile as the previous wave left it: warp D acquired that wave's
+        // release of this block before announcing the block's inputs
+        CHM_SEQ_WAIT(&S.dseq, b + 1);
+        {
+            T x[kW];
+#pragma unroll
+            for (int c = 0; c < kW; ++c)
+                x[c] = (lane <= c && c < ncols) ? __ldcg(P.L + c0 + lane + (c0 + c) * ld) : T(0);
+#pragma unroll
+            for (int c = 0; c < kW; ++c) S.DT[c][lane] = x[c];
+        }
+        CHM_WTRACE(b, 11);
+        CHM_SEQ_WAIT(&S.bseq, b + 1);
+        CHM_WTRACE(b, 12);
+        T Sv[kW];
+#pragma unroll
+        for (int r = 0; r < kW; ++r) Sv[r] = S.DT[lane][r];
+#pragma unroll
+        for (int r = 0; r < kW; ++r) {
+            if (r < lane) {
+                const CoefRow<T> c = S.cf[s][r];
+                Sv[r] = fma(c.a, uh, Sv[r]);
+                uh = fma(-c.b, Sv[r], uh);
+            }
+        }
+        if (has_next) {
+            // next wave's chain ratios for this block: -S'_rc e'_r / D'_r (r < c)
+            double *rd = P.rdiag + (((size_t)(q + 1) * nb) + b) * kW * kW;
+#pragma unroll
+            for (int r = 0; r < kW; ++r) {
+                const ChainRow cn = S.cnew[s][r];
+                const double v = (r < lane && active) ? -(double)Sv[r] * cn.e1 * cn.id1 : 0.0;
+                __stcg(rd + (size_t)r * kW + lane, v);
+            }
+        }
+        if (last) {
+#pragma unroll
+            for (int r = 0; r < kW; ++r)
+                if (r < lane) Sv[r] *= S.cf[s][r].e1;
+        }
+#pragma unroll
+        for (int r = 0; r < kW; ++r)
+            if (r < lane) S.DT[lane][r] = Sv[r];
+        if (active) S.DT[lane][lane] = (T)S.cnew[s][lane].d1;
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < kW; ++c)
+            if (lane <= c && c < ncols) __stcg(P.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
+        __syncwarp();
+        if (lane == 0) st_release_gpu(P.dflag + (size_t)q * P.fstride + b, epoch);
+        CHM_WTRACE(b, 13);
+        if (lane == 0) seq_post(&S.fseq, b + 1);
     }
 }
 
@@ -534,7 +678,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(WaveParams<T> P)
         if (smid < (unsigned)kMaxSm) {
             if (atomicAdd(P.smslot + smid, 1) == 0) {
                 const int d = atomicAdd(P.ndiag, 1);
-                if (d < P.ndiag_blocks) {
+                if (d < P.nwaves) {
                     role = kRoleDiag;
                     didx = d;
                 }
@@ -545,7 +689,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(WaveParams<T> P)
                 bounded_wait(
                     sy, [&] { return (seen = ld_relaxed_gpu(pr)) != 0; },
                     [&] { (void)ld_acquire_gpu(pr); }, -1000);
-                role = seen == kRoleDiag ? 0 : kRoleSweep;  // a wave-worker SM runs nothing else
+                role = seen == kRoleDiag ? 0 : kRoleSweep;  // a wave block's SM runs nothing else
             }
         }
         s_role = role;
@@ -554,12 +698,18 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(WaveParams<T> P)
     __syncthreads();
     const int role = s_role;
     if (role == 0) return;
-    unsigned char *sm = chm_smem + (size_t)warp * kWarpSmemBytes;
     if (role == kRoleDiag) {
-        const int q = s_didx * 4 + warp;
-        if (q < P.nwaves) wave_worker<T>(P, q, sm);
+        WaveSmem<T> &S = *reinterpret_cast<WaveSmem<T> *>(chm_smem);
+        if (threadIdx.x == 0) S.dseq = S.zseq = S.cseq = S.bseq = S.fseq = S.bail = 0;
+        __syncthreads();
+        const int q = s_didx;
+        if (warp == 0) wave_chain<T>(P, q, S);
+        else if (warp == 1) wave_coef<T>(P, q, S);
+        else if (warp == 2) wave_diag<T>(P, q, S);
+        else wave_prefetch<T>(P, q, S);
         return;
     }
+    unsigned char *sm = chm_smem + (size_t)warp * kWarpSmemBytes;
     const int ntasks = P.nwaves * P.nblocks;
     for (;;) {
         int t = 0;
@@ -572,6 +722,8 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(WaveParams<T> P)
 }
 
 #undef CHM_WARP_WAIT
+#undef CHM_SEQ_WAIT
 #undef CHM_TRACE
+#undef CHM_WTRACE
 
 }  // namespace chm
