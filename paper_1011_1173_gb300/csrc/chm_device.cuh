@@ -8,21 +8,16 @@
 
 namespace chm {
 
-// Columns per column block == rows per published rotation panel == one warp.
-constexpr int kW = 32;
-// Update vectors (waves) handled by one launch; more are split over launches.
-constexpr int kMaxWaves = 64;
-
 // Device status codes (mirror chm_status in chm.h).
 constexpr long long kStatusNotPD = -2;
 constexpr long long kStatusTimeout = -3;
 
-// Everything the blocks of one launch use to order themselves.
+// What a waiting or failing thread needs: the launch's abort flag and
+// status words, and the epoch that tags this launch's flags.
 struct SyncArgs {
-    int *ticket;           // task ticket counter, zero at launch
     int *abort_flag;       // non-zero once a block has timed out
-    long long *status;     // sticky {status, info} of the (device, stream)
-    long long *user_info;  // optional per-call {status, info}
+    long long *status;     // sticky {status, info} of the scratch owner
+    long long *user_info;  // optional {status, info} of the problem
     int epoch;             // distinguishes this launch's flags from older ones
     long long timeout_ns;  // bound on any single wait
 };

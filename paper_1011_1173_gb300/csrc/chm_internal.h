@@ -1,0 +1,75 @@
+// Host-side interface between the translation units of the library: the
+// scratch regions a launch of the wave kernel uses, the carving of problems
+// into them, and the launch itself (chm_modify.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "chm_layout.h"
+
+namespace chm {
+
+// Scratch of one owner (a stream's workspace, a batch plan, a server, the
+// no-allocation array).  The three regions are typed: a word of `iflags`
+// only ever holds an int flag and a word of `progress` only a progress
+// word, so stale words from earlier launches hold smaller epochs and never
+// match.  `ctl` holds kCtlInts control words whose epoch starts at 1.
+struct Scratch {
+    int *ctl = nullptr;
+    long long *status = nullptr;  // {status, row}, sticky
+    int *iflags = nullptr;
+    size_t iflags_cap = 0;        // ints
+    long long *progress = nullptr;
+    size_t progress_cap = 0;      // words
+    char *data = nullptr;
+    size_t data_bytes = 0;
+};
+
+// Shape of one problem as the scheduler sees it.
+struct ProbShape {
+    long long n;
+    int k;  // waves in the launch (1 .. kMaxWaves)
+};
+
+// Scratch needed by a list of problems laid out one after another.
+struct ScratchNeed {
+    size_t iflags = 0, progress = 0, data = 0;
+    int npairs = 0, nbmax = 0;
+};
+ScratchNeed scratch_need(const ProbShape *shapes, int count);
+
+// Fill the scratch pointers, nb, k and pair0 of problems[0..count) for the
+// layout of scratch_need(); the caller sets L, V, n, ld, ldv, down_mask and
+// info.  Returns the pair -> problem map.
+std::vector<int> carve(const ProbShape *shapes, int count, const Scratch &sc, Prob *problems);
+
+// Launch configuration.
+struct LaunchCfg {
+    int groups = 0;       // SM groups (0: automatic)
+    int ctas_per_sm = 0;  // resident blocks per SM (0: the occupancy limit)
+};
+
+// Number of SMs of a device and the occupancy limit of the wave kernel.
+int sm_count(int dev);
+int wave_occupancy(int dtype, int dev, int *ctas_per_sm);
+long long timeout_ns();
+int default_groups(int npairs, int nsm);
+
+// Enqueue one launch of the wave kernel on `stream`.  Either one problem
+// (`single`, no device tables) or `nprobs` problems whose records are in
+// device memory `d_probs` with pair map `d_pair_prob`.  `trace` is null or
+// a device array of 2 * npairs * nbmax * kTracePoints words.
+int launch_wave(int dtype, const Prob *single, const Prob *d_probs, const int *d_pair_prob,
+                int nprobs, int npairs, int nbmax, const Scratch &sc, const LaunchCfg &cfg,
+                long long *trace, cudaStream_t stream);
+
+// Set count {status, row} words to {0, -1} on `stream`.
+int info_init(long long *d_info, int count, cudaStream_t stream);
+
+// Allocate (and zero) a scratch with at least the given capacities.
+int scratch_alloc(Scratch *sc, size_t iflags, size_t progress, size_t data);
+void scratch_free(Scratch *sc);
+
+}  // namespace chm

@@ -1,6 +1,7 @@
 // C ABI of the rank-k Cholesky up/downdate (Walder 2010): argument checks,
-// the per-(device, stream) workspace, launches of the wave kernel
-// (chm_wave.cuh) and the device status word.
+// scratch carving, the launch of the wave kernel (chm_wave.cuh), the
+// per-(device, stream) workspace of the plain entry points, the
+// no-allocation variant and the device status word.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,82 +12,63 @@
 #include <vector>
 
 #include "chm.h"
+#include "chm_internal.h"
 #include "chm_wave.cuh"
 
 namespace chm {
 
-// ---------------------------------------------------------------- host side
+// ---------------------------------------------------------------- scratch carving
 
-// Device buffers of one (device, stream), grown on demand.
-struct Workspace {
-    int device = -1;
-    cudaStream_t stream = nullptr;
-    void *buf = nullptr;    // all per-launch arrays, carved by layout()
-    size_t bytes = 0;
-    int nb_cap = 0;         // blocks the flag arrays are laid out for
-    int *misc = nullptr;    // ticket, abort, ndiag, smslot[kMaxSm], smrole[kMaxSm]
-    long long *status = nullptr;
-    int epoch = 0;
-};
-
-// Byte offsets of the per-launch arrays.  The flag and counter arrays come
-// first, laid out for kMaxWaves waves and nb_cap blocks with fixed strides,
-// so a flag word keeps one meaning for the life of the allocation and stale
-// words from earlier launches (smaller epochs) never match; they are zeroed
-// once when allocated.  The data arrays after them are written before they
-// are read in every launch.
-struct Layout {
-    int nb_cap;
-    size_t pflag, progress, zflag, cflag, dflag, rflag0, flags_end;
-    size_t coef, chain, chain0, tend, zbuf, carry, rdiag, rtile, total;
-};
-
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t align_up_const(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-static Layout layout(int nb_cap, int nw, int nb)
+ScratchNeed scratch_need(const ProbShape *shapes, int count)
 {
-    Layout L;
-    L.nb_cap = nb_cap;
-    size_t o = 0;
-    const size_t nflag = (size_t)kMaxWaves * nb_cap;
-    const size_t rows = (size_t)nw * nb * kW;
-    L.pflag = o;    o = align256(o + sizeof(int) * nflag);
-    L.progress = o; o = align256(o + sizeof(long long) * nflag);
-    L.zflag = o;    o = align256(o + sizeof(int) * nflag);
-    L.cflag = o;    o = align256(o + sizeof(int) * nflag);
-    L.dflag = o;    o = align256(o + sizeof(int) * nflag);
-    L.rflag0 = o;   o = align256(o + sizeof(int) * (size_t)nb_cap);
-    L.flags_end = o;
-    L.coef = o;     o = align256(o + sizeof(CoefRow<double>) * rows);
-    L.chain = o;    o = align256(o + sizeof(ChainRow) * rows);
-    L.chain0 = o;   o = align256(o + sizeof(ChainRow) * (size_t)nb * kW);
-    L.tend = o;     o = align256(o + sizeof(double) * (size_t)nw * nb);
-    L.zbuf = o;     o = align256(o + sizeof(double) * rows);
-    L.carry = o;    o = align256(o + sizeof(double) * rows);
-    L.rdiag = o;    o = align256(o + sizeof(double) * rows * kW);
-    L.rtile = o;    o = align256(o + sizeof(double) * rows * kW);
-    L.total = o;
-    return L;
+    ScratchNeed r;
+    for (int i = 0; i < count; ++i) {
+        const int nb = (int)((shapes[i].n + kW - 1) / kW);
+        const int k = shapes[i].k;
+        r.iflags += prob_iflags(nb, k);
+        r.progress += prob_progress(nb, k);
+        r.data += prob_data_bytes(nb, k);
+        r.npairs += k;
+        r.nbmax = std::max(r.nbmax, nb);
+    }
+    return r;
 }
 
-static std::mutex g_mu;
-static std::vector<Workspace *> g_ws;
-
-// Diagnostics: with CHM_TRACE=1 in the environment every launch records
-// per-task %globaltimer stamps; chm_trace_dump writes the last launch's.
-static long long *g_trace = nullptr;
-static size_t g_trace_tasks = 0, g_trace_cap = 0;
-static bool trace_on()
+std::vector<int> carve(const ProbShape *shapes, int count, const Scratch &sc, Prob *problems)
 {
-    static int v = [] {
-        const char *e = getenv("CHM_TRACE");
-        return e && atoi(e) > 0 ? 1 : 0;
-    }();
-    return v != 0;
+    std::vector<int> pair_prob;
+    size_t fi = 0, fp = 0, fd = 0;
+    int pair = 0;
+    for (int i = 0; i < count; ++i) {
+        const int nb = (int)((shapes[i].n + kW - 1) / kW);
+        const int k = shapes[i].k;
+        Prob &p = problems[i];
+        p.nb = nb;
+        p.k = k;
+        p.pair0 = pair;
+        p.iflags = sc.iflags + fi;
+        p.progress = sc.progress + fp;
+        p.data = sc.data + fd;
+        fi += prob_iflags(nb, k);
+        fp += prob_progress(nb, k);
+        fd += prob_data_bytes(nb, k);
+        pair_prob.insert(pair_prob.end(), (size_t)k, i);
+        pair += k;
+    }
+    return pair_prob;
 }
 
-static long long timeout_ns()
+// ---------------------------------------------------------------- device facts
+
+int sm_count(int dev)
+{
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 1;
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cache[dev];
+}
+
+long long timeout_ns()
 {
     static long long v = [] {
         const char *e = getenv("CHM_TIMEOUT_NS");
@@ -96,52 +78,190 @@ static long long timeout_ns()
     return v;
 }
 
-static int sm_count(int dev)
+static int env_int(const char *name)
 {
-    static int cache[64] = {0};
-    if (dev < 0 || dev >= 64) return 1;
-    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
-    return cache[dev];
+    const char *e = getenv(name);
+    return e ? atoi(e) : 0;
+}
+
+// One-time per-(device, type) set-up: the shared-memory attribute and the
+// occupancy limit; allocates nothing.
+template <typename T>
+static int occupancy(int dev, int *bps_out)
+{
+    static int occ[2][64] = {{0}};
+    if (dev < 0 || dev >= 64) return CHM_ERR_ARG;
+    int &bps = occ[sizeof(T) == 8 ? 0 : 1][dev];
+    if (!bps) {
+        const size_t smem = kBlockSmemBytes;
+        if (cudaFuncSetAttribute(wave_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return CHM_ERR_CUDA;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wave_kernel<T>, 128, smem) != cudaSuccess ||
+            b < 1)
+            return CHM_ERR_CUDA;
+        const int cap = env_int("CHM_MAX_CTAS_PER_SM");
+        if (cap > 0 && cap < b) b = cap;
+        bps = b;
+    }
+    *bps_out = bps;
+    return CHM_OK;
+}
+
+int wave_occupancy(int dtype, int dev, int *ctas_per_sm)
+{
+    return dtype == CHM_F64 ? occupancy<double>(dev, ctas_per_sm) : occupancy<float>(dev, ctas_per_sm);
+}
+
+// Groups: one per concurrently running wave, each with about eight sweep SMs.
+int default_groups(int npairs, int nsm)
+{
+    int g = env_int("CHM_GROUPS");
+    if (g <= 0) g = std::max(1, nsm / 9);
+    return std::max(1, std::min(std::min(g, npairs), std::min(kMaxGroups, nsm / 2)));
+}
+
+// ---------------------------------------------------------------- launch
+
+template <typename T>
+static int launch_t(const Prob *single, const Prob *d_probs, const int *d_pair_prob, int nprobs,
+                    int npairs, int nbmax, const Scratch &sc, const LaunchCfg &cfg, long long *trace,
+                    cudaStream_t stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
+    int bps = 0;
+    int rc = occupancy<T>(dev, &bps);
+    if (rc != CHM_OK) return rc;
+    if (cfg.ctas_per_sm > 0) bps = std::min(bps, cfg.ctas_per_sm);
+    const int nsm = sm_count(dev);
+    if (nsm < 2 || nsm > kMaxSm || npairs < 1) return CHM_ERR_ARG;
+    int G = cfg.groups > 0 ? cfg.groups : default_groups(npairs, nsm);
+    G = std::max(1, std::min(std::min(G, npairs), std::min(kMaxGroups, nsm / 2)));
+    Launch<T> P;
+    memset(&P, 0, sizeof(P));
+    P.probs = d_probs;
+    if (single) P.prob0 = *single;
+    P.pair_prob = d_pair_prob;
+    P.nprobs = nprobs;
+    P.npairs = npairs;
+    P.ngroups = G;
+    P.nbmax = nbmax;
+    P.ctl = sc.ctl;
+    P.status = sc.status;
+    P.trace = trace;
+    P.timeout_ns = timeout_ns();
+    wave_kernel<T><<<nsm * bps, 128, kBlockSmemBytes, stream>>>(P);
+    return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
+}
+
+int launch_wave(int dtype, const Prob *single, const Prob *d_probs, const int *d_pair_prob, int nprobs,
+                int npairs, int nbmax, const Scratch &sc, const LaunchCfg &cfg, long long *trace,
+                cudaStream_t stream)
+{
+    if (dtype == CHM_F64)
+        return launch_t<double>(single, d_probs, d_pair_prob, nprobs, npairs, nbmax, sc, cfg, trace, stream);
+    return launch_t<float>(single, d_probs, d_pair_prob, nprobs, npairs, nbmax, sc, cfg, trace, stream);
+}
+
+__global__ void info_init_kernel(long long *info, int count)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        info[2 * i] = 0;
+        info[2 * i + 1] = -1;
+    }
+}
+
+int info_init(long long *d_info, int count, cudaStream_t stream)
+{
+    if (!d_info || count <= 0) return CHM_OK;
+    info_init_kernel<<<std::min(64, (count + 127) / 128), 128, 0, stream>>>(d_info, count);
+    return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
 }
 
 static const long long kStatusInit[2] = {0, -1};
-// Waves per launch: each takes one SM for its diagonal work.
-constexpr int kWavesPerLaunch = 16;
-// misc ints: [0] ticket, [32] abort, [64] ndiag, [128..] smslot, [128+kMaxSm..] smrole
-constexpr int kMiscInts = 128 + 2 * kMaxSm;
 
-static int alloc_workspace(Workspace *w, int nw, int nb, Layout *out)
+// Control words: zero, epoch 1 (flag regions are zero, so no flag matches
+// until a launch of epoch >= 1 raises it).
+static int ctl_init(int *ctl, long long *status)
 {
-    if (w->buf && w->nb_cap >= nb) {
-        const Layout lay = layout(w->nb_cap, nw, nb);
-        if (lay.total <= w->bytes && w->misc) {
-            *out = lay;
-            return CHM_OK;
-        }
-    }
-    // Queued work on this stream may still use the old buffers.
-    if (cudaStreamSynchronize(w->stream) != cudaSuccess) return CHM_ERR_CUDA;
-    const int nb_cap = std::max(nb, w->nb_cap);
-    const Layout lay = layout(nb_cap, std::max(nw, (int)std::min<long long>(kMaxWaves, 16)), nb_cap);
-    cudaFree(w->buf);
-    w->buf = nullptr;
-    w->bytes = 0;
-    w->nb_cap = 0;
-    if (cudaMalloc(&w->buf, lay.total) != cudaSuccess) return CHM_ERR_NOMEM;
-    if (cudaMemset(w->buf, 0, lay.flags_end) != cudaSuccess) return CHM_ERR_CUDA;
-    w->bytes = lay.total;
-    w->nb_cap = nb_cap;
-    w->epoch = 0;
-    if (!w->misc) {
-        if (cudaMalloc(&w->misc, kMiscInts * sizeof(int)) != cudaSuccess) return CHM_ERR_NOMEM;
-        if (cudaMalloc(&w->status, 2 * sizeof(long long)) != cudaSuccess) return CHM_ERR_NOMEM;
-        if (cudaMemset(w->misc, 0, kMiscInts * sizeof(int)) != cudaSuccess) return CHM_ERR_CUDA;
-        if (cudaMemcpy(w->status, kStatusInit, sizeof(kStatusInit), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-            return CHM_ERR_CUDA;
-    }
-    *out = layout(nb_cap, nw, nb);
+    if (cudaMemset(ctl, 0, kCtlInts * sizeof(int)) != cudaSuccess) return CHM_ERR_CUDA;
+    const int one = 1;
+    if (cudaMemcpy(ctl + kCtlEpoch, &one, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CHM_ERR_CUDA;
+    if (cudaMemcpy(status, kStatusInit, sizeof(kStatusInit), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CHM_ERR_CUDA;
     return CHM_OK;
+}
+
+int scratch_alloc(Scratch *sc, size_t iflags, size_t progress, size_t data)
+{
+    if (!sc->ctl) {
+        if (cudaMalloc(&sc->ctl, kCtlInts * sizeof(int)) != cudaSuccess) return CHM_ERR_NOMEM;
+        if (cudaMalloc(&sc->status, 2 * sizeof(long long)) != cudaSuccess) return CHM_ERR_NOMEM;
+        const int rc = ctl_init(sc->ctl, sc->status);
+        if (rc != CHM_OK) return rc;
+    }
+    if (sc->iflags_cap < iflags) {
+        cudaFree(sc->iflags);
+        sc->iflags = nullptr;
+        sc->iflags_cap = 0;
+        const size_t cap = std::max(iflags, (size_t)4096);
+        if (cudaMalloc(&sc->iflags, cap * sizeof(int)) != cudaSuccess) return CHM_ERR_NOMEM;
+        if (cudaMemset(sc->iflags, 0, cap * sizeof(int)) != cudaSuccess) return CHM_ERR_CUDA;
+        sc->iflags_cap = cap;
+    }
+    if (sc->progress_cap < progress) {
+        cudaFree(sc->progress);
+        sc->progress = nullptr;
+        sc->progress_cap = 0;
+        const size_t cap = std::max(progress, (size_t)1024);
+        if (cudaMalloc(&sc->progress, cap * sizeof(long long)) != cudaSuccess) return CHM_ERR_NOMEM;
+        if (cudaMemset(sc->progress, 0, cap * sizeof(long long)) != cudaSuccess) return CHM_ERR_CUDA;
+        sc->progress_cap = cap;
+    }
+    if (sc->data_bytes < data) {
+        cudaFree(sc->data);
+        sc->data = nullptr;
+        sc->data_bytes = 0;
+        if (cudaMalloc(&sc->data, data) != cudaSuccess) return CHM_ERR_NOMEM;
+        sc->data_bytes = data;
+    }
+    return CHM_OK;
+}
+
+void scratch_free(Scratch *sc)
+{
+    cudaFree(sc->ctl);
+    cudaFree(sc->status);
+    cudaFree(sc->iflags);
+    cudaFree(sc->progress);
+    cudaFree(sc->data);
+    *sc = Scratch();
+}
+
+// ---------------------------------------------------------------- plain entry points
+
+// Scratch of one (device, stream), grown on demand.
+struct Workspace {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    Scratch sc;
+};
+
+static std::mutex g_mu;
+static std::vector<Workspace *> g_ws;
+
+// Diagnostics: with CHM_TRACE=1 in the environment every launch of the plain
+// entry points records %globaltimer stamps per task; chm_trace_dump writes
+// the last launch's.
+static long long *g_trace = nullptr;
+static size_t g_trace_words = 0, g_trace_cap = 0;
+static bool trace_on()
+{
+    static int v = env_int("CHM_TRACE") > 0 ? 1 : 0;
+    return v != 0;
 }
 
 static Workspace *find_workspace(int dev, cudaStream_t s, bool create)
@@ -156,109 +276,42 @@ static Workspace *find_workspace(int dev, cudaStream_t s, bool create)
     return w;
 }
 
-__global__ void info_init_kernel(long long *info)
+static unsigned long long down_mask(const int8_t *sigma, int sign, long long q0, int kw)
 {
-    info[0] = 0;
-    info[1] = -1;
-}
-
-// Scratch memory of one launch sequence: the arrays of layout(), the misc
-// words and the status word, and the epoch counter of that scratch.
-struct Scratch {
-    char *base;
-    int nb_cap;
-    int *misc;
-    long long *status;
-    int *epoch;
-};
-
-// One-time per-(device, type) kernel set-up; allocates nothing.
-template <typename T>
-static int kernel_setup(int dev, int *bps_out)
-{
-    static int occ[2][64] = {{0}};
-    int &bps = occ[sizeof(T) == 8 ? 0 : 1][dev & 63];
-    if (!bps) {
-        const size_t smem = kBlockSmemBytes;
-        if (cudaFuncSetAttribute(wave_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return CHM_ERR_CUDA;
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wave_kernel<T>, 128, smem) != cudaSuccess ||
-            b < 1)
-            return CHM_ERR_CUDA;
-        const char *cap = getenv("CHM_MAX_CTAS_PER_SM");
-        if (cap && atoi(cap) > 0 && atoi(cap) < b) b = atoi(cap);
-        bps = b;
+    unsigned long long mask = 0;
+    for (int q = 0; q < kw; ++q) {
+        const int sg = sigma ? sigma[q0 + q] : sign;
+        if (sg < 0) mask |= 1ull << q;
     }
-    *bps_out = bps;
-    return CHM_OK;
+    return mask;
 }
 
-// Enqueue the launches of one modification (up to nw_max waves each) on
-// `stream` using scratch `sc`.  Tracing (which allocates) only if allowed.
-template <typename T>
-static int launch_waves(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
-                        const int8_t *sigma, int sign, cudaStream_t stream, long long *d_info,
-                        const Scratch &sc, int nw_max, bool allow_trace)
+// Enqueue the launches of one modification, at most kw_max waves each, on
+// scratch `sc` (already large enough for kw_max waves).
+static int enqueue_single(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
+                          const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
+                          const Scratch &sc, int kw_max, bool allow_trace)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
-    int bps = 0;
-    int rc = kernel_setup<T>(dev, &bps);
-    if (rc != CHM_OK) return rc;
+    const size_t elt = dtype == CHM_F64 ? 8 : 4;
     const int nb = (int)((n + kW - 1) / kW);
-    const int nsm = sm_count(dev);
-    if (d_info) {
-        info_init_kernel<<<1, 1, 0, stream>>>(d_info);
-        if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
-    }
-    const size_t smem = kBlockSmemBytes;
-    // one SM per wave: keep most SMs for the sweep
-    nw_max = std::max(1, std::min(nw_max, std::min(kWavesPerLaunch, nsm / 8)));
-    for (long long q0 = 0; q0 < k; q0 += nw_max) {
-        const int nw = (int)std::min<long long>(nw_max, k - q0);
-        if (nw + 1 > nsm) return CHM_ERR_ARG;
-        unsigned long long mask = 0;
-        for (int q = 0; q < nw; ++q) {
-            const int sg = sigma ? sigma[q0 + q] : sign;
-            if (sg < 0) mask |= 1ull << q;
-        }
-        // ticket, abort flag and the start-up role registry are zero for every launch
-        if (cudaMemsetAsync(sc.misc, 0, kMiscInts * sizeof(int), stream) != cudaSuccess)
-            return CHM_ERR_CUDA;
-        const Layout ly = layout(sc.nb_cap, nw, nb);
-        char *base = sc.base;
-        WaveParams<T> prm;
-        prm.L = L;
-        prm.n = n;
-        prm.ld = ld;
-        prm.V = V + q0 * ldv;
-        prm.ldv = ldv;
-        prm.nwaves = nw;
-        prm.nblocks = nb;
-        prm.fstride = sc.nb_cap;
-        prm.down_mask = mask;
-        prm.coef = reinterpret_cast<CoefRow<T> *>(base + ly.coef);
-        prm.chain = reinterpret_cast<ChainRow *>(base + ly.chain);
-        prm.chain0 = reinterpret_cast<ChainRow *>(base + ly.chain0);
-        prm.tend = reinterpret_cast<double *>(base + ly.tend);
-        prm.pflag = reinterpret_cast<int *>(base + ly.pflag);
-        prm.progress = reinterpret_cast<long long *>(base + ly.progress);
-        prm.zbuf = reinterpret_cast<double *>(base + ly.zbuf);
-        prm.zflag = reinterpret_cast<int *>(base + ly.zflag);
-        prm.cflag = reinterpret_cast<int *>(base + ly.cflag);
-        prm.dflag = reinterpret_cast<int *>(base + ly.dflag);
-        prm.carry = reinterpret_cast<double *>(base + ly.carry);
-        prm.rdiag = reinterpret_cast<double *>(base + ly.rdiag);
-        prm.rtile = reinterpret_cast<double *>(base + ly.rtile);
-        prm.rflag0 = reinterpret_cast<int *>(base + ly.rflag0);
-        prm.smslot = sc.misc + 128;
-        prm.smrole = sc.misc + 128 + kMaxSm;
-        prm.ndiag = sc.misc + 64;
-        prm.trace = nullptr;
+    int rc = info_init(d_info, 1, stream);
+    if (rc != CHM_OK) return rc;
+    for (long long q0 = 0; q0 < k; q0 += kw_max) {
+        const int kw = (int)std::min<long long>(kw_max, k - q0);
+        Prob pr;
+        memset(&pr, 0, sizeof(pr));
+        const ProbShape sh{n, kw};
+        carve(&sh, 1, sc, &pr);
+        pr.L = L;
+        pr.V = static_cast<const char *>(V) + (size_t)q0 * ldv * elt;
+        pr.n = n;
+        pr.ld = ld;
+        pr.ldv = ldv;
+        pr.down_mask = down_mask(sigma, sign, q0, kw);
+        pr.info = d_info;
+        long long *trace = nullptr;
         if (allow_trace && trace_on()) {
-            const size_t need = (size_t)2 * nw * nb * kTracePoints;
+            const size_t need = (size_t)2 * kw * nb * kTracePoints;
             if (g_trace_cap < need) {
                 cudaFree(g_trace);
                 g_trace = nullptr;
@@ -267,37 +320,14 @@ static int launch_waves(T *L, long long n, long long ld, const T *V, long long l
             }
             if (g_trace) {
                 cudaMemsetAsync(g_trace, 0, need * sizeof(long long), stream);
-                prm.trace = g_trace;
-                g_trace_tasks = (size_t)2 * nw * nb;
+                trace = g_trace;
+                g_trace_words = need;
             }
         }
-        prm.sync.ticket = sc.misc;
-        prm.sync.abort_flag = sc.misc + 32;
-        prm.sync.status = sc.status;
-        prm.sync.user_info = d_info;
-        prm.sync.epoch = ++*sc.epoch;
-        prm.sync.timeout_ns = timeout_ns();
-        wave_kernel<T><<<nsm * bps, 128, smem, stream>>>(prm);
-        if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
+        rc = launch_wave(dtype, &pr, nullptr, nullptr, 1, kw, nb, sc, LaunchCfg(), trace, stream);
+        if (rc != CHM_OK) return rc;
     }
     return CHM_OK;
-}
-
-template <typename T>
-static int launch_modify(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
-                         const int8_t *sigma, int sign, cudaStream_t stream, long long *d_info)
-{
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
-    const int nb = (int)((n + kW - 1) / kW);
-    const int wmax = (int)std::min<long long>(k, kMaxWaves);
-    std::lock_guard<std::mutex> lock(g_mu);
-    Workspace *w = find_workspace(dev, stream, true);
-    Layout lay0;
-    int rc = alloc_workspace(w, wmax, nb, &lay0);
-    if (rc != CHM_OK) return rc;
-    const Scratch sc{static_cast<char *>(w->buf), w->nb_cap, w->misc, w->status, &w->epoch};
-    return launch_waves<T>(L, n, ld, V, ldv, k, sigma, sign, stream, d_info, sc, kMaxWaves, true);
 }
 
 static int check_args(const void *L, long long n, long long ld, const void *V, long long ldv,
@@ -325,18 +355,22 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
 {
     int rc = check_args(L, n, ld, V, ldv, k, sigma, sign, dtype);
     if (rc != CHM_OK) return rc;
-    if (n == 0 || k == 0) {
-        if (d_info) {
-            info_init_kernel<<<1, 1, 0, stream>>>(d_info);
-            if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
-        }
-        return CHM_OK;
+    if (n == 0 || k == 0) return info_init(d_info, 1, stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
+    const int kw_max = (int)std::min<long long>(k, kMaxWaves);
+    const ProbShape sh{n, kw_max};
+    const ScratchNeed need = scratch_need(&sh, 1);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *w = find_workspace(dev, stream, true);
+    if (w->sc.iflags_cap < need.iflags || w->sc.progress_cap < need.progress || w->sc.data_bytes < need.data ||
+        !w->sc.ctl) {
+        // queued work on this stream may still use the old regions
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return CHM_ERR_CUDA;
+        rc = scratch_alloc(&w->sc, need.iflags, need.progress, need.data);
+        if (rc != CHM_OK) return rc;
     }
-    if (dtype == CHM_F64)
-        return launch_modify<double>(static_cast<double *>(L), n, ld, static_cast<const double *>(V),
-                                     ldv, k, sigma, sign, stream, d_info);
-    return launch_modify<float>(static_cast<float *>(L), n, ld, static_cast<const float *>(V), ldv,
-                                k, sigma, sign, stream, d_info);
+    return enqueue_single(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info, w->sc, kw_max, true);
 }
 
 // ---------------------------------------------------------------- no-allocation variant
@@ -346,23 +380,24 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
 // held until the process exits.  Every call shares it.
 constexpr size_t kNoAllocBytes = (size_t)16 << 20;
 constexpr long long kNoAllocMaxN = 8192;
-constexpr int kNoAllocNbCap = (int)((kNoAllocMaxN + kW - 1) / kW);
-// misc words, then the status word, then the arrays of layout()
-constexpr size_t kNoAllocStatusOff = align_up_const(kMiscInts * sizeof(int), 256);
-constexpr size_t kNoAllocHeader = kNoAllocStatusOff + 256;
+// control words, status word, int flags, progress words, data
+constexpr size_t kNoAllocStatusOff = align256(kCtlInts * sizeof(int));
+constexpr size_t kNoAllocIflagsOff = kNoAllocStatusOff + 256;
+constexpr size_t kNoAllocIflags = 65536;  // ints
+constexpr size_t kNoAllocProgressOff = kNoAllocIflagsOff + kNoAllocIflags * sizeof(int);
+constexpr size_t kNoAllocProgress = 32768;  // words
+constexpr size_t kNoAllocDataOff = kNoAllocProgressOff + kNoAllocProgress * sizeof(long long);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 struct NoAllocState {
     bool ready = false;
-    char *base = nullptr;  // device address of g_noalloc_scratch on this device
-    int epoch = 0;
+    Scratch sc;
 };
 static NoAllocState g_noalloc[64];
 static std::mutex g_noalloc_mu;
 
 // First call on a device (with that device current): look up the array's
-// device address and zero its flag words once; later launches only ever
-// compare flags against larger epochs.
+// device address, zero its control and flag words once and set the epoch.
 static int noalloc_setup(int dev, NoAllocState **out)
 {
     NoAllocState &st = g_noalloc[dev];
@@ -370,24 +405,36 @@ static int noalloc_setup(int dev, NoAllocState **out)
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CHM_ERR_CUDA;
         char *base = static_cast<char *>(p);
-        const Layout lay = layout(kNoAllocNbCap, 1, 1);
-        if (cudaMemset(base, 0, kNoAllocHeader + lay.flags_end) != cudaSuccess) return CHM_ERR_CUDA;
-        if (cudaMemcpy(base + kNoAllocStatusOff, kStatusInit, sizeof(kStatusInit),
-                       cudaMemcpyHostToDevice) != cudaSuccess)
-            return CHM_ERR_CUDA;
+        if (cudaMemset(base, 0, kNoAllocDataOff) != cudaSuccess) return CHM_ERR_CUDA;
+        Scratch sc;
+        sc.ctl = reinterpret_cast<int *>(base);
+        sc.status = reinterpret_cast<long long *>(base + kNoAllocStatusOff);
+        sc.iflags = reinterpret_cast<int *>(base + kNoAllocIflagsOff);
+        sc.iflags_cap = kNoAllocIflags;
+        sc.progress = reinterpret_cast<long long *>(base + kNoAllocProgressOff);
+        sc.progress_cap = kNoAllocProgress;
+        sc.data = base + kNoAllocDataOff;
+        sc.data_bytes = kNoAllocBytes - kNoAllocDataOff;
+        const int rc = ctl_init(sc.ctl, sc.status);
+        if (rc != CHM_OK) return rc;
         if (cudaDeviceSynchronize() != cudaSuccess) return CHM_ERR_CUDA;
-        st.base = base;
+        st.sc = sc;
         st.ready = true;
     }
     *out = &st;
     return CHM_OK;
 }
 
-// Waves per launch that fit the array for nb column blocks (0: none).
-static int noalloc_waves(int nb)
+// Waves per launch that fit the array for order n (0: none).
+static int noalloc_waves(long long n)
 {
-    for (int nw = kMaxWaves; nw >= 1; --nw)
-        if (kNoAllocHeader + layout(kNoAllocNbCap, nw, nb).total <= kNoAllocBytes) return nw;
+    for (int kw = kMaxWaves; kw >= 1; --kw) {
+        const ProbShape sh{n, kw};
+        const ScratchNeed need = scratch_need(&sh, 1);
+        if (need.iflags <= kNoAllocIflags && need.progress <= kNoAllocProgress &&
+            need.data <= kNoAllocBytes - kNoAllocDataOff)
+            return kw;
+    }
     return 0;
 }
 
@@ -398,16 +445,9 @@ static int modify_noalloc(void *L, long long n, long long ld, const void *V, lon
     int rc = check_args(L, n, ld, V, ldv, k, sigma, sign, dtype);
     if (rc != CHM_OK) return rc;
     if (n > kNoAllocMaxN) return CHM_ERR_BUDGET;
-    if (n == 0 || k == 0) {
-        if (d_info) {
-            info_init_kernel<<<1, 1, 0, stream>>>(d_info);
-            if (cudaGetLastError() != cudaSuccess) return CHM_ERR_CUDA;
-        }
-        return CHM_OK;
-    }
-    const int nb = (int)((n + kW - 1) / kW);
-    const int nw_max = noalloc_waves(nb);
-    if (nw_max < 1) return CHM_ERR_BUDGET;
+    if (n == 0 || k == 0) return info_init(d_info, 1, stream);
+    const int kw_max = std::min<int>(noalloc_waves(n), (int)std::min<long long>(k, kMaxWaves));
+    if (kw_max < 1) return CHM_ERR_BUDGET;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
     if (dev < 0 || dev >= 64) return CHM_ERR_ARG;
@@ -415,13 +455,7 @@ static int modify_noalloc(void *L, long long n, long long ld, const void *V, lon
     NoAllocState *st = nullptr;
     rc = noalloc_setup(dev, &st);
     if (rc != CHM_OK) return rc;
-    const Scratch sc{st->base + kNoAllocHeader, kNoAllocNbCap, reinterpret_cast<int *>(st->base),
-                     reinterpret_cast<long long *>(st->base + kNoAllocStatusOff), &st->epoch};
-    if (dtype == CHM_F64)
-        return launch_waves<double>(static_cast<double *>(L), n, ld, static_cast<const double *>(V), ldv,
-                                    k, sigma, sign, stream, d_info, sc, nw_max, false);
-    return launch_waves<float>(static_cast<float *>(L), n, ld, static_cast<const float *>(V), ldv, k,
-                               sigma, sign, stream, d_info, sc, nw_max, false);
+    return enqueue_single(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info, st->sc, kw_max, false);
 }
 
 }  // namespace chm
@@ -465,10 +499,10 @@ int chm_status_sync(chm_stream_t stream, int64_t *info)
     {
         std::lock_guard<std::mutex> lock(chm::g_mu);
         chm::Workspace *w = chm::find_workspace(dev, (cudaStream_t)stream, false);
-        if (w && w->status) {
-            if (cudaMemcpy(h, w->status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (w && w->sc.status) {
+            if (cudaMemcpy(h, w->sc.status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
                 return CHM_ERR_CUDA;
-            if (cudaMemcpy(w->status, chm::kStatusInit, sizeof(chm::kStatusInit),
+            if (cudaMemcpy(w->sc.status, chm::kStatusInit, sizeof(chm::kStatusInit),
                            cudaMemcpyHostToDevice) != cudaSuccess)
                 return CHM_ERR_CUDA;
         }
@@ -495,15 +529,15 @@ const char *chm_status_string(int status)
     }
 }
 
-int chm_version(void) { return 100; }
+int chm_version(void) { return 200; }
 
 int chm_trace_dump(const char *path)
 {
     if (!path) return CHM_ERR_ARG;
     std::lock_guard<std::mutex> lock(chm::g_mu);
-    if (!chm::g_trace || !chm::g_trace_tasks) return CHM_ERR_STATE;
+    if (!chm::g_trace || !chm::g_trace_words) return CHM_ERR_STATE;
     if (cudaDeviceSynchronize() != cudaSuccess) return CHM_ERR_CUDA;
-    std::vector<long long> h(chm::g_trace_tasks * chm::kTracePoints);
+    std::vector<long long> h(chm::g_trace_words);
     if (cudaMemcpy(h.data(), chm::g_trace, h.size() * sizeof(long long), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
         return CHM_ERR_CUDA;

@@ -1,9 +1,12 @@
 // Wave-pipelined rank-k up/downdate kernel (Walder 2010, Algorithm 1, with
-// the CPU/GPU panelling of Sec. 4 replaced by one device-resident launch).
+// the CPU/GPU panelling of Sec. 4 replaced by one device-resident launch
+// that may carry many independent factors).
 //
 // A rank-k modification is k waves: wave q is the rank-1 modification of the
 // factor left by waves < q by column q of V (Sec. 4.1 processes columns in
-// order; any dependency-respecting order gives the same factor).
+// order; any dependency-respecting order gives the same factor).  A launch
+// holds one or more problems (factor, V, signs); a (problem, wave) pair is
+// the unit of scheduling.
 //
 // Per wave, with F the current factor and v the vector (sign sigma):
 //   chain:  p = F^{-T} v (forward substitution), T_0 = 1, T_{i+1} = T_i + sigma p_i^2,
@@ -15,11 +18,12 @@
 // The chain carries no square root or division; the sweep is two FMAs per
 // element and vector.
 //
-// Work split (one launch):
-//   * wave blocks: one thread block per wave, each on an SM of its own
-//     (claimed at start-up through %smid), walks the diagonal blocks in
-//     order with four specialised warps that hand work to each other through
-//     shared memory:
+// Work split.  The SMs of the launch form G groups, each one wave SM plus
+// sweep SMs.  A group takes pairs from a global counter, in pair order, and
+// runs one pair at a time:
+//   * the wave block (the one thread block on the wave SM) walks the pair's
+//     diagonal blocks in order with four specialised warps that hand work to
+//     each other through shared memory:
 //       A  the forward substitution through the diagonal block, with ratio
 //          matrices prepared in advance;
 //       B  the 32-row dot product that carries the previous block's p into
@@ -28,70 +32,114 @@
 //       C  the wave's rotations inside the diagonal block, the next wave's
 //          ratio matrix of that block, and its store;
 //       D  prefetch of the next block's inputs (cp.async).
-//   * sweep workers: every other warp takes tasks (wave q, column block b)
-//     in ticket order t = b * nwaves + q and rotates the block's off-diagonal
-//     tiles with wave q's panels, the update vector held in registers.  It
-//     also publishes what the wave block needs: the carry z for the block,
-//     the carry u_hat at the diagonal, and the next wave's dot-product matrix.
-// Every wait is bounded (%globaltimer); a sweep task only waits on events of
-// tasks with smaller tickets or on wave blocks, which always run.
+//   * every warp of the group's sweep blocks takes tasks (column block b of
+//     the group's current pair) from the group's ticket word and rotates the
+//     block's off-diagonal tiles with the pair's panels, the update vector
+//     held in registers.  It also publishes what the wave block needs: the
+//     carry z for the block, the carry u_hat at the diagonal, and the next
+//     wave's dot-product matrix.
+// A pair waits only on itself and on the previous wave of its problem, which
+// was taken from the counter earlier and is running or done, so the launch
+// always progresses.  Every wait is bounded (%globaltimer).
 //
 // Storage between waves of one launch: the diagonal holds true values, an
-// off-diagonal L_ij is held as S_ij = L_ij / e_i; the last wave of the launch
-// stores true values again.
+// off-diagonal L_ij is held as S_ij = L_ij / e_i; the last wave of a problem
+// in the launch stores true values again.
 #pragma once
 
 #include "chm_device.cuh"
+#include "chm_layout.h"
 
 namespace chm {
 
-constexpr int kMaxSm = 1024;
-constexpr int kTracePoints = 16;
-constexpr int kRoleSweep = 1, kRoleDiag = 2;
-
-// Sweep coefficients of one row of one wave, in the Apply type T.
 template <typename T>
-struct CoefRow {
-    T a, b, e1, pad;
+struct Launch {
+    const Prob *probs;      // device array [nprobs]; null: the one problem is prob0
+    Prob prob0;
+    const int *pair_prob;   // device array [npairs]: problem of each pair; null: all 0
+    int nprobs, npairs, ngroups, nbmax;
+    int *ctl;               // kCtlInts control words
+    long long *status;      // sticky {status, row} of the scratch owner
+    long long *trace;       // optional timestamps, [2][npairs][nbmax][kTracePoints]
+    long long timeout_ns;
 };
 
-// Row data of one wave (double): new row scale and its inverse, new
-// diagonal and its inverse.  The "wave -1" entries (chain0) hold the
-// original factor's data: {1, 1, L_ii, 1 / L_ii}.
-struct ChainRow {
-    double e1, ie1, d1, id1;
-};
-
+// Everything one task needs about its pair.
 template <typename T>
-struct WaveParams {
+struct Wave {
     T *L;
+    const T *V;                 // column q of the problem's V
     long long n, ld;
-    const T *V;
-    long long ldv;
-    int nwaves;                    // waves in this launch (<= kMaxWaves)
-    int nblocks;                   // column blocks of kW columns
-    int fstride;                   // row stride (in blocks) of the flag arrays
-    unsigned long long down_mask;  // bit q set: wave q is a downdate
-    CoefRow<T> *coef;              // [nw][nb][kW]
-    ChainRow *chain;               // [nw][nb][kW]
-    ChainRow *chain0;              // [nb][kW]      original diagonal data
-    double *tend;                  // [nw][nb]      T after the block's last row
-    double *zbuf;                  // [nw][nb][kW]  T u_hat before the block's last tile
-    double *carry;                 // [nw][nb][kW]  u_hat at the diagonal block
-    double *rdiag;                 // [nw][nb][kW][kW] -S_rc e_r / D_r, r < c (diagonal block)
-    double *rtile;                 // [nw][nb][kW][kW] -S_rc e_r (tile: rows of block b, cols of b+1)
-    int *pflag;                    // [nw][fstride] panel published (== epoch)
-    long long *progress;           // [nw][fstride] (epoch << 32) + off-diagonal tiles done
-    int *zflag;                    // [nw][fstride] zbuf ready
-    int *cflag;                    // [nw][fstride] carry ready
-    int *dflag;                    // [nw][fstride] diagonal block done, next wave's rdiag ready
-    int *rflag0;                   // [nb]          wave-0 data of block b ready
-    int *smslot;                   // [kMaxSm]      arrivals per SM (zero at launch)
-    int *smrole;                   // [kMaxSm]      role decided by the SM's first block
-    int *ndiag;                    // wave blocks claimed so far
-    long long *trace;              // optional per-task timestamps
+    int nb, q, pair;
+    bool last, has_next;
+    double sg;                  // +1 update, -1 downdate
+    CoefRow<T> *coef;           // [nb][kW] this wave
+    ChainRow *chain;            // [nb][kW] this wave's output row data
+    const ChainRow *chain_in;   // [nb][kW] row data before this wave
+    ChainRow *chain0;           // [nb][kW] original factor's row data (wave 0 writes)
+    double *tend, *zbuf, *carry, *rdiag, *rtile;
+    double *rdiag_next, *rtile_next;  // the next wave's (null without one)
+    int *pflag, *zflag, *cflag, *dflag, *rflag0;
+    const int *dflag_prev;
+    long long *progress;
+    const long long *progress_prev;
+    long long *trace_sweep, *trace_wave;  // this pair's rows, or null
     SyncArgs sync;
 };
+
+template <typename T>
+__device__ Wave<T> make_wave(const Launch<T> &P, int j)
+{
+    const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
+    const Prob pr = P.probs ? P.probs[i] : P.prob0;
+    Wave<T> w;
+    const int q = j - pr.pair0, nb = pr.nb;
+    const PairRec rc = pair_rec(nb);
+    char *d = pr.data + (size_t)q * rc.bytes;
+    w.L = static_cast<T *>(pr.L);
+    w.V = static_cast<const T *>(pr.V) + (long long)q * pr.ldv;
+    w.n = pr.n;
+    w.ld = pr.ld;
+    w.nb = nb;
+    w.q = q;
+    w.pair = j;
+    w.last = q == pr.k - 1;
+    w.has_next = q + 1 < pr.k;
+    w.sg = ((pr.down_mask >> q) & 1ull) ? -1.0 : 1.0;
+    w.coef = reinterpret_cast<CoefRow<T> *>(d + rc.coef);
+    w.chain = reinterpret_cast<ChainRow *>(d + rc.chain);
+    w.chain0 = reinterpret_cast<ChainRow *>(pr.data + (size_t)pr.k * rc.bytes);
+    w.chain_in = q == 0 ? w.chain0 : reinterpret_cast<const ChainRow *>(d - rc.bytes + rc.chain);
+    w.tend = reinterpret_cast<double *>(d + rc.tend);
+    w.zbuf = reinterpret_cast<double *>(d + rc.zbuf);
+    w.carry = reinterpret_cast<double *>(d + rc.carry);
+    w.rdiag = reinterpret_cast<double *>(d + rc.rdiag);
+    w.rtile = reinterpret_cast<double *>(d + rc.rtile);
+    w.rdiag_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rdiag) : nullptr;
+    w.rtile_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rtile) : nullptr;
+    int *f = pr.iflags + (size_t)q * 4 * nb;
+    w.pflag = f;
+    w.zflag = f + nb;
+    w.cflag = f + 2 * nb;
+    w.dflag = f + 3 * nb;
+    w.dflag_prev = q > 0 ? f - nb : nullptr;
+    w.rflag0 = pr.iflags + (size_t)pr.k * 4 * nb;
+    w.progress = pr.progress + (size_t)q * nb;
+    w.progress_prev = q > 0 ? w.progress - nb : nullptr;
+    if (P.trace) {
+        const size_t row = (size_t)j * P.nbmax * kTracePoints;
+        w.trace_sweep = P.trace + row;
+        w.trace_wave = P.trace + (size_t)P.npairs * P.nbmax * kTracePoints + row;
+    } else {
+        w.trace_sweep = w.trace_wave = nullptr;
+    }
+    w.sync.abort_flag = P.ctl + kCtlAbort;
+    w.sync.status = P.status;
+    w.sync.user_info = pr.info;
+    w.sync.epoch = ld_relaxed_gpu(P.ctl + kCtlEpoch);
+    w.sync.timeout_ns = P.timeout_ns;
+    return w;
+}
 
 // Dynamic shared memory per thread block: four warps' worth.
 constexpr int kWarpSmemBytes = 18432;
@@ -171,7 +219,7 @@ __device__ __forceinline__ double rsqrt_refined(double x)
     return fma(y * e, h, y);
 }
 
-// Wait helpers (one thread).
+// Wait helpers.
 __device__ __forceinline__ bool wait_eq(const SyncArgs &s, const int *p, int want, long long who)
 {
     return bounded_wait(s, [&] { return ld_acquire_gpu(p) == want; }, [] {}, who);
@@ -253,53 +301,52 @@ __device__ __forceinline__ void fetch_bytes(void *dst, const void *src, int byte
 // The same for a shared-memory sequence counter of the wave block.
 #define CHM_SEQ_WAIT(seqp, want) CHM_WARP_WAIT(seq_wait(sy, (seqp), (want), &S.bail, who))
 
-#define CHM_TRACE(pt)                                                                            \
-    do {                                                                                         \
-        if (P.trace && lane == 0) P.trace[(size_t)trace_row * kTracePoints + (pt)] = global_ns(); \
+#define CHM_TRACE(pt)                                                               \
+    do {                                                                            \
+        if (w.trace_sweep && lane == 0)                                             \
+            w.trace_sweep[(size_t)b * kTracePoints + (pt)] = global_ns();           \
     } while (0)
 
 // ---------------------------------------------------------------- sweep task
 
+// Column block b of wave w: rotate its off-diagonal tiles (row blocks p < b)
+// in order, the block's update vector u_hat held in registers (lane = column).
 template <typename T>
-__device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *sm)
+__device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
 {
     T(*tile)[kW + 1] = reinterpret_cast<T(*)[kW + 1]>(sm);
     CoefRow<T> *cf = reinterpret_cast<CoefRow<T> *>(sm + sizeof(T) * kW * (kW + 1) + 64);
     ChainRow *ch = reinterpret_cast<ChainRow *>(cf + kW);
     const int lane = threadIdx.x & 31;
-    const SyncArgs &sy = P.sync;
-    const long long n = P.n, ld = P.ld;
-    const int nw = P.nwaves, nb = P.nblocks;
+    const SyncArgs &sy = w.sync;
+    const long long n = w.n, ld = w.ld;
     const long long c0 = (long long)b * kW;
     const int ncols = (int)min((long long)kW, n - c0);
     const bool active = lane < ncols;
-    const bool last = q == nw - 1;
-    const bool has_next = q + 1 < nw;
     const int epoch = sy.epoch;
     const long long ep64 = (long long)epoch << 32;
-    const long long who = (long long)b * nw + q;
-    const long long *prog_prev = q > 0 ? P.progress + (size_t)(q - 1) * P.fstride + b : nullptr;
-    long long *prog_me = P.progress + (size_t)q * P.fstride + b;
-    const size_t trace_row = (size_t)who;
+    const long long who = b;
+    const long long *prog_prev = w.progress_prev ? w.progress_prev + b : nullptr;
+    long long *prog_me = w.progress + b;
     CHM_TRACE(0);
 
-    T uh = active ? P.V[c0 + lane + (long long)q * P.ldv] : T(0);
+    T uh = active ? w.V[c0 + lane] : T(0);
 
-    if (q == 0) {
+    if (w.q == 0) {
         // Original-factor data of block b for wave 0: the diagonal and its
         // inverse, the diagonal block's chain ratios, and (b >= 1) the dot
         // product matrix of the tile above, taken before any wave rotates it.
         T x[kW];
 #pragma unroll
         for (int c = 0; c < kW; ++c)
-            x[c] = (lane <= c && c < ncols) ? __ldcg(P.L + c0 + lane + (c0 + c) * ld) : T(0);
+            x[c] = (lane <= c && c < ncols) ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
         double dl = 1.0;
 #pragma unroll
         for (int c = 0; c < kW; ++c)
             if (c == lane) dl = (double)x[c];
         const double idl = active ? rcp_refined(dl) : 1.0;
-        if (active) st_chain(P.chain0 + (size_t)b * kW + lane, ChainRow{1.0, 1.0, dl, idl});
-        double *rd = P.rdiag + (size_t)b * kW * kW;  // wave 0
+        if (active) st_chain(w.chain0 + (size_t)b * kW + lane, ChainRow{1.0, 1.0, dl, idl});
+        double *rd = w.rdiag + (size_t)b * kW * kW;
 #pragma unroll
         for (int c = 0; c < kW; ++c) {
             const double v = (lane < c && c < ncols) ? -(double)x[c] * idl : 0.0;
@@ -308,13 +355,13 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
         if (b >= 1) {
             const long long r0 = c0 - kW;
 #pragma unroll
-            for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(P.L + r0 + lane + (c0 + c) * ld) : T(0);
-            double *rt = P.rtile + (size_t)(b - 1) * kW * kW;  // wave 0, tile (b-1, b)
+            for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(w.L + r0 + lane + (c0 + c) * ld) : T(0);
+            double *rt = w.rtile + (size_t)(b - 1) * kW * kW;  // tile (b-1, b)
 #pragma unroll
             for (int c = 0; c < kW; ++c) __stcg(rt + (size_t)lane * kW + c, -(double)x[c]);
         }
         __syncwarp();
-        if (lane == 0) st_release_gpu(P.rflag0 + b, epoch);
+        if (lane == 0) st_release_gpu(w.rflag0 + b, epoch);
     }
 
     for (int p = 0; p < b; ++p) {
@@ -323,16 +370,15 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
         if (prog_prev) CHM_WARP_WAIT(wait_ge(sy, prog_prev, ep64 + p + 1, who));
         T x[kW];
         {
-            const T *src = P.L + (long long)p * kW + lane;
+            const T *src = w.L + (long long)p * kW + lane;
 #pragma unroll
             for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
         }
-        CHM_WARP_WAIT(wait_eq(sy, P.pflag + (size_t)q * P.fstride + p, epoch, who));
+        CHM_WARP_WAIT(wait_eq(sy, w.pflag + p, epoch, who));
         if (lastTile) CHM_TRACE(1);
-        const size_t prow = ((size_t)q * nb + p) * kW;
-        cf[lane] = ld_coef(P.coef + prow + lane);
-        if (lastTile && has_next) ch[lane] = ld_chain(P.chain + prow + lane);
-        const double tnext = (p == b - 2) ? __ldcg(P.tend + (size_t)q * nb + p) : 0.0;
+        cf[lane] = ld_coef(w.coef + (size_t)p * kW + lane);
+        if (lastTile && w.has_next) ch[lane] = ld_chain(w.chain + (size_t)p * kW + lane);
+        const double tnext = (p == b - 2) ? __ldcg(w.tend + p) : 0.0;
 #pragma unroll
         for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         __syncwarp();
@@ -349,26 +395,26 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
         }
         if (p == b - 2) {
             // the wave block's carry for block b: z = T u_hat after rows < (b-1) kW
-            __stcg(P.zbuf + ((size_t)q * nb + b) * kW + lane, active ? tnext * (double)uh : 0.0);
+            __stcg(w.zbuf + (size_t)b * kW + lane, active ? tnext * (double)uh : 0.0);
             __syncwarp();
-            if (lane == 0) st_release_gpu(P.zflag + (size_t)q * P.fstride + b, epoch);
+            if (lane == 0) st_release_gpu(w.zflag + b, epoch);
         }
         if (lastTile) {
             // u_hat entering the diagonal block, for the wave block's rotations there
-            __stcg(P.carry + ((size_t)q * nb + b) * kW + lane, active ? (double)uh : 0.0);
+            __stcg(w.carry + (size_t)b * kW + lane, active ? (double)uh : 0.0);
             __syncwarp();
-            if (lane == 0) st_release_gpu(P.cflag + (size_t)q * P.fstride + b, epoch);
+            if (lane == 0) st_release_gpu(w.cflag + b, epoch);
             CHM_TRACE(2);
         }
-        if (lastTile && has_next) {
+        if (lastTile && w.has_next) {
             // next wave's dot-product matrix for tile (b-1, b): -S' e'
-            double *rt = P.rtile + (((size_t)(q + 1) * nb) + (b - 1)) * kW * kW;
+            double *rt = w.rtile_next + (size_t)(b - 1) * kW * kW;
 #pragma unroll
             for (int r = 0; r < kW; ++r)
                 __stcg(rt + (size_t)r * kW + lane, active ? -(double)S[r] * ch[r].e1 : 0.0);
         }
         if (active) {
-            if (last) {
+            if (w.last) {
 #pragma unroll
                 for (int r = 0; r < kW; ++r) S[r] *= cf[r].e1;
             }
@@ -377,7 +423,7 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
         }
         __syncwarp();
         {
-            T *dst = P.L + (long long)p * kW + lane;
+            T *dst = w.L + (long long)p * kW + lane;
 #pragma unroll
             for (int c = 0; c < kW; ++c)
                 if (c < ncols) __stcg(dst + (c0 + c) * ld, tile[c][lane]);
@@ -390,48 +436,45 @@ __device__ void sweep_task(const WaveParams<T> &P, int q, int b, unsigned char *
 
 // ---------------------------------------------------------------- wave block
 
-#define CHM_WTRACE(b, pt)                                                                      \
-    do {                                                                                       \
-        if (P.trace && lane == 0)                                                              \
-            P.trace[((size_t)P.nwaves * P.nblocks + (size_t)q * P.nblocks + (b)) * kTracePoints + \
-                    (pt)] = global_ns();                                                       \
+#define CHM_WTRACE(b, pt)                                                              \
+    do {                                                                               \
+        if (w.trace_wave && lane == 0)                                                 \
+            w.trace_wave[(size_t)(b) * kTracePoints + (pt)] = global_ns();             \
     } while (0)
 
 // Warp D: the inputs of each block for warps A and B, one block ahead.
 template <typename T>
-__device__ void wave_prefetch(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+__device__ void wave_prefetch(const Wave<T> &w, WaveSmem<T> &S)
 {
     const int lane = threadIdx.x & 31;
-    const SyncArgs &sy = P.sync;
-    const long long n = P.n;
-    const int nb = P.nblocks;
+    const SyncArgs &sy = w.sync;
+    const long long n = w.n;
+    const int nb = w.nb;
     const int epoch = sy.epoch;
     const long long ep64 = (long long)epoch << 32;
-    const long long who = -1 - q;
-    const long long *prog_prev = q > 0 ? P.progress + (size_t)(q - 1) * P.fstride : nullptr;
+    const long long who = -1;
     for (int b = 0; b < nb; ++b) {
         const int s = b & 1;
         const long long c0 = (long long)b * kW;
         // the slot's previous block (b - 2) must be finished by warps A, B, C
         if (b >= 2) CHM_SEQ_WAIT(&S.fseq, b - 1);
         CHM_WTRACE(b, 0);
-        if (q == 0) {
-            CHM_WARP_WAIT(wait_eq(sy, P.rflag0 + b, epoch, who));
+        if (w.q == 0) {
+            CHM_WARP_WAIT(wait_eq(sy, w.rflag0 + b, epoch, who));
         } else {
-            CHM_WARP_WAIT(wait_eq(sy, P.dflag + (size_t)(q - 1) * P.fstride + b, epoch, who) &&
-                          (b == 0 || wait_ge(sy, prog_prev + b, ep64 + b, who)));
+            CHM_WARP_WAIT(wait_eq(sy, w.dflag_prev + b, epoch, who) &&
+                          (b == 0 || wait_ge(sy, w.progress_prev + b, ep64 + b, who)));
         }
         CHM_WTRACE(b, 1);
-        if (b >= 2) CHM_WARP_WAIT(wait_eq(sy, P.zflag + (size_t)q * P.fstride + b, epoch, who));
+        if (b >= 2) CHM_WARP_WAIT(wait_eq(sy, w.zflag + b, epoch, who));
         CHM_WTRACE(b, 2);
-        fetch_bytes(&S.R[s][0][0], P.rdiag + ((size_t)q * nb + b) * kW * kW, kW * kW * 8, lane);
-        if (b >= 1) fetch_bytes(&S.Rt[s][0][0], P.rtile + ((size_t)q * nb + (b - 1)) * kW * kW, kW * kW * 8, lane);
-        fetch_bytes(&S.rowd[s][0], (q == 0 ? P.chain0 + (size_t)b * kW : P.chain + ((size_t)(q - 1) * nb + b) * kW),
-                    kW * (int)sizeof(ChainRow), lane);
+        fetch_bytes(&S.R[s][0][0], w.rdiag + (size_t)b * kW * kW, kW * kW * 8, lane);
+        if (b >= 1) fetch_bytes(&S.Rt[s][0][0], w.rtile + (size_t)(b - 1) * kW * kW, kW * kW * 8, lane);
+        fetch_bytes(&S.rowd[s][0], w.chain_in + (size_t)b * kW, kW * (int)sizeof(ChainRow), lane);
         if (b >= 2) {
-            fetch_bytes(&S.zpart[s][0], P.zbuf + ((size_t)q * nb + b) * kW, kW * 8, lane);
+            fetch_bytes(&S.zpart[s][0], w.zbuf + (size_t)b * kW, kW * 8, lane);
         } else {
-            S.zpart[s][lane] = (c0 + lane < n) ? (double)P.V[c0 + lane + (long long)q * P.ldv] : 0.0;
+            S.zpart[s][lane] = (c0 + lane < n) ? (double)w.V[c0 + lane] : 0.0;
         }
         cp_async_commit();
         cp_async_wait();
@@ -443,13 +486,13 @@ __device__ void wave_prefetch(const WaveParams<T> &P, int q, WaveSmem<T> &S)
 
 // Warp A: the forward substitution through each diagonal block.
 template <typename T>
-__device__ void wave_chain(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+__device__ void wave_chain(const Wave<T> &w, WaveSmem<T> &S)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    const SyncArgs &sy = P.sync;
-    const long long who = -1 - q;
-    for (int b = 0; b < P.nblocks; ++b) {
+    const SyncArgs &sy = w.sync;
+    const long long who = -1;
+    for (int b = 0; b < w.nb; ++b) {
         CHM_SEQ_WAIT(&S.zseq, b + 1);
         CHM_WTRACE(b, 8);
         double(*R)[kW] = S.R[b & 1];
@@ -465,21 +508,20 @@ __device__ void wave_chain(const WaveParams<T> &P, int q, WaveSmem<T> &S)
         if (lane == 0) seq_post(&S.cseq, b + 1);
     }
 }
-
 // Warp B: the dot product into each block, then p, T and the coefficients
 // of the block just chained, and the panel's publication.  The next chain
 // is started before a panel is published whenever its inputs are already in.
 template <typename T>
-__device__ void wave_coef(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+__device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    const SyncArgs &sy = P.sync;
-    const long long n = P.n;
-    const int nb = P.nblocks;
+    const SyncArgs &sy = w.sync;
+    const long long n = w.n;
+    const int nb = w.nb;
     const int epoch = sy.epoch;
-    const double sgd = ((P.down_mask >> q) & 1ull) ? -1.0 : 1.0;
-    const long long who = -1 - q;
+    const double sgd = w.sg;
+    const long long who = -1;
     double pprev = 0.0;  // p of the block last chained, row `lane`
     double Tend = 1.0, iTend = 1.0;
     int pending = -1;    // block chained (or being chained) but not yet published
@@ -542,13 +584,13 @@ __device__ void wave_coef(const WaveParams<T> &P, int q, WaveSmem<T> &S)
         __syncwarp();
         if (lane == 0) seq_post(&S.bseq, b + 1);
         if (active) {
-            const size_t prow = ((size_t)q * nb + b) * kW + lane;
-            st_coef(P.coef + prow, cr);
-            st_chain(P.chain + prow, nrow);
+            const size_t prow = (size_t)b * kW + lane;
+            st_coef(w.coef + prow, cr);
+            st_chain(w.chain + prow, nrow);
         }
-        if (lane == 0) __stcg(P.tend + (size_t)q * nb + b, Tlast);
+        if (lane == 0) __stcg(w.tend + b, Tlast);
         __syncwarp();
-        if (lane == 0) st_release_gpu(P.pflag + (size_t)q * P.fstride + b, epoch);
+        if (lane == 0) st_release_gpu(w.pflag + b, epoch);
         CHM_WTRACE(b, 5);
         Tend = Tlast;
         iTend = __shfl_sync(FULL, iTn, rows - 1);
@@ -583,16 +625,14 @@ __device__ void wave_coef(const WaveParams<T> &P, int q, WaveSmem<T> &S)
 
 // Warp C: the wave's rotations inside each diagonal block.
 template <typename T>
-__device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
+__device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
 {
     const int lane = threadIdx.x & 31;
-    const SyncArgs &sy = P.sync;
-    const long long n = P.n, ld = P.ld;
-    const int nw = P.nwaves, nb = P.nblocks;
+    const SyncArgs &sy = w.sync;
+    const long long n = w.n, ld = w.ld;
+    const int nb = w.nb;
     const int epoch = sy.epoch;
-    const bool last = q == nw - 1;
-    const bool has_next = q + 1 < nw;
-    const long long who = -1 - q;
+    const long long who = -1;
     for (int b = 0; b < nb; ++b) {
         const int s = b & 1;
         const long long c0 = (long long)b * kW;
@@ -601,10 +641,10 @@ __device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
         // u_hat entering the block (from the sweep of its last off-diagonal tile)
         T uh = T(0);
         if (b == 0) {
-            uh = active ? P.V[c0 + lane + (long long)q * P.ldv] : T(0);
+            uh = active ? w.V[c0 + lane] : T(0);
         } else {
-            CHM_WARP_WAIT(wait_eq(sy, P.cflag + (size_t)q * P.fstride + b, epoch, who));
-            uh = (T)__ldcg(P.carry + ((size_t)q * nb + b) * kW + lane);
+            CHM_WARP_WAIT(wait_eq(sy, w.cflag + b, epoch, who));
+            uh = (T)__ldcg(w.carry + (size_t)b * kW + lane);
         }
         CHM_WTRACE(b, 10);
         // the tile as the previous wave left it: warp D acquired that wave's
@@ -614,7 +654,7 @@ __device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
             T x[kW];
 #pragma unroll
             for (int c = 0; c < kW; ++c)
-                x[c] = (lane <= c && c < ncols) ? __ldcg(P.L + c0 + lane + (c0 + c) * ld) : T(0);
+                x[c] = (lane <= c && c < ncols) ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
 #pragma unroll
             for (int c = 0; c < kW; ++c) S.DT[c][lane] = x[c];
         }
@@ -632,9 +672,9 @@ __device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
                 uh = fma(-c.b, Sv[r], uh);
             }
         }
-        if (has_next) {
+        if (w.has_next) {
             // next wave's chain ratios for this block: -S'_rc e'_r / D'_r (r < c)
-            double *rd = P.rdiag + (((size_t)(q + 1) * nb) + b) * kW * kW;
+            double *rd = w.rdiag_next + (size_t)b * kW * kW;
 #pragma unroll
             for (int r = 0; r < kW; ++r) {
                 const ChainRow cn = S.cnew[s][r];
@@ -642,7 +682,7 @@ __device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
                 __stcg(rd + (size_t)r * kW + lane, v);
             }
         }
-        if (last) {
+        if (w.last) {
 #pragma unroll
             for (int r = 0; r < kW; ++r)
                 if (r < lane) Sv[r] *= S.cf[s][r].e1;
@@ -654,9 +694,9 @@ __device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < kW; ++c)
-            if (lane <= c && c < ncols) __stcg(P.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
+            if (lane <= c && c < ncols) __stcg(w.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
         __syncwarp();
-        if (lane == 0) st_release_gpu(P.dflag + (size_t)q * P.fstride + b, epoch);
+        if (lane == 0) st_release_gpu(w.dflag + b, epoch);
         CHM_WTRACE(b, 13);
         if (lane == 0) seq_post(&S.fseq, b + 1);
     }
@@ -664,60 +704,180 @@ __device__ void wave_diag(const WaveParams<T> &P, int q, WaveSmem<T> &S)
 
 // ---------------------------------------------------------------- entry
 
+// Roles, decided per SM by the first block that starts there.
+constexpr int kRoleIdle = 0, kRoleWave = 1, kRoleSweep = 2;
+__device__ __forceinline__ int role_code(int role, int group) { return role | (group << 4); }
+
+// Column blocks of pair j that carry sweep tasks: [first, nb).
 template <typename T>
-__global__ void __launch_bounds__(128, 3) wave_kernel(WaveParams<T> P)
+__device__ __forceinline__ void task_range(const Launch<T> &P, int j, int *first, int *nb)
+{
+    const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
+    const Prob *pr = P.probs ? P.probs + i : &P.prob0;
+    *first = j > pr->pair0 ? 1 : 0;  // block 0 of a later wave has no off-diagonal tile
+    *nb = pr->nb;
+}
+
+// Take one sweep task: the warp's own group first, then the other groups'
+// current pairs.  Each ticket word is read before it is incremented, so a
+// group whose pair has no task left is not counted up.  Returns the pair
+// (or -1) and the column block; all lanes get the same answer.
+template <typename T>
+__device__ __forceinline__ int take_task(const Launch<T> &P, int group, int *block)
+{
+    unsigned long long *gts = reinterpret_cast<unsigned long long *>(P.ctl + kCtlGroupTicket);
+    const int lane = threadIdx.x & 31;
+    int j = -1, b = -1;
+    for (int d = 0; d < P.ngroups && j < 0; ++d) {
+        int g = group + d;
+        if (g >= P.ngroups) g -= P.ngroups;
+        const unsigned long long v = (unsigned long long)ld_relaxed_gpu(reinterpret_cast<const long long *>(gts + g));
+        const unsigned hi = (unsigned)(v >> 32);
+        if (hi == 0u || hi == kGroupDone) continue;
+        int first = 0, nb = 0;
+        task_range(P, (int)hi - 1, &first, &nb);
+        if ((long long)(unsigned)v + first >= nb) continue;
+        unsigned long long v2 = 0;
+        if (lane == 0) v2 = atomicAdd(gts + g, 1ull);
+        v2 = __shfl_sync(0xffffffffu, v2, 0);
+        if ((unsigned)(v2 >> 32) == hi && (long long)(unsigned)v2 + first < nb) {
+            j = (int)hi - 1;
+            b = (int)(unsigned)v2 + first;
+        }
+    }
+    *block = b;
+    return j;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
 {
     extern __shared__ __align__(16) unsigned char chm_smem[];
-    __shared__ int s_role, s_didx;
+    __shared__ int s_role, s_pair, s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const SyncArgs &sy = P.sync;
+    int *ctl = P.ctl;
+    SyncArgs sy;  // launch-level waits
+    sy.abort_flag = ctl + kCtlAbort;
+    sy.status = P.status;
+    sy.user_info = nullptr;
+    sy.epoch = 0;
+    sy.timeout_ns = P.timeout_ns;
+
     if (threadIdx.x == 0) {
+        atomicAdd(ctl + kCtlStarted, 1);
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        int role = kRoleSweep, didx = -1;
+        int code = role_code(kRoleIdle, 0);
         if (smid < (unsigned)kMaxSm) {
-            if (atomicAdd(P.smslot + smid, 1) == 0) {
-                const int d = atomicAdd(P.ndiag, 1);
-                if (d < P.nwaves) {
-                    role = kRoleDiag;
-                    didx = d;
-                }
-                st_release_gpu(P.smrole + smid, role);
+            if (atomicAdd(ctl + kCtlSmSlot + smid, 1) == 0) {
+                // the SM's first block: rank the SM; the first G SMs carry the
+                // groups' wave blocks, the others are dealt to the groups
+                const int r = atomicAdd(ctl + kCtlSmRank, 1);
+                const int G = P.ngroups;
+                code = r < G ? role_code(kRoleWave, r) : role_code(kRoleSweep, (r - G) % G);
+                if (r >= G) atomicAdd(ctl + kCtlGroupSweepers + (r - G) % G, 1);
+                st_release_gpu(ctl + kCtlSmRole + smid, code + 1);
             } else {
-                const int *pr = P.smrole + smid;
+                const int *pr = ctl + kCtlSmRole + smid;
                 int seen = 0;
                 bounded_wait(
                     sy, [&] { return (seen = ld_relaxed_gpu(pr)) != 0; },
                     [&] { (void)ld_acquire_gpu(pr); }, -1000);
-                role = seen == kRoleDiag ? 0 : kRoleSweep;  // a wave block's SM runs nothing else
+                code = seen - 1;
+                // a wave SM runs its wave block alone
+                if (seen == 0 || (code & 15) == kRoleWave) code = role_code(kRoleIdle, 0);
             }
         }
-        s_role = role;
-        s_didx = didx;
+        s_role = code;
     }
     __syncthreads();
-    const int role = s_role;
-    if (role == 0) return;
-    if (role == kRoleDiag) {
+    const int role = s_role & 15, group = s_role >> 4;
+    unsigned long long *gt = reinterpret_cast<unsigned long long *>(ctl + kCtlGroupTicket) + group;
+
+    if (role == kRoleWave) {
         WaveSmem<T> &S = *reinterpret_cast<WaveSmem<T> *>(chm_smem);
-        if (threadIdx.x == 0) S.dseq = S.zseq = S.cseq = S.bseq = S.fseq = S.bail = 0;
+        if (threadIdx.x == 0) {
+            // every block of the launch is resident before pairs are taken,
+            // so that the group's sweep SMs are all known
+            const bool all = bounded_wait(
+                sy, [&] { return ld_relaxed_gpu(ctl + kCtlStarted) >= (int)gridDim.x; },
+                [] { __threadfence(); }, -3);
+            s_pair = (all && ld_relaxed_gpu(ctl + kCtlGroupSweepers + group) > 0) ? 0 : -1;
+        }
         __syncthreads();
-        const int q = s_didx;
-        if (warp == 0) wave_chain<T>(P, q, S);
-        else if (warp == 1) wave_coef<T>(P, q, S);
-        else if (warp == 2) wave_diag<T>(P, q, S);
-        else wave_prefetch<T>(P, q, S);
-        return;
+        const bool can_run = s_pair == 0;
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int j = -1;
+                if (can_run && !aborted(sy)) j = atomicAdd(ctl + kCtlPairNext, 1);
+                if (j < 0 || j >= P.npairs) {
+                    j = -1;
+                    __threadfence();
+                    atomicExch(gt, (unsigned long long)kGroupDone << 32);
+                } else {
+                    S.dseq = S.zseq = S.cseq = S.bseq = S.fseq = S.bail = 0;
+                    __threadfence();
+                    atomicExch(gt, (unsigned long long)(j + 1) << 32);
+                }
+                s_pair = j;
+            }
+            __syncthreads();
+            const int j = s_pair;
+            if (j < 0) break;
+            const Wave<T> w = make_wave(P, j);
+            if (warp == 0) wave_chain<T>(w, S);
+            else if (warp == 1) wave_coef<T>(w, S);
+            else if (warp == 2) wave_diag<T>(w, S);
+            else wave_prefetch<T>(w, S);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(ctl + kCtlPairsDone, 1);
+            }
+        }
+    } else if (role == kRoleSweep) {
+        unsigned char *sm = chm_smem + (size_t)warp * kWarpSmemBytes;
+        long long idle_since = -1;
+        for (;;) {
+            if (aborted(sy)) break;
+            int b = -1;
+            const int j = take_task(P, group, &b);
+            if (j >= 0) {
+                sweep_task<T>(make_wave(P, j), b, sm);
+                idle_since = -1;
+                continue;
+            }
+            // nothing to take: stop once every pair is done, else look again
+            if (ld_relaxed_gpu(ctl + kCtlPairsDone) >= P.npairs) break;
+            const long long now = global_ns();
+            if (idle_since < 0) {
+                idle_since = now;
+            } else if (now - idle_since > P.timeout_ns) {
+                if (lane == 0) record_error(sy, kStatusTimeout, -2);
+                break;
+            }
+            __nanosleep(500);
+        }
     }
-    unsigned char *sm = chm_smem + (size_t)warp * kWarpSmemBytes;
-    const int ntasks = P.nwaves * P.nblocks;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(sy.ticket, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntasks || aborted(sy)) return;
-        sweep_task<T>(P, t % P.nwaves, t / P.nwaves, sm);
-        if (aborted(sy)) return;
+
+    // The last block to finish zeroes the control words for the next launch
+    // and advances the epoch.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ctl + kCtlExited, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int i = threadIdx.x; i < kCtlInts; i += blockDim.x)
+            if (i != kCtlEpoch) ctl[i] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            ctl[kCtlEpoch] = ctl[kCtlEpoch] + 1;
+            __threadfence();
+        }
     }
 }
 
