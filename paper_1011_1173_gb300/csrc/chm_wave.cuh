@@ -141,25 +141,42 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     return w;
 }
 
-// Dynamic shared memory per thread block: four warps' worth.
-constexpr int kWarpSmemBytes = 18432;
-constexpr int kBlockSmemBytes = 4 * kWarpSmemBytes;
+// Input slots of the wave block: block b's inputs live in slot b % kSlots,
+// so the prefetch may run up to kSlots - 1 blocks ahead of the finish.
+constexpr int kSlots = 3;
 
 // Shared memory of a wave block.
 template <typename T>
 struct WaveSmem {
-    double R[2][kW][kW];   // chain ratios of the block, [r][c]
-    double Rt[2][kW][kW];  // dot-product matrix of the tile above, [r][c]
-    ChainRow rowd[2][kW];  // row data of the block before this wave
-    double zpart[2][kW];   // carry z before the tile above
-    double zbox[kW];       // B -> A: z entering the chain
-    double cbox[kW];       // A -> B: z after the chain
-    CoefRow<T> cf[2][kW];  // B -> C: sweep coefficients of the block
-    ChainRow cnew[2][kW];  // B -> C: row data after this wave
-    T DT[kW][kW + 1];      // C: the diagonal tile, [c][r]
-    int dseq, zseq, cseq, bseq, fseq, bail;
+    double R[kSlots][kW][kW];   // chain ratios of the block, [r][c]
+    double Rt[kSlots][kW][kW];  // dot-product matrix of the tile above, [r][c]
+    ChainRow rowd[kSlots][kW];  // row data of the block before this wave
+    double zpart[kSlots][kW];   // carry z before the tile above
+    double zbox[kW];            // B -> A: z entering the chain
+    double cbox[kW];            // A -> B: z after the chain
+    CoefRow<T> cf[kSlots][kW];  // B -> C: sweep coefficients of the block
+    ChainRow cnew[kSlots][kW];  // B -> C, D: row data after this wave
+    T DT[kW][kW + 1];           // C -> D: the rotated diagonal tile, [c][r]
+    double F[kW];               // D: -e'_r / D'_r of the block being finished
+    int dseq;                   // D: inputs of blocks < dseq fetched
+    int zseq;                   // B: chain inputs of blocks < zseq formed
+    int cseq;                   // A: blocks < cseq chained
+    int bseq;                   // B: coefficients of blocks < bseq formed
+    int cdone;                  // C: blocks < cdone rotated (in DT)
+    int fseq;                   // D: blocks < fseq finished (stored, released)
+    int bail;
 };
-static_assert(sizeof(WaveSmem<double>) <= kBlockSmemBytes, "wave block shared memory");
+
+// Dynamic shared memory per thread block: a sweep warp's tile and panel
+// rows, four warps per block, or a wave block's WaveSmem.
+constexpr int kWarpSmemBytes = 10752;
+constexpr int kBlockSmemBytes =
+    (int)(((sizeof(WaveSmem<double>) > 4 * (size_t)kWarpSmemBytes ? sizeof(WaveSmem<double>)
+                                                                   : 4 * (size_t)kWarpSmemBytes) +
+           1023) & ~(size_t)1023);
+static_assert(sizeof(double) * kW * (kW + 1) + 64 + kW * sizeof(CoefRow<double>) + kW * sizeof(ChainRow) <=
+                  (size_t)kWarpSmemBytes,
+              "sweep warp shared memory");
 
 // ---------------------------------------------------------------- small helpers
 
@@ -442,45 +459,108 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
             w.trace_wave[(size_t)(b) * kTracePoints + (pt)] = global_ns();             \
     } while (0)
 
-// Warp D: the inputs of each block for warps A and B, one block ahead.
+// Warp D: the wave block's memory traffic.  It fetches each block's inputs
+// for warps A, B and C into slot b % kSlots (up to kSlots - 1 blocks ahead)
+// and finishes each block warp C has rotated: the next wave's chain ratios,
+// the store of the diagonal tile and the release of the block to the next
+// wave.  Neither job blocks the other: the warp polls both.
 template <typename T>
-__device__ void wave_prefetch(const Wave<T> &w, WaveSmem<T> &S)
+__device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
     const SyncArgs &sy = w.sync;
-    const long long n = w.n;
+    const long long n = w.n, ld = w.ld;
     const int nb = w.nb;
     const int epoch = sy.epoch;
     const long long ep64 = (long long)epoch << 32;
-    const long long who = -1;
-    for (int b = 0; b < nb; ++b) {
-        const int s = b & 1;
-        const long long c0 = (long long)b * kW;
-        // the slot's previous block (b - 2) must be finished by warps A, B, C
-        if (b >= 2) CHM_SEQ_WAIT(&S.fseq, b - 1);
-        CHM_WTRACE(b, 0);
-        if (w.q == 0) {
-            CHM_WARP_WAIT(wait_eq(sy, w.rflag0 + b, epoch, who));
-        } else {
-            CHM_WARP_WAIT(wait_eq(sy, w.dflag_prev + b, epoch, who) &&
-                          (b == 0 || wait_ge(sy, w.progress_prev + b, ep64 + b, who)));
+    volatile int *cdone = &S.cdone;
+    int next_fetch = 0, next_fin = 0;
+    long long idle_since = -1;
+    while (next_fin < nb) {
+        bool progressed = false;
+        // finish block next_fin once warp C has rotated it
+        if (next_fin < next_fetch && __shfl_sync(FULL, *cdone > next_fin ? 1 : 0, 0)) {
+            __threadfence_block();
+            const int b = next_fin, s = b % kSlots;
+            const long long c0 = (long long)b * kW;
+            const int ncols = (int)min((long long)kW, n - c0);
+            const bool active = lane < ncols;
+            if (w.has_next) {
+                // next wave's chain ratios for this block: S'_rc (-e'_r / D'_r), r < c
+                const ChainRow cn = S.cnew[s][lane];
+                S.F[lane] = -cn.e1 * cn.id1;
+                __syncwarp();
+                double *rd = w.rdiag_next + (size_t)b * kW * kW;
+#pragma unroll
+                for (int r = 0; r < kW; ++r) {
+                    const double v = (r < lane && active) ? (double)S.DT[lane][r] * S.F[r] : 0.0;
+                    __stcg(rd + (size_t)r * kW + lane, v);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kW; ++c)
+                if (lane <= c && c < ncols) __stcg(w.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
+            __syncwarp();
+            if (lane == 0) st_release_gpu(w.dflag + b, epoch);
+            CHM_WTRACE(b, 13);
+            if (lane == 0) seq_post(&S.fseq, b + 1);
+            ++next_fin;
+            progressed = true;
         }
-        CHM_WTRACE(b, 1);
-        if (b >= 2) CHM_WARP_WAIT(wait_eq(sy, w.zflag + b, epoch, who));
-        CHM_WTRACE(b, 2);
-        fetch_bytes(&S.R[s][0][0], w.rdiag + (size_t)b * kW * kW, kW * kW * 8, lane);
-        if (b >= 1) fetch_bytes(&S.Rt[s][0][0], w.rtile + (size_t)(b - 1) * kW * kW, kW * kW * 8, lane);
-        fetch_bytes(&S.rowd[s][0], w.chain_in + (size_t)b * kW, kW * (int)sizeof(ChainRow), lane);
-        if (b >= 2) {
-            fetch_bytes(&S.zpart[s][0], w.zbuf + (size_t)b * kW, kW * 8, lane);
-        } else {
-            S.zpart[s][lane] = (c0 + lane < n) ? (double)w.V[c0 + lane] : 0.0;
+        // fetch the inputs of block next_fetch once they are published and its slot is free
+        if (next_fetch < nb && next_fetch - next_fin < kSlots) {
+            const int b = next_fetch, s = b % kSlots;
+            int ready = 1;
+            if (lane == 0) {
+                if (w.q == 0) {
+                    ready = ld_relaxed_gpu(w.rflag0 + b) == epoch;
+                } else {
+                    ready = ld_relaxed_gpu(w.dflag_prev + b) == epoch &&
+                            (b == 0 || ld_relaxed_gpu(w.progress_prev + b) >= ep64 + b);
+                }
+                if (ready && b >= 2) ready = ld_relaxed_gpu(w.zflag + b) == epoch;
+                if (ready) __threadfence();  // acquire what those flags released
+            }
+            if (__shfl_sync(FULL, ready, 0)) {
+                __syncwarp();
+                CHM_WTRACE(b, 2);
+                const long long c0 = (long long)b * kW;
+                fetch_bytes(&S.R[s][0][0], w.rdiag + (size_t)b * kW * kW, kW * kW * 8, lane);
+                if (b >= 1) fetch_bytes(&S.Rt[s][0][0], w.rtile + (size_t)(b - 1) * kW * kW, kW * kW * 8, lane);
+                fetch_bytes(&S.rowd[s][0], w.chain_in + (size_t)b * kW, kW * (int)sizeof(ChainRow), lane);
+                if (b >= 2) {
+                    fetch_bytes(&S.zpart[s][0], w.zbuf + (size_t)b * kW, kW * 8, lane);
+                } else {
+                    S.zpart[s][lane] = (c0 + lane < n) ? (double)w.V[c0 + lane] : 0.0;
+                }
+                cp_async_commit();
+                cp_async_wait();
+                __syncwarp();
+                CHM_WTRACE(b, 3);
+                if (lane == 0) seq_post(&S.dseq, b + 1);
+                ++next_fetch;
+                progressed = true;
+            }
         }
-        cp_async_commit();
-        cp_async_wait();
-        __syncwarp();
-        CHM_WTRACE(b, 3);
-        if (lane == 0) seq_post(&S.dseq, b + 1);
+        if (progressed) {
+            idle_since = -1;
+            continue;
+        }
+        // neither: stop on an abort or a stopped warp, else wait a little (bounded)
+        const int stop = __shfl_sync(FULL, (*reinterpret_cast<volatile int *>(&S.bail) || aborted(sy)) ? 1 : 0, 0);
+        if (stop) return;
+        const long long now = global_ns();
+        if (idle_since < 0) {
+            idle_since = now;
+        } else if (now - idle_since > sy.timeout_ns) {
+            if (lane == 0) {
+                record_error(sy, kStatusTimeout, -4);
+                S.bail = 1;
+            }
+            return;
+        }
+        __nanosleep(32);
     }
 }
 
@@ -495,7 +575,7 @@ __device__ void wave_chain(const Wave<T> &w, WaveSmem<T> &S)
     for (int b = 0; b < w.nb; ++b) {
         CHM_SEQ_WAIT(&S.zseq, b + 1);
         CHM_WTRACE(b, 8);
-        double(*R)[kW] = S.R[b & 1];
+        double(*R)[kW] = S.R[b % kSlots];
         double z = S.zbox[lane];
 #pragma unroll
         for (int r = 0; r < kW; ++r) {
@@ -535,7 +615,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
     };
     auto form_input = [&](int b) {
         // z entering block b's chain: the carry plus the rows of the block above
-        const int s = b & 1;
+        const int s = b % kSlots;
         double z = S.zpart[s][lane];
         if (b >= 1) {
             double z1 = 0.0, z2 = 0.0, z3 = 0.0;
@@ -555,7 +635,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
     };
     auto publish = [&](int b, double p) {
         // T and the coefficients of block b (already chained), given its p
-        const int s = b & 1;
+        const int s = b % kSlots;
         const long long c0 = (long long)b * kW;
         const int rows = (int)min((long long)kW, n - c0);
         const bool active = lane < rows;
@@ -609,7 +689,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
         pending = -1;
         {
             const long long c0 = (long long)done * kW;
-            pprev = (c0 + lane < n) ? S.cbox[lane] * S.rowd[done & 1][lane].id1 : 0.0;
+            pprev = (c0 + lane < n) ? S.cbox[lane] * S.rowd[done % kSlots][lane].id1 : 0.0;
         }
         if (next < nb) {
             const int ready = __shfl_sync(FULL, *reinterpret_cast<volatile int *>(&S.dseq) >= next + 1 ? 1 : 0, 0);
@@ -623,7 +703,8 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
     }
 }
 
-// Warp C: the wave's rotations inside each diagonal block.
+// Warp C: the wave's rotations inside each diagonal block; warp D stores
+// the result.
 template <typename T>
 __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
 {
@@ -634,7 +715,7 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
     const int epoch = sy.epoch;
     const long long who = -1;
     for (int b = 0; b < nb; ++b) {
-        const int s = b & 1;
+        const int s = b % kSlots;
         const long long c0 = (long long)b * kW;
         const int ncols = (int)min((long long)kW, n - c0);
         const bool active = lane < ncols;
@@ -650,36 +731,27 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
         // the tile as the previous wave left it: warp D acquired that wave's
         // release of this block before announcing the block's inputs
         CHM_SEQ_WAIT(&S.dseq, b + 1);
-        {
-            T x[kW];
+        T x[kW];
 #pragma unroll
-            for (int c = 0; c < kW; ++c)
-                x[c] = (lane <= c && c < ncols) ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
+        for (int c = 0; c < kW; ++c)
+            x[c] = (lane <= c && c < ncols) ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
+        // the tile buffer is free once warp D has finished the previous block
+        CHM_SEQ_WAIT(&S.fseq, b);
 #pragma unroll
-            for (int c = 0; c < kW; ++c) S.DT[c][lane] = x[c];
-        }
+        for (int c = 0; c < kW; ++c) S.DT[c][lane] = x[c];
+        __syncwarp();
         CHM_WTRACE(b, 11);
-        CHM_SEQ_WAIT(&S.bseq, b + 1);
-        CHM_WTRACE(b, 12);
         T Sv[kW];
 #pragma unroll
         for (int r = 0; r < kW; ++r) Sv[r] = S.DT[lane][r];
+        CHM_SEQ_WAIT(&S.bseq, b + 1);
+        CHM_WTRACE(b, 12);
 #pragma unroll
         for (int r = 0; r < kW; ++r) {
             if (r < lane) {
                 const CoefRow<T> c = S.cf[s][r];
                 Sv[r] = fma(c.a, uh, Sv[r]);
                 uh = fma(-c.b, Sv[r], uh);
-            }
-        }
-        if (w.has_next) {
-            // next wave's chain ratios for this block: -S'_rc e'_r / D'_r (r < c)
-            double *rd = w.rdiag_next + (size_t)b * kW * kW;
-#pragma unroll
-            for (int r = 0; r < kW; ++r) {
-                const ChainRow cn = S.cnew[s][r];
-                const double v = (r < lane && active) ? -(double)Sv[r] * cn.e1 * cn.id1 : 0.0;
-                __stcg(rd + (size_t)r * kW + lane, v);
             }
         }
         if (w.last) {
@@ -692,13 +764,7 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
             if (r < lane) S.DT[lane][r] = Sv[r];
         if (active) S.DT[lane][lane] = (T)S.cnew[s][lane].d1;
         __syncwarp();
-#pragma unroll
-        for (int c = 0; c < kW; ++c)
-            if (lane <= c && c < ncols) __stcg(w.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
-        __syncwarp();
-        if (lane == 0) st_release_gpu(w.dflag + b, epoch);
-        CHM_WTRACE(b, 13);
-        if (lane == 0) seq_post(&S.fseq, b + 1);
+        if (lane == 0) seq_post(&S.cdone, b + 1);
     }
 }
 
@@ -815,7 +881,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
                     __threadfence();
                     atomicExch(gt, (unsigned long long)kGroupDone << 32);
                 } else {
-                    S.dseq = S.zseq = S.cseq = S.bseq = S.fseq = S.bail = 0;
+                    S.dseq = S.zseq = S.cseq = S.bseq = S.cdone = S.fseq = S.bail = 0;
                     __threadfence();
                     atomicExch(gt, (unsigned long long)(j + 1) << 32);
                 }
@@ -828,7 +894,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             if (warp == 0) wave_chain<T>(w, S);
             else if (warp == 1) wave_coef<T>(w, S);
             else if (warp == 2) wave_diag<T>(w, S);
-            else wave_prefetch<T>(w, S);
+            else wave_io<T>(w, S);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
