@@ -142,6 +142,63 @@ int chm_modify_noalloc(void *L, int64_t n, int64_t ld, const void *V, int64_t ld
                        int64_t *d_info);
 
 /*
+ * Batched up/downdate of many independent factors (a systems form of the
+ * method; Sec. 4.1's rank-k blocking applied to each factor).  A plan fixes
+ * the shapes; each execution takes the factors' and update blocks' device
+ * addresses and runs every factor in ONE launch of the wave kernel, replayed
+ * from a CUDA graph captured by the plan (a copy of the problem table from
+ * pinned host memory, a reset of the per-factor status words, the launch).
+ *
+ * chm_batch_plan_create
+ *   count   number of factors, >= 0
+ *   n, ld   HOST arrays [count]: order and leading dimension of factor i
+ *   k       HOST array [count]: update vectors of factor i, 0 <= k_i <= 64
+ *   sigma   HOST array [count] of +1 (update) / -1 (downdate) per factor,
+ *           or NULL for all updates
+ *   dtype   CHM_F64 or CHM_F32_MIXED
+ *   plan    receives the plan
+ * Factors with n_i == 0 or k_i == 0 are no-ops.  V_i is n_i x k_i
+ * column-major with leading dimension n_i.  The plan owns all device scratch
+ * (about n_i * 19 KB per vector of every factor) and pinned staging memory;
+ * nothing is allocated by chm_batch_execute.  The current device at creation
+ * is the plan's device.  Returns CHM_OK, CHM_ERR_ARG, CHM_ERR_NOMEM or
+ * CHM_ERR_CUDA.
+ *
+ * chm_batch_autotune: times candidate launch configurations (SM groups,
+ * blocks per SM, largest-work-first or caller order) on synthetic factors of
+ * the plan's shapes (L = I, V = 1e-3, allocated for the duration of the call)
+ * and keeps the fastest.  Synchronises `stream`.  The plan's status words
+ * are reset.  Returns CHM_OK, CHM_ERR_NOMEM (no room for the synthetic
+ * factors; the plan keeps its configuration), CHM_ERR_STATE (another device
+ * is current) or CHM_ERR_CUDA.
+ *
+ * chm_batch_config: the configuration in use (groups 0 = automatic,
+ * ctas_per_sm 0 = occupancy limit, largest_first 1/0); any pointer may be NULL.
+ *
+ * chm_batch_execute
+ *   L, V    HOST arrays [count] of DEVICE pointers (entries of no-op factors
+ *           are ignored); L[i] is modified in place, V[i] is read only
+ * Enqueues the execution on `stream` and returns.  Executions of one plan
+ * run in the order they are enqueued, on any streams; a plan must not be
+ * used from several host threads at once.  Returns CHM_OK, CHM_ERR_ARG
+ * (null or misaligned pointer), CHM_ERR_STATE (wrong device) or CHM_ERR_CUDA.
+ *
+ * chm_batch_status: waits for the plan's last execution and copies the
+ * per-factor {status, row} words into the HOST array info[2 * count]
+ * ({CHM_OK, -1} for factors without a device-side error).  Returns the first
+ * non-OK status in factor order, else CHM_OK.
+ *
+ * chm_batch_plan_destroy: waits for the plan's work and frees it.
+ */
+int chm_batch_plan_create(int count, const int64_t *n, const int64_t *ld, const int64_t *k,
+                          const int8_t *sigma, int dtype, void **plan);
+int chm_batch_autotune(void *plan, chm_stream_t stream);
+int chm_batch_config(void *plan, int *groups, int *ctas_per_sm, int *largest_first);
+int chm_batch_execute(void *plan, void *const *L, const void *const *V, chm_stream_t stream);
+int chm_batch_status(void *plan, int64_t *info);
+int chm_batch_plan_destroy(void *plan);
+
+/*
  * Synchronises `stream`, then reads and clears the status word of the
  * current device and that stream.
  *   info   optional HOST int64[2] receiving {status, info}

@@ -64,6 +64,12 @@ def load(build_if_missing: bool = False):
         "chm_status_string": ([i32], ctypes.c_char_p),
         "chm_version": ([], i32),
         "chm_trace_dump": ([ctypes.c_char_p], i32),
+        "chm_batch_plan_create": ([i32, vp, vp, vp, vp, i32, vp], i32),
+        "chm_batch_autotune": ([vp, vp], i32),
+        "chm_batch_config": ([vp, vp, vp, vp], i32),
+        "chm_batch_execute": ([vp, vp, vp, vp], i32),
+        "chm_batch_status": ([vp, vp], i32),
+        "chm_batch_plan_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -113,6 +119,30 @@ def chm_version() -> int:
 
 def chm_trace_dump(path) -> int:
     return load().chm_trace_dump(path.encode() if isinstance(path, str) else path)
+
+
+def chm_batch_plan_create(count, n, ld, k, sigma, dtype, plan_out):
+    return load().chm_batch_plan_create(count, n, ld, k, sigma, dtype, plan_out)
+
+
+def chm_batch_autotune(plan, stream):
+    return load().chm_batch_autotune(plan, stream)
+
+
+def chm_batch_config(plan, groups, ctas, largest_first):
+    return load().chm_batch_config(plan, groups, ctas, largest_first)
+
+
+def chm_batch_execute(plan, L, V, stream):
+    return load().chm_batch_execute(plan, L, V, stream)
+
+
+def chm_batch_status(plan, info):
+    return load().chm_batch_status(plan, info)
+
+
+def chm_batch_plan_destroy(plan):
+    return load().chm_batch_plan_destroy(plan)
 
 
 # ---------------------------------------------------------------- tensor helpers
@@ -179,3 +209,59 @@ def status_sync(stream=None):
 def check(status, what=""):
     if status != CHM_OK:
         raise ChmError(status, what)
+
+
+class BatchPlan:
+    """A batch plan (chm_batch_*): shapes fixed at creation, factors given per execution.
+
+    ``ns``, ``lds``, ``ks``: per-factor order, leading dimension and vector
+    count; ``signs``: per-factor +1/-1 (or None for all updates)."""
+
+    def __init__(self, ns, lds, ks, signs=None, dtype=CHM_F64):
+        self.count = len(ns)
+        arr = ctypes.c_int64 * max(1, self.count)
+        self._n = arr(*[int(x) for x in ns])
+        self._ld = arr(*[int(x) for x in lds])
+        self._k = arr(*[int(x) for x in ks])
+        self._sig = None if signs is None else (ctypes.c_int8 * max(1, self.count))(*[int(s) for s in signs])
+        h = ctypes.c_void_p()
+        st = chm_batch_plan_create(self.count, ctypes.cast(self._n, ctypes.c_void_p),
+                                   ctypes.cast(self._ld, ctypes.c_void_p), ctypes.cast(self._k, ctypes.c_void_p),
+                                   None if self._sig is None else ctypes.cast(self._sig, ctypes.c_void_p),
+                                   int(dtype), ctypes.byref(h))
+        check(st, "chm_batch_plan_create")
+        self.handle = h
+
+    def autotune(self, stream=None) -> int:
+        return chm_batch_autotune(self.handle, _stream_handle(stream))
+
+    def config(self):
+        g, c, l = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(chm_batch_config(self.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(l)))
+        return g.value, c.value, l.value
+
+    def execute(self, Ls, Vs, stream=None) -> int:
+        """Ls, Vs: sequences of CUDA tensors (or raw device addresses) in factor order."""
+        ptr = ctypes.c_void_p * max(1, self.count)
+        addr = lambda t: t if isinstance(t, int) else (0 if t is None else t.data_ptr())
+        self._Lp = ptr(*[addr(t) for t in Ls])
+        self._Vp = ptr(*[addr(t) for t in Vs])
+        return chm_batch_execute(self.handle, ctypes.cast(self._Lp, ctypes.c_void_p),
+                                 ctypes.cast(self._Vp, ctypes.c_void_p), _stream_handle(stream))
+
+    def status(self):
+        """(first non-OK status, [(status, row)] per factor)."""
+        info = (ctypes.c_int64 * max(2, 2 * self.count))()
+        st = chm_batch_status(self.handle, ctypes.cast(info, ctypes.c_void_p))
+        return st, [(int(info[2 * i]), int(info[2 * i + 1])) for i in range(self.count)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            chm_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -63,3 +63,23 @@ def test_argument_errors_return_synchronously_without_gpu():
     # n == 0 or k == 0 with no per-call info word: nothing to do, no CUDA call
     assert chm.chm_update(None, 0, 1, None, 3, chm.CHM_F64, None) == chm.CHM_OK
     assert chm.chm_update(8, 5, 5, None, 0, chm.CHM_F64, None) == chm.CHM_OK
+
+
+def test_batch_argument_errors_without_gpu():
+    E = chm.CHM_ERR_ARG
+    i64 = ctypes.c_int64
+    plan = ctypes.c_void_p()
+    n, ld, k = (i64 * 2)(10, 20), (i64 * 2)(10, 19), (i64 * 2)(1, 2)       # ld[1] < n[1]
+    vp = lambda a: ctypes.cast(a, ctypes.c_void_p)
+    assert chm.chm_batch_plan_create(2, vp(n), vp(ld), vp(k), None, chm.CHM_F64, ctypes.byref(plan)) == E
+    ld2, k2 = (i64 * 2)(10, 20), (i64 * 2)(1, 65)                            # k above 64
+    assert chm.chm_batch_plan_create(2, vp(n), vp(ld2), vp(k2), None, chm.CHM_F64, ctypes.byref(plan)) == E
+    sig = (ctypes.c_int8 * 2)(1, 0)                                          # sign not +-1
+    assert chm.chm_batch_plan_create(2, vp(n), vp(ld2), vp(k), vp(sig), chm.CHM_F64, ctypes.byref(plan)) == E
+    assert chm.chm_batch_plan_create(-1, None, None, None, None, chm.CHM_F64, ctypes.byref(plan)) == E
+    assert chm.chm_batch_plan_create(1, vp(n), vp(ld2), vp(k), None, 9, ctypes.byref(plan)) == E  # dtype
+    assert chm.chm_batch_plan_create(1, vp(n), vp(ld2), vp(k), None, chm.CHM_F64, None) == E      # no out
+    assert not plan.value
+    assert chm.chm_batch_execute(None, None, None, None) == E
+    assert chm.chm_batch_status(None, None) == E
+    assert chm.chm_batch_plan_destroy(None) == E
