@@ -199,6 +199,68 @@ int chm_batch_status(void *plan, int64_t *info);
 int chm_batch_plan_destroy(void *plan);
 
 /*
+ * Serving: many factors resident in device memory, up/downdate requests
+ * admitted against a memory budget and run by continuous batching (a
+ * systems form of the method; each request is Algorithm 1 with its own V
+ * and sign).  A worker thread keeps one FIFO per factor; whenever one of
+ * its launch slots is free it packs the oldest ready request of every idle
+ * factor into one launch of the wave kernel on that slot's stream.  Each
+ * slot launches with 1/max_inflight of the GPU's resident blocks, so a
+ * launch formed from requests that arrived while another was running
+ * overlaps it on the device.  Requests on one factor run one after another
+ * in submission order, each in its own launch; a factor's result is
+ * bit-identical to applying the same requests alone with chm_modify_ex.
+ *
+ * chm_server_create
+ *   hbm_budget_bytes  device memory the server may hold: factors (n^2
+ *                     elements each), queued update blocks and the launch
+ *                     slots' scratch (a sixteenth of the budget per slot,
+ *                     between 256 MiB and 8 GiB)
+ *   dtype             CHM_F64 or CHM_F32_MIXED for every factor
+ *   max_inflight      launch slots (concurrent launches), 1..4; <= 0 means 2
+ *   srv               receives the server
+ *   Returns CHM_OK, CHM_ERR_ARG, CHM_ERR_BUDGET (budget below the slots'
+ *   scratch), CHM_ERR_NOMEM or CHM_ERR_CUDA.  The current device is the
+ *   server's device.
+ * chm_server_add_factor: copies the upper factor L (n x n, leading dimension
+ *   ld, HOST or DEVICE memory) into the server; fid receives its id (0, 1,
+ *   ...).  Synchronous.  CHM_ERR_BUDGET if it does not fit the budget.
+ * chm_server_submit: queues L_fid <- modification by V (n x k column-major,
+ *   leading dimension n, HOST or DEVICE memory, 1 <= k <= 64) with sign
+ *   sigma = +1 or -1.  V is copied (the caller may reuse it on return) and
+ *   the call does not wait for the GPU.  req_id receives the request id
+ *   (1, 2, ...).  CHM_ERR_BUDGET if the block does not fit the budget or a
+ *   launch slot's scratch.
+ * chm_server_poll: moves up to `max` completed requests into req_ids[],
+ *   status[] (CHM_OK, CHM_ERR_NOT_PD, CHM_ERR_TIMEOUT, or CHM_ERR_STATE for a
+ *   request on a factor invalidated by an earlier failure) and latency_s[]
+ *   (seconds from submission to the worker seeing the launch complete);
+ *   status and latency_s may be NULL.  *got receives the count.  Does not
+ *   block.  Returns CHM_OK or the worker's sticky CUDA error.
+ * chm_server_drain: waits until every submitted request has completed or
+ *   timeout_s has passed (CHM_ERR_TIMEOUT).
+ * chm_server_get_factor: waits until factor fid has no queued or running
+ *   request, then copies it to `out` (HOST or DEVICE, leading dimension ld,
+ *   n x n with the strictly lower part as stored).  Returns CHM_ERR_NOT_PD
+ *   (after copying) if a modification of this factor failed.  Submissions
+ *   on fid during the copy race with it.
+ * chm_server_stats: out[6] = {launches, requests launched, requests
+ *   completed, largest number of launches seen in flight at once, device
+ *   bytes held, requests outstanding}.
+ * chm_server_destroy: stops the worker, waits for the device and frees
+ *   everything; requests still queued are dropped.
+ * A server may be used from several host threads.
+ */
+int chm_server_create(size_t hbm_budget_bytes, int dtype, int max_inflight, void **srv);
+int chm_server_add_factor(void *srv, const void *L, int64_t n, int64_t ld, int64_t *fid);
+int chm_server_submit(void *srv, int64_t fid, const void *V, int64_t k, int sigma, int64_t *req_id);
+int chm_server_poll(void *srv, int64_t *req_ids, int *status, double *latency_s, int max, int *got);
+int chm_server_drain(void *srv, double timeout_s);
+int chm_server_get_factor(void *srv, int64_t fid, void *out, int64_t ld);
+int chm_server_stats(void *srv, int64_t *out);
+int chm_server_destroy(void *srv);
+
+/*
  * Synchronises `stream`, then reads and clears the status word of the
  * current device and that stream.
  *   info   optional HOST int64[2] receiving {status, info}

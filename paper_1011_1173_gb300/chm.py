@@ -70,6 +70,14 @@ def load(build_if_missing: bool = False):
         "chm_batch_execute": ([vp, vp, vp, vp], i32),
         "chm_batch_status": ([vp, vp], i32),
         "chm_batch_plan_destroy": ([vp], i32),
+        "chm_server_create": ([ctypes.c_size_t, i32, i32, vp], i32),
+        "chm_server_add_factor": ([vp, vp, i64, i64, vp], i32),
+        "chm_server_submit": ([vp, i64, vp, i64, i32, vp], i32),
+        "chm_server_poll": ([vp, vp, vp, vp, i32, vp], i32),
+        "chm_server_drain": ([vp, ctypes.c_double], i32),
+        "chm_server_get_factor": ([vp, i64, vp, i64], i32),
+        "chm_server_stats": ([vp, vp], i32),
+        "chm_server_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -143,6 +151,38 @@ def chm_batch_status(plan, info):
 
 def chm_batch_plan_destroy(plan):
     return load().chm_batch_plan_destroy(plan)
+
+
+def chm_server_create(budget, dtype, max_inflight, srv_out):
+    return load().chm_server_create(budget, dtype, max_inflight, srv_out)
+
+
+def chm_server_add_factor(srv, L, n, ld, fid_out):
+    return load().chm_server_add_factor(srv, L, n, ld, fid_out)
+
+
+def chm_server_submit(srv, fid, V, k, sigma, req_out):
+    return load().chm_server_submit(srv, fid, V, k, sigma, req_out)
+
+
+def chm_server_poll(srv, ids, status, latency, max_count, got):
+    return load().chm_server_poll(srv, ids, status, latency, max_count, got)
+
+
+def chm_server_drain(srv, timeout_s):
+    return load().chm_server_drain(srv, timeout_s)
+
+
+def chm_server_get_factor(srv, fid, out, ld):
+    return load().chm_server_get_factor(srv, fid, out, ld)
+
+
+def chm_server_stats(srv, out):
+    return load().chm_server_stats(srv, out)
+
+
+def chm_server_destroy(srv):
+    return load().chm_server_destroy(srv)
 
 
 # ---------------------------------------------------------------- tensor helpers
@@ -258,6 +298,66 @@ class BatchPlan:
     def close(self):
         if getattr(self, "handle", None):
             chm_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A serving loop (chm_server_*): resident factors, queued requests, continuous batching."""
+
+    def __init__(self, budget_bytes, dtype=CHM_F64, max_inflight=2):
+        h = ctypes.c_void_p()
+        check(chm_server_create(int(budget_bytes), int(dtype), int(max_inflight), ctypes.byref(h)),
+              "chm_server_create")
+        self.handle = h
+        self.dtype = dtype
+
+    def add_factor(self, L: torch.Tensor, n=None) -> int:
+        """L: (n, ld) tensor in the C-ABI storage convention (host or device)."""
+        n = L.shape[0] if n is None else int(n)
+        fid = ctypes.c_int64()
+        st = chm_server_add_factor(self.handle, L.data_ptr(), n, L.shape[1], ctypes.byref(fid))
+        if st != CHM_OK:
+            raise ChmError(st, "chm_server_add_factor")
+        return fid.value
+
+    def submit(self, fid, V: torch.Tensor, sigma=1) -> int:
+        """V: contiguous (k, n) tensor (host or device).  Returns the request id or raises."""
+        rid = ctypes.c_int64()
+        st = chm_server_submit(self.handle, int(fid), V.data_ptr(), V.shape[0], int(sigma), ctypes.byref(rid))
+        if st != CHM_OK:
+            raise ChmError(st, "chm_server_submit")
+        return rid.value
+
+    def poll(self, max_count=4096):
+        ids = (ctypes.c_int64 * max_count)()
+        sts = (ctypes.c_int * max_count)()
+        lat = (ctypes.c_double * max_count)()
+        got = ctypes.c_int()
+        check(chm_server_poll(self.handle, ctypes.cast(ids, ctypes.c_void_p), ctypes.cast(sts, ctypes.c_void_p),
+                              ctypes.cast(lat, ctypes.c_void_p), max_count, ctypes.byref(got)), "chm_server_poll")
+        return [(int(ids[i]), int(sts[i]), float(lat[i])) for i in range(got.value)]
+
+    def drain(self, timeout_s=60.0) -> int:
+        return chm_server_drain(self.handle, float(timeout_s))
+
+    def get_factor(self, fid, out: torch.Tensor) -> int:
+        return chm_server_get_factor(self.handle, int(fid), out.data_ptr(), out.shape[1])
+
+    def stats(self):
+        out = (ctypes.c_int64 * 6)()
+        check(chm_server_stats(self.handle, ctypes.cast(out, ctypes.c_void_p)), "chm_server_stats")
+        keys = ("launches", "requests_launched", "completed", "max_concurrent", "bytes_held", "outstanding")
+        return dict(zip(keys, [int(x) for x in out]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            chm_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -49,6 +49,8 @@ std::vector<int> carve(const ProbShape *shapes, int count, const Scratch &sc, Pr
 struct LaunchCfg {
     int groups = 0;       // SM groups (0: automatic)
     int ctas_per_sm = 0;  // resident blocks per SM (0: the occupancy limit)
+    int grid = 0;         // blocks of the launch (0: every SM x ctas_per_sm); a
+                          // smaller grid leaves room for concurrent launches
 };
 
 // Number of SMs of a device and the occupancy limit of the wave kernel.

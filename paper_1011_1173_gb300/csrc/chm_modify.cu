@@ -137,8 +137,11 @@ static int launch_t(const Prob *single, const Prob *d_probs, const int *d_pair_p
     if (cfg.ctas_per_sm > 0) bps = std::min(bps, cfg.ctas_per_sm);
     const int nsm = sm_count(dev);
     if (nsm < 2 || nsm > kMaxSm || npairs < 1) return CHM_ERR_ARG;
-    int G = cfg.groups > 0 ? cfg.groups : default_groups(npairs, nsm);
-    G = std::max(1, std::min(std::min(G, npairs), std::min(kMaxGroups, nsm / 2)));
+    const int grid = cfg.grid > 0 ? std::max(2, std::min(cfg.grid, nsm * bps)) : nsm * bps;
+    // SMs the launch can hold at the occupancy limit
+    const int nsm_eff = std::max(2, std::min(nsm, grid / bps));
+    int G = cfg.groups > 0 ? cfg.groups : default_groups(npairs, nsm_eff);
+    G = std::max(1, std::min(std::min(G, npairs), std::min(kMaxGroups, nsm_eff / 2)));
     Launch<T> P;
     memset(&P, 0, sizeof(P));
     P.probs = d_probs;
@@ -152,7 +155,7 @@ static int launch_t(const Prob *single, const Prob *d_probs, const int *d_pair_p
     P.status = sc.status;
     P.trace = trace;
     P.timeout_ns = timeout_ns();
-    wave_kernel<T><<<nsm * bps, 128, kBlockSmemBytes, stream>>>(P);
+    wave_kernel<T><<<grid, 128, kBlockSmemBytes, stream>>>(P);
     return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
 }
 

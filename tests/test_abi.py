@@ -83,3 +83,19 @@ def test_batch_argument_errors_without_gpu():
     assert chm.chm_batch_execute(None, None, None, None) == E
     assert chm.chm_batch_status(None, None) == E
     assert chm.chm_batch_plan_destroy(None) == E
+
+
+def test_server_argument_errors_without_gpu():
+    E = chm.CHM_ERR_ARG
+    srv = ctypes.c_void_p()
+    assert chm.chm_server_create(1 << 30, 9, 2, ctypes.byref(srv)) == E   # bad dtype
+    assert chm.chm_server_create(1 << 30, chm.CHM_F64, 2, None) == E        # no out
+    assert not srv.value
+    assert chm.chm_server_add_factor(None, None, 4, 4, None) == E
+    assert chm.chm_server_submit(None, 0, None, 1, 1, None) == E
+    got = ctypes.c_int()
+    assert chm.chm_server_poll(None, None, None, None, 0, ctypes.byref(got)) == E
+    assert chm.chm_server_drain(None, 1.0) == E
+    assert chm.chm_server_get_factor(None, 0, None, 1) == E
+    assert chm.chm_server_stats(None, None) == E
+    assert chm.chm_server_destroy(None) == E
