@@ -12,6 +12,19 @@ triangle) + elt*n*k (one read of V).  The L factor (100 MB upper triangle)
 fits in the 126 MB L2, so L2 is flushed (a 512 MB write) between timed steps,
 outside the timed events.
 
+The JSON line also carries the metric's second half, batched and served
+latency against plain per-request launches:
+  batch  512 independent factors, n log-uniform on [64, 4096], k from
+         {1, 4, 16}, random signs whose downdates remove a previously applied
+         V, float64, one graph-replayed launch per execution (chm_batch_*)
+         against one chm_modify_ex launch per factor on one stream;
+  serve  2000 resident factors, n log-uniform on [256, 8192], float32 storage
+         with float64 Compute (dense float64 would exceed the 120 GB budget),
+         Poisson arrivals of requests with k uniform on [1, 32], factor
+         Zipf(1.1), 70 % updates and 30 % downdates of the factor's latest
+         update, through chm_server_* against plain launches serialised on
+         one stream, both fed the same arrival sequence.
+
 Arms:
   default          the CUDA library through its C ABI (this repository)
   --impl reference the serial CPU oracle on the host cores, same workload and metric
@@ -45,7 +58,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # capture of an older kernel version reads as null.
 NCU_TRAFFIC = {("wave_kernel<double>", "859a14c4a7d3e184"): 279.7e6}
 KERNEL_SOURCES = ("paper_1011_1173_gb300/csrc/chm_wave.cuh", "paper_1011_1173_gb300/csrc/chm_device.cuh",
-                  "paper_1011_1173_gb300/csrc/chm_modify.cu")
+                  "paper_1011_1173_gb300/csrc/chm_layout.h", "paper_1011_1173_gb300/csrc/chm_modify.cu")
 
 
 def kernel_source_hash():
@@ -74,7 +87,199 @@ def parse():
     ap.add_argument("--impl", default="chm", choices=["chm", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="autotune the batch plan before timing")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-factors", type=int, default=2000)
     return ap.parse_args()
+
+
+def percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else None
+
+
+def bench_batch(dev, autotune=False, count=512, reps=5):
+    """Batched launch (chm_batch_*) against one plain launch per factor."""
+    import numpy as np
+    import torch
+
+    from paper_1011_1173_gb300 import chm, inputs
+    rng = np.random.default_rng(inputs.config_seed(3))
+    ns = np.exp(rng.uniform(np.log(64), np.log(4096), count)).astype(int)
+    ks = rng.choice([1, 4, 16], count)
+    sg = rng.choice([1, -1], count)
+    Ls, Vs = [], []
+    for i in range(count):
+        n, k = int(ns[i]), int(ks[i])
+        Ls.append(inputs.random_factor(n, 10000 + i, device=dev))
+        Vs.append(inputs.update_block(n, k, 10000 + i, device=dev))
+    stream = torch.cuda.current_stream()
+    # downdates remove a previously applied V: apply those first (untimed)
+    pre = chm.BatchPlan(ns.tolist(), ns.tolist(), [int(k) if s < 0 else 0 for k, s in zip(ks, sg)],
+                        [1] * count)
+    chm.check(pre.execute(Ls, Vs, stream), "batch pre-update")
+    fwd = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), sg.tolist())
+    inv = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), (-sg).tolist())
+    if autotune:
+        chm.check(fwd.autotune(stream), "autotune")
+        chm.check(inv.autotune(stream), "autotune")
+    bytes_exec = float(sum(alg_bytes(int(n), int(k)) for n, k in zip(ns, ks)))
+
+    def timed(fn, reps):
+        ts = []
+        for r in range(reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(r)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                ts.append(a.elapsed_time(b))
+        return ts
+
+    # an even number of executions (forward, inverse, ...) leaves every factor as it started
+    bt = timed(lambda r: chm.check((fwd if r % 2 == 0 else inv).execute(Ls, Vs, stream), "batch"), 2 * reps - 1)
+    st1, _ = fwd.status()
+    st2, _ = inv.status()
+    chm.check(st1, "batch status")
+    chm.check(st2, "batch status")
+    # plain: one launch per factor in the same order, completion time of each
+    lat_plain = []
+    plain_ms = []
+    for r in range(2 * reps + 1):
+        sign = sg if r % 2 == 0 else -sg
+        evs = []
+        a = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(count):
+            chm.check(chm.modify(Ls[i], Vs[i], int(sign[i]), stream=stream), "plain")
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs.append(e)
+        torch.cuda.synchronize()
+        if r > 0:
+            lat = [a.elapsed_time(e) for e in evs]
+            lat_plain += lat
+            plain_ms.append(lat[-1])
+    chm.check(chm.status_sync(stream)[0], "plain status")
+    g, c, lpt = fwd.config()
+    for p in (pre, fwd, inv):
+        p.close()
+    del Ls, Vs
+    torch.cuda.empty_cache()
+    b_ms = statistics.median(bt)
+    p_ms = statistics.median(plain_ms)
+    return {"workload": "%d factors, n log-uniform [64, 4096], k in {1,4,16}, random signs (downdates "
+                        "remove an applied V), float64" % count,
+            "alg_bytes_per_exec": bytes_exec,
+            "batch": {"ms_per_exec": b_ms, "GBps": bytes_exec / (b_ms / 1e3) / 1e9,
+                      "factor_latency_ms": {"p50": percentile(bt, 50), "p99": percentile(bt, 99)},
+                      "launches_per_exec": 1, "graph": True,
+                      "config": {"groups": g, "ctas_per_sm": c, "largest_first": lpt, "autotuned": autotune}},
+            "plain": {"ms_per_exec": p_ms, "GBps": bytes_exec / (p_ms / 1e3) / 1e9,
+                      "factor_latency_ms": {"p50": percentile(lat_plain, 50), "p99": percentile(lat_plain, 99)},
+                      "launches_per_exec": count},
+            "speedup": p_ms / b_ms}
+
+
+def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30)):
+    """Served requests (chm_server_*) against plain launches serialised on one stream."""
+    import numpy as np
+    import torch
+
+    from paper_1011_1173_gb300 import chm, inputs
+    rng = np.random.default_rng(inputs.config_seed(4))
+    ns = np.exp(rng.uniform(np.log(256), np.log(8192), nfactors)).astype(int)
+    dt = torch.float32
+    srv = chm.Server(budget, chm.CHM_F32_MIXED, max_inflight=2)
+    plainL = {}
+    perm = rng.permutation(nfactors)
+    for i in range(nfactors):
+        L = inputs.random_factor(int(ns[i]), 20000 + i, device=dev, dtype=dt)
+        srv.add_factor(L)
+        del L
+    # request sequence: factor Zipf(1.1) over a permutation, k ~ U{1..32},
+    # 70 % updates with a fresh V, 30 % downdates of the latest applied V
+    reqs, hist = [], {}
+    for r in range(nreq):
+        f = int(perm[min(nfactors - 1, rng.zipf(1.1) - 1)])
+        n = int(ns[f])
+        if rng.random() < 0.3 and hist.get(f):
+            V, s = hist[f].pop(), -1
+        else:
+            k = int(rng.integers(1, 33))
+            V, s = inputs.update_block(n, k, 30000 + r, device=dev, dtype=dt), 1
+            hist.setdefault(f, []).append(V)
+        reqs.append((f, V, s))
+    used = sorted(set(f for f, _, _ in reqs))
+    for f in used:  # plain comparator's copies of the factors touched
+        plainL[f] = inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt)
+    bytes_req = [alg_bytes(int(ns[f]), V.shape[0], 4) for f, V, _ in reqs]
+    # plain saturation rate: back-to-back launches on one stream
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f, V, s in reqs[:200]:
+        chm.check(chm.modify(plainL[f], V, s, stream=stream), "plain")
+    torch.cuda.synchronize()
+    sat = 200 / (time.perf_counter() - t0)
+    rate = 0.9 * sat
+    gaps = rng.exponential(1.0 / rate, nreq)
+    arrivals = np.cumsum(gaps)
+    # undo the 200 requests on the plain copies: regenerate them
+    for f in used:
+        plainL[f] = inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt)
+    torch.cuda.synchronize()
+
+    # served run: the host submits at the arrival times
+    t_start = time.perf_counter()
+    for j, (f, V, s) in enumerate(reqs):
+        while time.perf_counter() - t_start < arrivals[j]:
+            pass
+        srv.submit(f, V, s)
+    chm.check(srv.drain(600.0), "serve drain")
+    t_serve = time.perf_counter() - t_start
+    done = srv.poll(nreq + 16)
+    lat_srv = [d[2] * 1e3 for d in done]
+    bad = sum(1 for d in done if d[1] != chm.CHM_OK)
+    st = srv.stats()
+    srv.close()
+
+    # plain run: same arrivals, one launch per request on one stream; a
+    # request completes at its event, timed from an event recorded when the
+    # arrival clock starts (the stream is idle then)
+    evs = []
+    a0 = torch.cuda.Event(enable_timing=True)
+    t_start = time.perf_counter()
+    a0.record(stream)
+    for j, (f, V, s) in enumerate(reqs):
+        while time.perf_counter() - t_start < arrivals[j]:
+            pass
+        chm.check(chm.modify(plainL[f], V, s, stream=stream), "plain")
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t_start
+    chm.check(chm.status_sync(stream)[0], "plain status")
+    del plainL, reqs, hist
+    torch.cuda.empty_cache()
+    tot = float(sum(bytes_req))
+    lat_plain = [a0.elapsed_time(e) - arrivals[j] * 1e3 for j, e in enumerate(evs)]
+    t_plain = max(t_plain, a0.elapsed_time(evs[-1]) / 1e3)
+    return {"workload": "%d resident factors, n log-uniform [256, 8192], float32 storage + float64 Compute, "
+                        "%d requests, k ~ U{1..32}, factor Zipf(1.1), 70%% updates / 30%% downdates, Poisson "
+                        "arrivals at 0.9 x the plain path's saturation rate" % (nfactors, nreq),
+            "offered_rate_rps": rate, "plain_saturation_rps": sat,
+            "served": {"rps": nreq / t_serve, "GBps": tot / t_serve / 1e9,
+                       "latency_ms": {"p50": percentile(lat_srv, 50), "p99": percentile(lat_srv, 99)},
+                       "failed": bad, "launches": st["launches"], "max_concurrent": st["max_concurrent"]},
+            "plain": {"rps": nreq / t_plain, "GBps": tot / t_plain / 1e9,
+                      "latency_ms": {"p50": percentile(lat_plain, 50), "p99": percentile(lat_plain, 99)},
+                      "launches": nreq}}
 
 
 class ClockSampler:
@@ -309,6 +514,12 @@ def main():
                 "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash())),
                 "kernel_source_hash": kernel_source_hash()}
 
+    batch = serve = None
+    if rank == 0 and not args.no_batch:
+        batch = bench_batch(dev, autotune=args.autotune)
+    if rank == 0 and not args.no_serve:
+        serve = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests)
+
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(n, k)
@@ -324,6 +535,7 @@ def main():
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "batched": batch, "served": serve,
                 "gpu_launches": 2 * args.steps * ((k + 63) // 64),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -105,3 +105,25 @@ def sigma_vector(k: int, seed: int, p_update: float = 0.5) -> torch.Tensor:
     g = _gen(seed + 104729, "cpu")
     r = torch.rand((k,), generator=g)
     return torch.where(r < p_update, 1, -1).to(torch.int8)
+
+
+def random_factor(n: int, seed: int, ld: int | None = None, device="cpu",
+                  dtype=torch.float64) -> torch.Tensor:
+    """A cheap upper-triangular factor for workloads that need many of them
+    (batched and served runs): diagonal 1 + U[0, 1), strictly upper entries
+    N(0, 1/n), in (n, ld) storage.  Any upper-triangular matrix with positive
+    diagonal is the Cholesky factor of A = L^T L, so this is a valid input of
+    the method; its conditioning is close to that of ``spd_factor``'s."""
+    ld = n if ld is None else int(ld)
+    if ld < max(1, n):
+        raise ValueError("ld must be >= max(1, n)")
+    out = torch.zeros((n, ld), dtype=dtype, device=device)
+    if n == 0:
+        return out
+    g = _gen(seed, device)
+    # row j of the storage is column j of L: its entries i <= j are the lower
+    # triangle (with the diagonal) of the (n, n) storage block
+    R = torch.randn((n, n), generator=g, dtype=dtype, device=device).mul_(n ** -0.5).tril_(-1)
+    R.diagonal().copy_(1.0 + torch.rand((n,), generator=g, dtype=dtype, device=device))
+    out[:, :n].copy_(R)
+    return out
