@@ -277,12 +277,24 @@ int chm_version(void);
 
 /*
  * Diagnostics.  When the environment variable CHM_TRACE is set to 1 before
- * the first call, every launch records, per task, 16 int64 stamps of the
- * device's %globaltimer (ns) at fixed points of the task (slot 15 holds the
- * SM id).  chm_trace_dump synchronises the device and writes the last
- * launch's records (tasks x 16 int64, native endianness) to the file `path`.
+ * the first call, every launch of the plain entry points records 16 int64
+ * stamps of the device's %globaltimer (ns) at fixed points per (wave, column
+ * block): first the sweep tasks' records, then the wave blocks'
+ * ([2][waves][blocks][16]).  chm_trace_dump synchronises the device and
+ * writes the last launch's records (native endianness) to the file `path`.
  * Returns CHM_OK, CHM_ERR_STATE if tracing is off, CHM_ERR_ARG if the file
  * cannot be written, or CHM_ERR_CUDA.  Not for production use.
+ *
+ * Environment read once per process:
+ *   CHM_TIMEOUT_NS         bound on any single wait between thread blocks
+ *                          (default 4e9); a wait that runs out ends the
+ *                          launch with CHM_ERR_TIMEOUT and the context stays
+ *                          usable
+ *   CHM_GROUPS             SM groups (concurrent waves) of a launch
+ *   CHM_MAX_CTAS_PER_SM    cap on resident blocks per SM
+ *   CHM_TEST_SKIP_PUBLISH  test hook: the next launch of the plain entry
+ *                          points leaves the given block's rotation panel
+ *                          unreleased, so the waits on it run out
  */
 int chm_trace_dump(const char *path);
 

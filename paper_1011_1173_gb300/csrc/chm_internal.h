@@ -51,6 +51,8 @@ struct LaunchCfg {
     int ctas_per_sm = 0;  // resident blocks per SM (0: the occupancy limit)
     int grid = 0;         // blocks of the launch (0: every SM x ctas_per_sm); a
                           // smaller grid leaves room for concurrent launches
+    int skip_publish = -1;  // test hook: no wave releases this block's panel, so
+                            // its consumers' bounded waits run out (-1: none)
 };
 
 // Number of SMs of a device and the occupancy limit of the wave kernel.

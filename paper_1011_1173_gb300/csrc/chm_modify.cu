@@ -155,6 +155,7 @@ static int launch_t(const Prob *single, const Prob *d_probs, const int *d_pair_p
     P.status = sc.status;
     P.trace = trace;
     P.timeout_ns = timeout_ns();
+    P.skip_publish = cfg.skip_publish;
     wave_kernel<T><<<grid, 128, kBlockSmemBytes, stream>>>(P);
     return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
 }
@@ -279,6 +280,21 @@ static Workspace *find_workspace(int dev, cudaStream_t s, bool create)
     return w;
 }
 
+// Test hook for the bounded waits: CHM_TEST_SKIP_PUBLISH=b in the environment
+// makes the next launch of the plain entry points leave block b's panel
+// unreleased (once), so that the waits on it run out and the launch ends
+// with CHM_ERR_TIMEOUT.  Nothing faults; the context stays usable.
+static int take_test_skip()
+{
+    static int pending = [] {
+        const char *e = getenv("CHM_TEST_SKIP_PUBLISH");
+        return e ? atoi(e) : -1;
+    }();
+    const int v = pending;
+    pending = -1;
+    return v;
+}
+
 static unsigned long long down_mask(const int8_t *sigma, int sign, long long q0, int kw)
 {
     unsigned long long mask = 0;
@@ -327,7 +343,9 @@ static int enqueue_single(void *L, long long n, long long ld, const void *V, lon
                 g_trace_words = need;
             }
         }
-        rc = launch_wave(dtype, &pr, nullptr, nullptr, 1, kw, nb, sc, LaunchCfg(), trace, stream);
+        LaunchCfg cfg;
+        cfg.skip_publish = take_test_skip();
+        rc = launch_wave(dtype, &pr, nullptr, nullptr, 1, kw, nb, sc, cfg, trace, stream);
         if (rc != CHM_OK) return rc;
     }
     return CHM_OK;

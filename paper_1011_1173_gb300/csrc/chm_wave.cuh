@@ -62,6 +62,7 @@ struct Launch {
     long long *status;      // sticky {status, row} of the scratch owner
     long long *trace;       // optional timestamps, [2][npairs][nbmax][kTracePoints]
     long long timeout_ns;
+    int skip_publish;       // test hook: wave blocks never release this block's panel (-1: none)
 };
 
 // Everything one task needs about its pair.
@@ -84,6 +85,7 @@ struct Wave {
     long long *progress;
     const long long *progress_prev;
     long long *trace_sweep, *trace_wave;  // this pair's rows, or null
+    int skip_publish;                     // test hook (see Launch)
     SyncArgs sync;
 };
 
@@ -133,6 +135,7 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     } else {
         w.trace_sweep = w.trace_wave = nullptr;
     }
+    w.skip_publish = P.skip_publish;
     w.sync.abort_flag = P.ctl + kCtlAbort;
     w.sync.status = P.status;
     w.sync.user_info = pr.info;
@@ -477,6 +480,7 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
     volatile int *cdone = &S.cdone;
     int next_fetch = 0, next_fin = 0;
     long long idle_since = -1;
+    unsigned idle_iters = 0;
     while (next_fin < nb) {
         bool progressed = false;
         // finish block next_fin once warp C has rotated it
@@ -545,6 +549,7 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
         }
         if (progressed) {
             idle_since = -1;
+            idle_iters = 0;
             continue;
         }
         // neither: stop on an abort or a stopped warp, else wait a little (bounded)
@@ -553,7 +558,7 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
         const long long now = global_ns();
         if (idle_since < 0) {
             idle_since = now;
-        } else if (now - idle_since > sy.timeout_ns) {
+        } else if (now - idle_since > sy.timeout_ns || ++idle_iters > (1u << 27)) {
             if (lane == 0) {
                 record_error(sy, kStatusTimeout, -4);
                 S.bail = 1;
@@ -670,7 +675,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
         }
         if (lane == 0) __stcg(w.tend + b, Tlast);
         __syncwarp();
-        if (lane == 0) st_release_gpu(w.pflag + b, epoch);
+        if (lane == 0 && b != w.skip_publish) st_release_gpu(w.pflag + b, epoch);
         CHM_WTRACE(b, 5);
         Tend = Tlast;
         iTend = __shfl_sync(FULL, iTn, rows - 1);
@@ -904,6 +909,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
     } else if (role == kRoleSweep) {
         unsigned char *sm = chm_smem + (size_t)warp * kWarpSmemBytes;
         long long idle_since = -1;
+        unsigned idle_iters = 0;
         for (;;) {
             if (aborted(sy)) break;
             int b = -1;
@@ -911,6 +917,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             if (j >= 0) {
                 sweep_task<T>(make_wave(P, j), b, sm);
                 idle_since = -1;
+                idle_iters = 0;
                 continue;
             }
             // nothing to take: stop once every pair is done, else look again
@@ -918,7 +925,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             const long long now = global_ns();
             if (idle_since < 0) {
                 idle_since = now;
-            } else if (now - idle_since > P.timeout_ns) {
+            } else if (now - idle_since > P.timeout_ns || ++idle_iters > (1u << 24)) {
                 if (lane == 0) record_error(sy, kStatusTimeout, -2);
                 break;
             }
