@@ -59,7 +59,7 @@ struct LaunchCfg {
 int sm_count(int dev);
 int wave_occupancy(int dtype, int dev, int *ctas_per_sm);
 long long timeout_ns();
-int default_groups(int npairs, int nsm);
+int default_groups(int npairs, int nsm, int nprobs);
 
 // Enqueue one launch of the wave kernel on `stream`.  Either one problem
 // (`single`, no device tables) or `nprobs` problems whose records are in
