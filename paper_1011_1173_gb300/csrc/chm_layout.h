@@ -45,8 +45,6 @@ struct PairRec {
     size_t coef;   // [nb][kW] CoefRow (32-byte rows for either type)
     size_t chain;  // [nb][kW] ChainRow, this wave's row data after the wave
     size_t tend;   // [nb]     T after the block's last row
-    size_t zbuf;   // [nb][kW] T u_hat before the block's last tile
-    size_t carry;  // [nb][kW] u_hat at the diagonal block
     size_t rdiag;  // [nb][kW][kW] -S_rc e_r / D_r, r < c (diagonal block), for this wave
     size_t rtile;  // [nb][kW][kW] -S_rc e_r (rows of block b, cols of b+1), for this wave
     size_t bytes;
@@ -59,8 +57,6 @@ CHM_HD inline PairRec pair_rec(int nb)
     r.coef = x;  x += rows * 32;
     r.chain = x; x += rows * sizeof(ChainRow);
     r.tend = x;  x = align256(x + (size_t)nb * sizeof(double));
-    r.zbuf = x;  x += rows * sizeof(double);
-    r.carry = x; x += rows * sizeof(double);
     r.rdiag = x; x += rows * kW * sizeof(double);
     r.rtile = x; x += rows * kW * sizeof(double);
     r.bytes = align256(x);
@@ -71,10 +67,16 @@ CHM_HD inline size_t prob_data_bytes(int nb, int k)
 {
     return (size_t)k * pair_rec(nb).bytes + align256((size_t)nb * kW * sizeof(ChainRow));
 }
-// Its int flags: per pair pflag, zflag, cflag, dflag ([nb] each), then rflag0 [nb].
-CHM_HD inline size_t prob_iflags(int nb, int k) { return ((size_t)(4 * k + 1) * nb + 63) & ~(size_t)63; }
-// Its progress words: per pair [nb] of (epoch << 32) + off-diagonal tiles done.
-CHM_HD inline size_t prob_progress(int nb, int k) { return ((size_t)k * nb + 31) & ~(size_t)31; }
+// Its int flags: per pair pflag, dflag ([nb] each), then rflag0 [nb].
+CHM_HD inline size_t prob_iflags(int nb, int k) { return ((size_t)(2 * k + 1) * nb + 63) & ~(size_t)63; }
+// Its tagged 64-bit words, each (epoch << 32) | 32-bit payload: per pair
+// [nb] progress words (payload: off-diagonal tiles done), then per pair
+// [nb][kW][2] the carry z = T u_hat before the block's last tile and
+// [nb][kW][2] the carry u_hat at the diagonal block (payload: the high and
+// the low half of a double).  A reader takes a carry once both halves carry
+// the current epoch, so the writer needs no fence.
+constexpr int kTagsPerBlock = 1 + 4 * kW;
+CHM_HD inline size_t prob_progress(int nb, int k) { return ((size_t)k * nb * kTagsPerBlock + 31) & ~(size_t)31; }
 
 // One problem of a launch (L and V of the launch's element type).
 struct Prob {
@@ -88,7 +90,7 @@ struct Prob {
     unsigned long long down_mask;  // bit q set: wave q is a downdate
     char *data;                    // prob_data_bytes(nb, k), 256-byte aligned
     int *iflags;                   // prob_iflags(nb, k) ints
-    long long *progress;           // prob_progress(nb, k) words
+    long long *progress;           // prob_progress(nb, k) tagged words
     long long *info;               // optional {status, row} of this problem
 };
 

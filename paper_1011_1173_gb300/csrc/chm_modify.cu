@@ -408,9 +408,9 @@ constexpr long long kNoAllocMaxN = 8192;
 // control words, status word, int flags, progress words, data
 constexpr size_t kNoAllocStatusOff = align256(kCtlInts * sizeof(int));
 constexpr size_t kNoAllocIflagsOff = kNoAllocStatusOff + 256;
-constexpr size_t kNoAllocIflags = 65536;  // ints
+constexpr size_t kNoAllocIflags = 32768;  // ints
 constexpr size_t kNoAllocProgressOff = kNoAllocIflagsOff + kNoAllocIflags * sizeof(int);
-constexpr size_t kNoAllocProgress = 32768;  // words
+constexpr size_t kNoAllocProgress = 196608;  // tagged words (1.5 MiB)
 constexpr size_t kNoAllocDataOff = kNoAllocProgressOff + kNoAllocProgress * sizeof(long long);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

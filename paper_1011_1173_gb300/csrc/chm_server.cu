@@ -332,8 +332,9 @@ int create(size_t budget, int dtype, int max_inflight, Server **out)
     if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) rc = CHM_ERR_CUDA;
     for (int i = 0; i < s->nslots && rc == CHM_OK; ++i) {
         Slot &sl = s->slots[i];
-        // flags sized for blocks of 32 columns: about 1/4500 of the data region
-        const size_t iflags = per / 2048, progress = per / 8192;
+        // flag and tagged-word regions in proportion to the data region: per
+        // 32 columns and wave, ~18 KB of data against 3 int flags and 129 tags
+        const size_t iflags = per / 4096, progress = per / 128;
         const size_t data = per - iflags * sizeof(int) - progress * sizeof(long long);
         rc = scratch_alloc(&sl.sc, iflags, progress, data);
         sl.scratch_bytes = per;

@@ -78,12 +78,13 @@ struct Wave {
     ChainRow *chain;            // [nb][kW] this wave's output row data
     const ChainRow *chain_in;   // [nb][kW] row data before this wave
     ChainRow *chain0;           // [nb][kW] original factor's row data (wave 0 writes)
-    double *tend, *zbuf, *carry, *rdiag, *rtile;
+    double *tend, *rdiag, *rtile;
     double *rdiag_next, *rtile_next;  // the next wave's (null without one)
-    int *pflag, *zflag, *cflag, *dflag, *rflag0;
+    int *pflag, *dflag, *rflag0;
     const int *dflag_prev;
     long long *progress;
     const long long *progress_prev;
+    long long *ztag, *ctag;     // [nb][kW][2] tagged carries z and u_hat
     long long *trace_sweep, *trace_wave;  // this pair's rows, or null
     int skip_publish;                     // test hook (see Launch)
     SyncArgs sync;
@@ -113,21 +114,19 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.chain0 = reinterpret_cast<ChainRow *>(pr.data + (size_t)pr.k * rc.bytes);
     w.chain_in = q == 0 ? w.chain0 : reinterpret_cast<const ChainRow *>(d - rc.bytes + rc.chain);
     w.tend = reinterpret_cast<double *>(d + rc.tend);
-    w.zbuf = reinterpret_cast<double *>(d + rc.zbuf);
-    w.carry = reinterpret_cast<double *>(d + rc.carry);
     w.rdiag = reinterpret_cast<double *>(d + rc.rdiag);
     w.rtile = reinterpret_cast<double *>(d + rc.rtile);
     w.rdiag_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rdiag) : nullptr;
     w.rtile_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rtile) : nullptr;
-    int *f = pr.iflags + (size_t)q * 4 * nb;
+    int *f = pr.iflags + (size_t)q * 2 * nb;
     w.pflag = f;
-    w.zflag = f + nb;
-    w.cflag = f + 2 * nb;
-    w.dflag = f + 3 * nb;
+    w.dflag = f + nb;
     w.dflag_prev = q > 0 ? f - nb : nullptr;
-    w.rflag0 = pr.iflags + (size_t)pr.k * 4 * nb;
+    w.rflag0 = pr.iflags + (size_t)pr.k * 2 * nb;
     w.progress = pr.progress + (size_t)q * nb;
     w.progress_prev = q > 0 ? w.progress - nb : nullptr;
+    w.ztag = pr.progress + (size_t)pr.k * nb + (size_t)q * nb * kW * 2;
+    w.ctag = pr.progress + (size_t)pr.k * nb * (1 + kW * 2) + (size_t)q * nb * kW * 2;
     if (P.trace) {
         const size_t row = (size_t)j * P.nbmax * kTracePoints;
         w.trace_sweep = P.trace + row;
@@ -295,6 +294,53 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// A double published as two tagged words, (epoch << 32) | high half and
+// (epoch << 32) | low half: each 8-byte store is single-copy atomic, so a
+// reader that sees both tags equal to the current epoch has the value, and
+// the writer needs no fence or flag.
+__device__ __forceinline__ void put_tagged(long long *w2, double v, long long ep64)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    __stcg(w2, ep64 | (long long)(u >> 32));
+    __stcg(w2 + 1, ep64 | (long long)(u & 0xffffffffull));
+}
+// Read a tagged double: true (and *v) once both words carry `ep64`.
+__device__ __forceinline__ bool get_tagged(const long long *w2, long long ep64, double *v)
+{
+    const long long h = ld_relaxed_gpu(w2), l = ld_relaxed_gpu(w2 + 1);
+    if ((h & ~0xffffffffll) != ep64 || (l & ~0xffffffffll) != ep64) return false;
+    *v = __longlong_as_double((long long)(((unsigned long long)h << 32) | ((unsigned long long)l & 0xffffffffull)));
+    return true;
+}
+
+// The whole warp waits (bounded) until every lane's tagged double carries
+// `ep64`; every exit is decided for the warp as a whole.  Returns false if
+// the launch is being aborted or the wait ran out of time (recorded).
+__device__ __forceinline__ bool warp_wait_tagged(const SyncArgs &s, const long long *w2, long long ep64,
+                                                 long long who, double *v)
+{
+    const long long t0 = global_ns();
+    unsigned ns = 16;
+    for (unsigned it = 0;; ++it) {
+        if (__all_sync(0xffffffffu, get_tagged(w2, ep64, v))) return true;
+        if ((it & 15u) == 15u) {
+            const int lane = threadIdx.x & 31;
+            int stop = 0;
+            if (lane == 0) {
+                if (aborted(s)) {
+                    stop = 1;
+                } else if (global_ns() - t0 > s.timeout_ns || it > (1u << 26)) {
+                    record_error(s, kStatusTimeout, who);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+}
+
 // Copy `bytes` (a multiple of 16) from global to shared memory with the 32
 // lanes of a warp.
 __device__ __forceinline__ void fetch_bytes(void *dst, const void *src, int bytes, int lane)
@@ -384,23 +430,27 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
         if (lane == 0) st_release_gpu(w.rflag0 + b, epoch);
     }
 
+    // The shared tile is staged with the next tile right after this tile's
+    // stores are issued, when the previous wave has released it, so that its
+    // load overlaps the acknowledgement the progress release waits for.
+    bool staged = false;
     for (int p = 0; p < b; ++p) {
         const bool lastTile = p == b - 1;
-        // the tile as the previous wave left it, fetched while the panel is pending
-        if (prog_prev) CHM_WARP_WAIT(wait_ge(sy, prog_prev, ep64 + p + 1, who));
-        T x[kW];
-        {
+        if (!staged) {
+            // the tile as the previous wave left it, fetched while the panel is pending
+            if (prog_prev) CHM_WARP_WAIT(wait_ge(sy, prog_prev, ep64 + p + 1, who));
+            T x[kW];
             const T *src = w.L + (long long)p * kW + lane;
 #pragma unroll
             for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
+#pragma unroll
+            for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         }
         CHM_WARP_WAIT(wait_eq(sy, w.pflag + p, epoch, who));
         if (lastTile) CHM_TRACE(1);
         cf[lane] = ld_coef(w.coef + (size_t)p * kW + lane);
         if (lastTile && w.has_next) ch[lane] = ld_chain(w.chain + (size_t)p * kW + lane);
         const double tnext = (p == b - 2) ? __ldcg(w.tend + p) : 0.0;
-#pragma unroll
-        for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         __syncwarp();
         T S[kW];
 #pragma unroll
@@ -413,17 +463,10 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
                 uh = fma(-c.b, S[r], uh);
             }
         }
-        if (p == b - 2) {
-            // the wave block's carry for block b: z = T u_hat after rows < (b-1) kW
-            __stcg(w.zbuf + (size_t)b * kW + lane, active ? tnext * (double)uh : 0.0);
-            __syncwarp();
-            if (lane == 0) st_release_gpu(w.zflag + b, epoch);
-        }
-        if (lastTile) {
-            // u_hat entering the diagonal block, for the wave block's rotations there
-            __stcg(w.carry + (size_t)b * kW + lane, active ? (double)uh : 0.0);
-            __syncwarp();
-            if (lane == 0) st_release_gpu(w.cflag + b, epoch);
+        if (p == b - 2)  // the wave block's carry for block b: z = T u_hat after rows < (b-1) kW
+            put_tagged(w.ztag + ((size_t)b * kW + lane) * 2, active ? tnext * (double)uh : 0.0, ep64);
+        if (lastTile) {  // u_hat entering the diagonal block, for the wave block's rotations there
+            put_tagged(w.ctag + ((size_t)b * kW + lane) * 2, active ? (double)uh : 0.0, ep64);
             CHM_TRACE(2);
         }
         if (lastTile && w.has_next) {
@@ -447,6 +490,21 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
 #pragma unroll
             for (int c = 0; c < kW; ++c)
                 if (c < ncols) __stcg(dst + (c0 + c) * ld, tile[c][lane]);
+        }
+        __syncwarp();
+        staged = false;
+        if (p + 1 < b) {
+            const int ready = prog_prev ? __shfl_sync(0xffffffffu, ld_acquire_gpu(prog_prev) >= ep64 + p + 2 ? 1 : 0, 0)
+                                        : 1;
+            if (ready) {
+                T x[kW];
+                const T *src = w.L + (long long)(p + 1) * kW + lane;
+#pragma unroll
+                for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
+#pragma unroll
+                for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
+                staged = true;
+            }
         }
         __syncwarp();
         if (lane == 0) st_release_gpu(prog_me, ep64 + p + 1);
@@ -523,10 +581,13 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
                     ready = ld_relaxed_gpu(w.dflag_prev + b) == epoch &&
                             (b == 0 || ld_relaxed_gpu(w.progress_prev + b) >= ep64 + b);
                 }
-                if (ready && b >= 2) ready = ld_relaxed_gpu(w.zflag + b) == epoch;
                 if (ready) __threadfence();  // acquire what those flags released
             }
-            if (__shfl_sync(FULL, ready, 0)) {
+            ready = __shfl_sync(FULL, ready, 0);
+            // the carry z of the block (b >= 2), from the sweep's tagged words
+            double zc = 0.0;
+            if (ready && b >= 2) ready = __all_sync(FULL, get_tagged(w.ztag + ((size_t)b * kW + lane) * 2, ep64, &zc));
+            if (ready) {
                 __syncwarp();
                 CHM_WTRACE(b, 2);
                 const long long c0 = (long long)b * kW;
@@ -534,7 +595,7 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
                 if (b >= 1) fetch_bytes(&S.Rt[s][0][0], w.rtile + (size_t)(b - 1) * kW * kW, kW * kW * 8, lane);
                 fetch_bytes(&S.rowd[s][0], w.chain_in + (size_t)b * kW, kW * (int)sizeof(ChainRow), lane);
                 if (b >= 2) {
-                    fetch_bytes(&S.zpart[s][0], w.zbuf + (size_t)b * kW, kW * 8, lane);
+                    S.zpart[s][lane] = zc;
                 } else {
                     S.zpart[s][lane] = (c0 + lane < n) ? (double)w.V[c0 + lane] : 0.0;
                 }
@@ -718,6 +779,7 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
     const long long n = w.n, ld = w.ld;
     const int nb = w.nb;
     const int epoch = sy.epoch;
+    const long long ep64 = (long long)epoch << 32;
     const long long who = -1;
     for (int b = 0; b < nb; ++b) {
         const int s = b % kSlots;
@@ -729,8 +791,9 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
         if (b == 0) {
             uh = active ? w.V[c0 + lane] : T(0);
         } else {
-            CHM_WARP_WAIT(wait_eq(sy, w.cflag + b, epoch, who));
-            uh = (T)__ldcg(w.carry + (size_t)b * kW + lane);
+            double u = 0.0;
+            if (!warp_wait_tagged(sy, w.ctag + ((size_t)b * kW + lane) * 2, ep64, who, &u)) return;
+            uh = (T)u;
         }
         CHM_WTRACE(b, 10);
         // the tile as the previous wave left it: warp D acquired that wave's
