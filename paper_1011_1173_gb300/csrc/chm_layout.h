@@ -85,7 +85,7 @@ struct Prob {
     long long n, ld, ldv;
     int k;                         // waves of this problem in the launch (<= kMaxWaves)
     int nb;                        // column blocks of kW columns
-    int pair0;                     // index of its first pair
+    int pair0;                     // index of its first pair (k waves, then the final pass)
     int pad_;
     unsigned long long down_mask;  // bit q set: wave q is a downdate
     char *data;                    // prob_data_bytes(nb, k), 256-byte aligned

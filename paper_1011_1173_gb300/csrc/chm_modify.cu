@@ -28,7 +28,7 @@ ScratchNeed scratch_need(const ProbShape *shapes, int count)
         r.iflags += prob_iflags(nb, k);
         r.progress += prob_progress(nb, k);
         r.data += prob_data_bytes(nb, k);
-        r.npairs += k;
+        r.npairs += k + 1;  // its waves and the final pass
         r.nbmax = std::max(r.nbmax, nb);
     }
     return r;
@@ -52,8 +52,8 @@ std::vector<int> carve(const ProbShape *shapes, int count, const Scratch &sc, Pr
         fi += prob_iflags(nb, k);
         fp += prob_progress(nb, k);
         fd += prob_data_bytes(nb, k);
-        pair_prob.insert(pair_prob.end(), (size_t)k, i);
-        pair += k;
+        pair_prob.insert(pair_prob.end(), (size_t)k + 1, i);
+        pair += k + 1;
     }
     return pair_prob;
 }
@@ -334,7 +334,7 @@ static int enqueue_single(void *L, long long n, long long ld, const void *V, lon
         pr.info = d_info;
         long long *trace = nullptr;
         if (allow_trace && trace_on()) {
-            const size_t need = (size_t)2 * kw * nb * kTracePoints;
+            const size_t need = (size_t)2 * (kw + 1) * nb * kTracePoints;
             if (g_trace_cap < need) {
                 cudaFree(g_trace);
                 g_trace = nullptr;
@@ -349,7 +349,7 @@ static int enqueue_single(void *L, long long n, long long ld, const void *V, lon
         }
         LaunchCfg cfg;
         cfg.skip_publish = take_test_skip();
-        rc = launch_wave(dtype, &pr, nullptr, nullptr, 1, kw, nb, sc, cfg, trace, stream);
+        rc = launch_wave(dtype, &pr, nullptr, nullptr, 1, kw + 1, nb, sc, cfg, trace, stream);
         if (rc != CHM_OK) return rc;
     }
     return CHM_OK;

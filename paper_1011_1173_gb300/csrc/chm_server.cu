@@ -342,10 +342,10 @@ int create(size_t budget, int dtype, int max_inflight, Server **out)
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost(&sl.h_probs, kMaxProbsPerLaunch * sizeof(Prob)) != cudaSuccess ||
-            cudaMallocHost(&sl.h_pair, kMaxProbsPerLaunch * kMaxWaves * sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&sl.h_pair, kMaxProbsPerLaunch * (kMaxWaves + 1) * sizeof(int)) != cudaSuccess ||
             cudaMallocHost(&sl.h_info, 2 * kMaxProbsPerLaunch * sizeof(long long)) != cudaSuccess ||
             cudaMalloc(&sl.d_probs, kMaxProbsPerLaunch * sizeof(Prob)) != cudaSuccess ||
-            cudaMalloc(&sl.d_pair, kMaxProbsPerLaunch * kMaxWaves * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&sl.d_pair, kMaxProbsPerLaunch * (kMaxWaves + 1) * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&sl.d_info, 2 * kMaxProbsPerLaunch * sizeof(long long)) != cudaSuccess)
             rc = CHM_ERR_NOMEM;
     }

@@ -43,8 +43,9 @@
 // always progresses.  Every wait is bounded (%globaltimer).
 //
 // Storage between waves of one launch: the diagonal holds true values, an
-// off-diagonal L_ij is held as S_ij = L_ij / e_i; the last wave of a problem
-// in the launch stores true values again.
+// off-diagonal L_ij is held as S_ij = L_ij / e_i.  Each problem's last pair
+// is a final pass that multiplies the last wave's scales back in, trailing
+// that wave tile by tile.
 #pragma once
 
 #include "chm_device.cuh"
@@ -72,7 +73,8 @@ struct Wave {
     const T *V;                 // column q of the problem's V
     long long n, ld;
     int nb, q, pair;
-    bool last, has_next;
+    bool has_next;
+    bool unscale;               // the problem's final pass: rows times the last wave's scale
     double sg;                  // +1 update, -1 downdate
     CoefRow<T> *coef;           // [nb][kW] this wave
     ChainRow *chain;            // [nb][kW] this wave's output row data
@@ -106,8 +108,8 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.nb = nb;
     w.q = q;
     w.pair = j;
-    w.last = q == pr.k - 1;
     w.has_next = q + 1 < pr.k;
+    w.unscale = q == pr.k;  // the pair after the last wave; it owns no scratch of its own
     w.sg = ((pr.down_mask >> q) & 1ull) ? -1.0 : 1.0;
     w.coef = reinterpret_cast<CoefRow<T> *>(d + rc.coef);
     w.chain = reinterpret_cast<ChainRow *>(d + rc.chain);
@@ -477,10 +479,6 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
                 __stcg(rt + (size_t)r * kW + lane, active ? -(double)S[r] * ch[r].e1 : 0.0);
         }
         if (active) {
-            if (w.last) {
-#pragma unroll
-                for (int r = 0; r < kW; ++r) S[r] *= cf[r].e1;
-            }
 #pragma unroll
             for (int r = 0; r < kW; ++r) tile[lane][r] = S[r];
         }
@@ -510,6 +508,63 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
         if (lane == 0) st_release_gpu(prog_me, ep64 + p + 1);
     }
     CHM_TRACE(3);
+}
+
+// ---------------------------------------------------------------- final pass
+
+// Between the waves of a launch an off-diagonal entry is stored as
+// S_ij = L_ij / e_i.  After a problem's last wave the true values are
+// S_ij e'_i, e'_i the last wave's row scale; this pass multiplies them in,
+// tile by tile as the last wave releases each tile, so that the waves
+// themselves never spend FP64 issue on it.  (The row scale is taken in the
+// storage type, as the rotations' coefficients are.)
+
+// Column block b's off-diagonal tiles, row by row (lane = row).
+template <typename T>
+__device__ void unscale_task(const Wave<T> &w, int b)
+{
+    const int lane = threadIdx.x & 31;
+    const SyncArgs &sy = w.sync;
+    const long long n = w.n, ld = w.ld;
+    const long long c0 = (long long)b * kW;
+    const int ncols = (int)min((long long)kW, n - c0);
+    const long long ep64 = (long long)sy.epoch << 32;
+    const long long who = b;
+    for (int p = 0; p < b; ++p) {
+        CHM_WARP_WAIT(wait_ge(sy, w.progress_prev + b, ep64 + p + 1, who));
+        const T e = (T)__ldcg(&w.chain_in[(size_t)p * kW + lane].e1);
+        T *src = w.L + (long long)p * kW + lane;
+        T x[kW];
+#pragma unroll
+        for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
+#pragma unroll
+        for (int c = 0; c < kW; ++c)
+            if (c < ncols) __stcg(src + (c0 + c) * ld, x[c] * e);
+    }
+}
+
+// The strictly upper part of the diagonal blocks, after the last wave has
+// released each block; block b goes to warp b % 4 of the wave block.
+template <typename T>
+__device__ void unscale_diag(const Wave<T> &w, int warp)
+{
+    const int lane = threadIdx.x & 31;
+    const SyncArgs &sy = w.sync;
+    const long long n = w.n, ld = w.ld;
+    const int epoch = sy.epoch;
+    const long long who = -1;
+    for (int b = warp; b < w.nb; b += 4) {
+        const long long c0 = (long long)b * kW;
+        const int ncols = (int)min((long long)kW, n - c0);
+        CHM_WARP_WAIT(wait_eq(sy, w.dflag_prev + b, epoch, who));
+        if (lane < ncols) {
+            const T e = (T)__ldcg(&w.chain_in[(size_t)b * kW + lane].e1);
+            T *src = w.L + c0 + lane;
+#pragma unroll
+            for (int c = 0; c < kW; ++c)
+                if (lane < c && c < ncols) __stcg(src + (c0 + c) * ld, __ldcg(src + (c0 + c) * ld) * e);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- wave block
@@ -822,11 +877,6 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
                 uh = fma(-c.b, Sv[r], uh);
             }
         }
-        if (w.last) {
-#pragma unroll
-            for (int r = 0; r < kW; ++r)
-                if (r < lane) Sv[r] *= S.cf[s][r].e1;
-        }
 #pragma unroll
         for (int r = 0; r < kW; ++r)
             if (r < lane) S.DT[lane][r] = Sv[r];
@@ -959,7 +1009,8 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             const int j = s_pair;
             if (j < 0) break;
             const Wave<T> w = make_wave(P, j);
-            if (warp == 0) wave_chain<T>(w, S);
+            if (w.unscale) unscale_diag<T>(w, warp);
+            else if (warp == 0) wave_chain<T>(w, S);
             else if (warp == 1) wave_coef<T>(w, S);
             else if (warp == 2) wave_diag<T>(w, S);
             else wave_io<T>(w, S);
@@ -978,7 +1029,9 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             int b = -1;
             const int j = take_task(P, group, &b);
             if (j >= 0) {
-                sweep_task<T>(make_wave(P, j), b, sm);
+                const Wave<T> w = make_wave(P, j);
+                if (w.unscale) unscale_task<T>(w, b);
+                else sweep_task<T>(w, b, sm);
                 idle_since = -1;
                 idle_iters = 0;
                 continue;
