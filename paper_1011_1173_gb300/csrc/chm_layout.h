@@ -75,8 +75,9 @@ CHM_HD inline size_t prob_iflags(int nb, int k) { return ((size_t)(2 * k + 1) * 
 // [nb][kW][2] the carry u_hat at the diagonal block (payload: the high and
 // the low half of a double).  A reader takes a carry once both halves carry
 // the current epoch, so the writer needs no fence.
+// The last word counts the final pass's finished column tasks (payload).
 constexpr int kTagsPerBlock = 1 + 4 * kW;
-CHM_HD inline size_t prob_progress(int nb, int k) { return ((size_t)k * nb * kTagsPerBlock + 31) & ~(size_t)31; }
+CHM_HD inline size_t prob_progress(int nb, int k) { return ((size_t)k * nb * kTagsPerBlock + 1 + 31) & ~(size_t)31; }
 
 // One problem of a launch (L and V of the launch's element type).
 struct Prob {

@@ -87,6 +87,7 @@ struct Wave {
     long long *progress;
     const long long *progress_prev;
     long long *ztag, *ctag;     // [nb][kW][2] tagged carries z and u_hat
+    long long *final_done;      // final pass: tagged count of finished column tasks
     long long *trace_sweep, *trace_wave;  // this pair's rows, or null
     int skip_publish;                     // test hook (see Launch)
     SyncArgs sync;
@@ -129,6 +130,7 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.progress_prev = q > 0 ? w.progress - nb : nullptr;
     w.ztag = pr.progress + (size_t)pr.k * nb + (size_t)q * nb * kW * 2;
     w.ctag = pr.progress + (size_t)pr.k * nb * (1 + kW * 2) + (size_t)q * nb * kW * 2;
+    w.final_done = pr.progress + (size_t)pr.k * nb * kTagsPerBlock;
     if (P.trace) {
         const size_t row = (size_t)j * P.nbmax * kTracePoints;
         w.trace_sweep = P.trace + row;
@@ -541,6 +543,16 @@ __device__ void unscale_task(const Wave<T> &w, int b)
         for (int c = 0; c < kW; ++c)
             if (c < ncols) __stcg(src + (c0 + c) * ld, x[c] * e);
     }
+    // count this task done (the pair's wave block waits for all of them);
+    // the count word is tagged with the epoch, so it restarts every launch
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) {
+        // lift a count left by an earlier launch to (epoch << 32), then count
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(w.final_done);
+        atomicMax(cnt, (unsigned long long)ep64);
+        atomicAdd(cnt, 1ull);
+    }
 }
 
 // The strictly upper part of the diagonal blocks, after the last wave has
@@ -564,6 +576,12 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
             for (int c = 0; c < kW; ++c)
                 if (lane < c && c < ncols) __stcg(src + (c0 + c) * ld, __ldcg(src + (c0 + c) * ld) * e);
         }
+    }
+    // the pair is done only when its column tasks are: idle sweep warps stop
+    // once every pair is done, so none of those tasks may still be unclaimed
+    if (warp == 0 && w.nb > 1) {
+        const long long want = ((long long)epoch << 32) + (w.nb - 1);
+        CHM_WARP_WAIT(wait_ge(sy, w.final_done, want, who));
     }
 }
 
@@ -780,17 +798,18 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
         const double c = ratio * rc;
         const CoefRow<T> cr{(T)(sgd * p * rowd.ie1), (T)(p * rowd.e1 * iTn), (T)(rowd.e1 * rc), T(0)};
         const ChainRow nrow{rowd.e1 * rc, rowd.ie1 * c, rowd.d1 * c, rowd.id1 * rc};
-        S.cf[s][lane] = cr;
-        S.cnew[s][lane] = nrow;
-        __syncwarp();
-        if (lane == 0) seq_post(&S.bseq, b + 1);
+        // the block's global row data first: everything warps C and D later
+        // release at GPU scope (the next wave's inputs) is ordered after it
         if (active) {
             const size_t prow = (size_t)b * kW + lane;
             st_coef(w.coef + prow, cr);
             st_chain(w.chain + prow, nrow);
         }
         if (lane == 0) __stcg(w.tend + b, Tlast);
+        S.cf[s][lane] = cr;
+        S.cnew[s][lane] = nrow;
         __syncwarp();
+        if (lane == 0) seq_post(&S.bseq, b + 1);
         if (lane == 0 && b != w.skip_publish) st_release_gpu(w.pflag + b, epoch);
         CHM_WTRACE(b, 5);
         Tend = Tlast;

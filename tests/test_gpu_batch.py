@@ -178,3 +178,35 @@ def test_batch_rejects_bad_arguments():
     plan = chm.BatchPlan([10], [10], [1])
     assert plan.execute([None], [None]) == chm.CHM_ERR_ARG
     plan.close()
+
+
+def test_batch_many_groups_many_factors_match_solo_calls():
+    """Many factors under the default many-group configuration, several
+    executions: every factor's final pass (the last wave's scales) must run
+    in full before the launch ends."""
+    rng = np.random.default_rng(77)
+    count = 128
+    ns = np.exp(rng.uniform(np.log(64), np.log(2048), count)).astype(int).tolist()
+    ks = rng.choice([1, 4, 16], count).tolist()
+    sg = rng.choice([1, -1], count).tolist()
+    Ls = [inputs.random_factor(n, 500 + i, device="cuda") for i, n in enumerate(ns)]
+    Vs = [inputs.update_block(n, k, 500 + i, device="cuda", scale=0.2 / np.sqrt(n * k))
+          for i, (n, k) in enumerate(zip(ns, ks))]
+    L0 = [L.clone() for L in Ls]
+    fwd = chm.BatchPlan(ns, ns, ks, sg)
+    inv = chm.BatchPlan(ns, ns, ks, [-s for s in sg])
+    for r in range(3):
+        assert fwd.execute(Ls, Vs) == chm.CHM_OK
+        assert inv.execute(Ls, Vs) == chm.CHM_OK
+    assert fwd.execute(Ls, Vs) == chm.CHM_OK
+    assert fwd.status()[0] == chm.CHM_OK and inv.status()[0] == chm.CHM_OK
+    fwd.close()
+    inv.close()
+    for i in range(count):
+        solo = L0[i].clone()
+        for r in range(3):
+            assert chm.modify(solo, Vs[i], sg[i]) == chm.CHM_OK
+            assert chm.modify(solo, Vs[i], -sg[i]) == chm.CHM_OK
+        assert chm.modify(solo, Vs[i], sg[i]) == chm.CHM_OK
+        assert torch.equal(solo, Ls[i]), (i, ns[i], ks[i])
+    assert chm.status_sync()[0] == chm.CHM_OK
