@@ -276,6 +276,32 @@ const char *chm_status_string(int status);
 int chm_version(void);
 
 /*
+ * Microbenchmarks of the hardware facts the kernel is designed around
+ * (diagnostics; the up/downdate entry points never call them).  Runs on the
+ * current device, allocates and frees its own buffers, synchronises.
+ *   which   one of chm_microbench_kind
+ *   out     HOST array of at least 2 doubles:
+ *     CHM_MB_FP64_RATE / CHM_MB_FP32_RATE  {T FMA/s for the GPU, per SM}
+ *     CHM_MB_FP64_WARP       {cycles per FP64 FMA of one warp issuing
+ *                             independent FMAs, cycles per dependent FMA}
+ *     CHM_MB_SHFL_SPLIT      {cycles of 32 dependent shuffles in a converged
+ *                             warp, the same after a wait run by lane 0 alone}
+ *     CHM_MB_HBM_COPY        {GB/s of a 2 GiB device copy (read + write), ms}
+ *     CHM_MB_FLAG_ROUND_TRIP {microseconds per release/acquire round trip
+ *                             between two thread blocks, 1 if a wait gave up}
+ * Returns CHM_OK, CHM_ERR_ARG, CHM_ERR_NOMEM or CHM_ERR_CUDA.
+ */
+typedef enum {
+    CHM_MB_FP64_RATE = 0,
+    CHM_MB_FP32_RATE = 1,
+    CHM_MB_FP64_WARP = 2,
+    CHM_MB_SHFL_SPLIT = 3,
+    CHM_MB_HBM_COPY = 4,
+    CHM_MB_FLAG_ROUND_TRIP = 5
+} chm_microbench_kind;
+int chm_microbench(int which, double *out, int nout);
+
+/*
  * Diagnostics.  When the environment variable CHM_TRACE is set to 1 before
  * the first call, every launch of the plain entry points records 16 int64
  * stamps of the device's %globaltimer (ns) at fixed points per (wave, column

@@ -78,6 +78,7 @@ def load(build_if_missing: bool = False):
         "chm_server_get_factor": ([vp, i64, vp, i64], i32),
         "chm_server_stats": ([vp, vp], i32),
         "chm_server_destroy": ([vp], i32),
+        "chm_microbench": ([i32, vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -183,6 +184,21 @@ def chm_server_stats(srv, out):
 
 def chm_server_destroy(srv):
     return load().chm_server_destroy(srv)
+
+
+def chm_microbench(which, out, nout):
+    return load().chm_microbench(which, out, nout)
+
+
+MICROBENCH = {"fp64_rate": 0, "fp32_rate": 1, "fp64_warp": 2, "shfl_split": 3, "hbm_copy": 4,
+              "flag_round_trip": 5}
+
+
+def microbench(name):
+    """Run one microbenchmark (chm_microbench); returns its two numbers."""
+    out = (ctypes.c_double * 2)()
+    check(chm_microbench(MICROBENCH[name], ctypes.cast(out, ctypes.c_void_p), 2), "chm_microbench")
+    return float(out[0]), float(out[1])
 
 
 # ---------------------------------------------------------------- tensor helpers
