@@ -95,6 +95,19 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate(ms_local, bytes_per_rank, world, device="cpu"):
+    """Whole-job throughput of `world` replicas: every rank's bytes over the
+    slowest rank's time (max over ranks, through torch.distributed when
+    world > 1).  Returns (GB/s, max ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * bytes_per_rank / (ms_max / 1e3) / 1e9, ms_max
+
+
 def percentile(xs, q):
     import numpy as np
     return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else None
@@ -457,12 +470,8 @@ def main():
 
     ms = sum(a.elapsed_time(b) for a, b in step_ev) / len(step_ev)
     launch_ms = sum(a.elapsed_time(b) for a, b in launch_ev) / len(launch_ev)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     bytes_step = 2 * alg_bytes(n, k)
-    value = world * bytes_step / (ms_max / 1e3) / 1e9
+    value, ms_max = aggregate(ms, bytes_step, world, dev)
 
     # End to end through the public API with host buffers: pinned host L and
     # V copied in, update + downdate, the modified factor copied back.
@@ -496,13 +505,11 @@ def main():
         torch.cuda.synchronize()
         chm.check(chm.status_sync(stream)[0], "e2e status")
         e2e_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_value, e2e_max = aggregate(e2e_ms, bytes_step, world, dev)
         h2d = Lh0.numel() * Lh0.element_size() + Vh.numel() * Vh.element_size()
-        e2e = {"value": world * bytes_step / (float(te.item()) / 1e3) / 1e9, "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Lh_out.numel() * Lh_out.element_size(),
-               "ms_per_step": float(te.item())}
+               "ms_per_step": e2e_max}
 
     kernel = "wave_kernel<double>"
     achieved = alg_flops(n, k) / (launch_ms / 1e3) / 1e12
