@@ -19,9 +19,19 @@
  *     column are left bit-for-bit unchanged.  V is column-major n x k with
  *     leading dimension ldv (ldv = n in the short forms); column p is the
  *     p-th update vector.  V is read only.
- *   - Pointers.  L, V and d_info are DEVICE pointers owned by the caller
- *     (the library never frees them).  L and V must be aligned to their
- *     element size.  sigma arrays are HOST pointers.
+ *   - Pointers.  L, V and d_info are pointers the current device can
+ *     dereference, owned by the caller (the library never frees them):
+ *     device memory of the current device, managed memory, or page-locked
+ *     host memory (cudaHostAlloc, cudaHostRegister) mapped at the same
+ *     address, which every unified-addressing system provides.  Pageable
+ *     host memory and other devices' memory are rejected with CHM_ERR_ARG
+ *     before any work is enqueued.  With L in page-locked host memory the
+ *     kernel reads and writes the factor in place across the CPU-GPU link
+ *     and the device holds only the O(n k) workspace of chm_workspace_bytes:
+ *     the paper's property that device memory grows as O(n), not O(n^2)
+ *     (abstract, Sec. 5), so a factor may be as large as host memory.
+ *     L and V must be aligned to their element size.  sigma arrays are HOST
+ *     pointers.
  *   - Precision.  CHM_F64: L and V are double; all arithmetic in double.
  *     CHM_F32_MIXED: L and V are float; the Apply sweep runs in float while
  *     every Compute step (the square root and the c, s ratios) runs in
@@ -38,10 +48,12 @@
  *     L_ii^2 + sigma V_i^2 <= 0 or a non-finite value; info = the 0-based
  *     row) and CHM_ERR_TIMEOUT (a wait between thread blocks exceeded its
  *     bound; info = the column block).  After either, L is unspecified.
- *   - Memory.  The library keeps a small workspace per (device, stream):
- *     rotation panels (n * 512 bytes), flags and the status word.  It is
- *     allocated on the first call that needs a larger one; later calls of
- *     the same or smaller size allocate nothing.
+ *   - Memory.  The library keeps a workspace per (device, stream): per
+ *     vector of a launch (at most 64 per launch) rotation panels, ratio
+ *     tiles and flags of about 19 KB per 32 rows, and the status word
+ *     (chm_workspace_bytes gives the total).  It is allocated on the first
+ *     call that needs a larger one; later calls of the same or smaller size
+ *     allocate nothing.
  *
  * Thread safety: entry points may be called from several host threads; calls
  * on the same stream from different threads must be ordered by the caller.
@@ -259,6 +271,18 @@ int chm_server_drain(void *srv, double timeout_s);
 int chm_server_get_factor(void *srv, int64_t fid, void *out, int64_t ld);
 int chm_server_stats(void *srv, int64_t *out);
 int chm_server_destroy(void *srv);
+
+/*
+ * Device memory that chm_update / chm_downdate / chm_modify_ex hold for one
+ * factor of order n modified by k vectors (the per-stream workspace; the
+ * factor and V themselves are the caller's).  It grows as O(n min(k, 64)):
+ * with L in page-locked host memory this is all the device memory a
+ * modification needs (abstract, Sec. 5: O(n) device memory).  Host only.
+ *   bytes  receives the size
+ * Returns CHM_OK or CHM_ERR_ARG (n or k negative or n > 2^26, bad dtype,
+ * bytes NULL).
+ */
+int chm_workspace_bytes(int64_t n, int64_t k, int dtype, size_t *bytes);
 
 /*
  * Synchronises `stream`, then reads and clears the status word of the

@@ -79,6 +79,7 @@ def load(build_if_missing: bool = False):
         "chm_server_stats": ([vp, vp], i32),
         "chm_server_destroy": ([vp], i32),
         "chm_microbench": ([i32, vp, i32], i32),
+        "chm_workspace_bytes": ([i64, i64, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +191,17 @@ def chm_microbench(which, out, nout):
     return load().chm_microbench(which, out, nout)
 
 
+def chm_workspace_bytes(n, k, dtype, out):
+    return load().chm_workspace_bytes(n, k, dtype, out)
+
+
+def workspace_bytes(n, k, dtype=CHM_F64) -> int:
+    """Device bytes a single-factor modification of order n by k vectors holds."""
+    out = ctypes.c_size_t()
+    check(chm_workspace_bytes(int(n), int(k), int(dtype), ctypes.byref(out)), "chm_workspace_bytes")
+    return int(out.value)
+
+
 MICROBENCH = {"fp64_rate": 0, "fp32_rate": 1, "fp64_warp": 2, "shfl_split": 3, "hbm_copy": 4,
               "flag_round_trip": 5}
 
@@ -212,8 +224,8 @@ def dtype_code(t: torch.Tensor) -> int:
 
 
 def _check_layout(L: torch.Tensor, V: torch.Tensor, n):
-    if not (L.is_cuda and V.is_cuda):
-        raise ValueError("L and V must be CUDA tensors")
+    if not all(t.is_cuda or t.is_pinned() for t in (L, V)):
+        raise ValueError("L and V must be CUDA tensors or page-locked host tensors")
     if L.dtype != V.dtype:
         raise TypeError("L and V must have the same dtype")
     if L.dim() != 2 or V.dim() != 2 or not L.is_contiguous() or not V.is_contiguous():

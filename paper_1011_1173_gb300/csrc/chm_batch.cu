@@ -157,6 +157,9 @@ int execute(Plan *p, void *const *L, const void *const *V, cudaStream_t stream)
     for (size_t q = 0; q < np; ++q) {
         const int i = p->order[q];
         if (!L[i] || !V[i] || (uintptr_t)L[i] % elt || (uintptr_t)V[i] % elt) return CHM_ERR_ARG;
+        int rc = check_reachable(L[i]);
+        if (rc == CHM_OK) rc = check_reachable(V[i]);
+        if (rc != CHM_OK) return rc;
         Prob pr = p->tmpl[q];
         pr.L = L[i];
         pr.V = V[i];

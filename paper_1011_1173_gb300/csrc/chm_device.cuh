@@ -125,4 +125,63 @@ __device__ __forceinline__ bool bounded_wait(const SyncArgs &s, F ready, A acqui
     }
 }
 
+// Wait helpers.
+__device__ __forceinline__ bool wait_eq(const SyncArgs &s, const int *p, int want, long long who)
+{
+    return bounded_wait(s, [&] { return ld_acquire_gpu(p) == want; }, [] {}, who);
+}
+__device__ __forceinline__ bool wait_ge(const SyncArgs &s, const long long *p, long long want,
+                                        long long who)
+{
+    return bounded_wait(s, [&] { return ld_acquire_gpu(p) >= want; }, [] {}, who);
+}
+
+
+// A double published as two tagged words, (epoch << 32) | high half and
+// (epoch << 32) | low half: each 8-byte store is single-copy atomic, so a
+// reader that sees both tags equal to the current epoch has the value, and
+// the writer needs no fence or flag.
+__device__ __forceinline__ void put_tagged(long long *w2, double v, long long ep64)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    __stcg(w2, ep64 | (long long)(u >> 32));
+    __stcg(w2 + 1, ep64 | (long long)(u & 0xffffffffull));
+}
+// Read a tagged double: true (and *v) once both words carry `ep64`.
+__device__ __forceinline__ bool get_tagged(const long long *w2, long long ep64, double *v)
+{
+    const long long h = ld_relaxed_gpu(w2), l = ld_relaxed_gpu(w2 + 1);
+    if ((h & ~0xffffffffll) != ep64 || (l & ~0xffffffffll) != ep64) return false;
+    *v = __longlong_as_double((long long)(((unsigned long long)h << 32) | ((unsigned long long)l & 0xffffffffull)));
+    return true;
+}
+
+// The whole warp waits (bounded) until every lane's tagged double carries
+// `ep64`; every exit is decided for the warp as a whole.  Returns false if
+// the launch is being aborted or the wait ran out of time (recorded).
+__device__ __forceinline__ bool warp_wait_tagged(const SyncArgs &s, const long long *w2, long long ep64,
+                                                 long long who, double *v)
+{
+    const long long t0 = global_ns();
+    unsigned ns = 16;
+    for (unsigned it = 0;; ++it) {
+        if (__all_sync(0xffffffffu, get_tagged(w2, ep64, v))) return true;
+        if ((it & 15u) == 15u) {
+            const int lane = threadIdx.x & 31;
+            int stop = 0;
+            if (lane == 0) {
+                if (aborted(s)) {
+                    stop = 1;
+                } else if (global_ns() - t0 > s.timeout_ns || it > (1u << 26)) {
+                    record_error(s, kStatusTimeout, who);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+}
+
 }  // namespace chm

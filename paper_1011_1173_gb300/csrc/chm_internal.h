@@ -74,6 +74,13 @@ int info_init(long long *d_info, int count, cudaStream_t stream);
 
 // Allocate (and zero) a scratch with at least the given capacities.
 int scratch_alloc(Scratch *sc, size_t iflags, size_t progress, size_t data);
+// CHM_OK if the current device can dereference p at that address (its own
+// device memory, managed memory, or page-locked host memory mapped at the
+// same address); CHM_ERR_ARG otherwise (pageable host memory, another
+// device's memory, an unknown address).
+int check_reachable(const void *p);
+// Device bytes the single-factor entry points hold for order n, k vectors.
+size_t single_workspace_bytes(long long n, long long k);
 void scratch_free(Scratch *sc);
 
 }  // namespace chm

@@ -203,6 +203,33 @@ static int ctl_init(int *ctl, long long *status)
     return CHM_OK;
 }
 
+int check_reachable(const void *p)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorInvalidValue ? CHM_ERR_ARG : CHM_ERR_CUDA;
+    }
+    switch (a.type) {
+    case cudaMemoryTypeDevice: return a.device == dev ? CHM_OK : CHM_ERR_ARG;
+    case cudaMemoryTypeManaged: return CHM_OK;
+    case cudaMemoryTypeHost: return a.devicePointer == p ? CHM_OK : CHM_ERR_ARG;
+    default: return CHM_ERR_ARG;
+    }
+}
+
+size_t single_workspace_bytes(long long n, long long k)
+{
+    if (n <= 0 || k <= 0) return 0;
+    const ProbShape sh{n, (int)std::min<long long>(k, kMaxWaves)};
+    const ScratchNeed need = scratch_need(&sh, 1);
+    return kCtlInts * sizeof(int) + 2 * sizeof(long long) + std::max(need.iflags, (size_t)4096) * sizeof(int) +
+           std::max(need.progress, (size_t)1024) * sizeof(long long) + need.data;
+}
+
 int scratch_alloc(Scratch *sc, size_t iflags, size_t progress, size_t data)
 {
     if (!sc->ctl) {
@@ -381,6 +408,7 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
     int rc = check_args(L, n, ld, V, ldv, k, sigma, sign, dtype);
     if (rc != CHM_OK) return rc;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
+    if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
     const int kw_max = (int)std::min<long long>(k, kMaxWaves);
@@ -471,6 +499,7 @@ static int modify_noalloc(void *L, long long n, long long ld, const void *V, lon
     if (rc != CHM_OK) return rc;
     if (n > kNoAllocMaxN) return CHM_ERR_BUDGET;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
+    if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;
     const int kw_max = std::min<int>(noalloc_waves(n), (int)std::min<long long>(k, kMaxWaves));
     if (kw_max < 1) return CHM_ERR_BUDGET;
     int dev = 0;
@@ -513,6 +542,14 @@ int chm_modify_noalloc(void *L, int64_t n, int64_t ld, const void *V, int64_t ld
 {
     return chm::modify_noalloc(L, n, ld, V, ldv, k, sigma, sign, dtype, (cudaStream_t)stream,
                                reinterpret_cast<long long *>(d_info));
+}
+
+int chm_workspace_bytes(int64_t n, int64_t k, int dtype, size_t *bytes)
+{
+    if (!bytes || n < 0 || k < 0 || n > (1ll << 26)) return CHM_ERR_ARG;
+    if (dtype != CHM_F64 && dtype != CHM_F32_MIXED) return CHM_ERR_ARG;
+    *bytes = chm::single_workspace_bytes(n, k);
+    return CHM_OK;
 }
 
 int chm_status_sync(chm_stream_t stream, int64_t *info)

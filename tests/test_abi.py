@@ -99,3 +99,22 @@ def test_server_argument_errors_without_gpu():
     assert chm.chm_server_get_factor(None, 0, None, 1) == E
     assert chm.chm_server_stats(None, None) == E
     assert chm.chm_server_destroy(None) == E
+
+
+def test_workspace_bytes_grow_as_n_times_k():
+    """Host-only sizing: the device workspace of a single-factor modification
+    is O(n min(k, 64)), far below the n^2 factor (so a factor kept in host
+    memory needs only this much device memory)."""
+    ws = chm.workspace_bytes
+    n = 1 << 16
+    assert ws(0, 5) == 0 and ws(n, 0) == 0
+    assert 1.95 <= ws(2 * n, 8) / ws(n, 8) <= 2.05
+    assert 1.9 <= ws(n, 16) / ws(n, 8) <= 2.05
+    assert ws(n, 100) == ws(n, 64)
+    assert ws(n, 16) < 8 * n * n / 40
+    assert ws(n, 16, chm.CHM_F32_MIXED) == ws(n, 16)
+    for bad in ((-1, 1), (1, -1), (1 << 27, 1)):
+        with pytest.raises(chm.ChmError):
+            ws(*bad)
+    with pytest.raises(chm.ChmError):
+        ws(10, 1, 9)
