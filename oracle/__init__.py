@@ -12,6 +12,10 @@ Two implementations of the same serial algorithm (Algorithm 1):
   bit-identical to the C routine (numpy rounds every elementwise operation
   separately, as the C build does).
 
+``solve`` (``orc_solve`` in the C file) solves with a factor, the use the
+factor is kept for (Sec. 1): forward substitution with L^T, then back
+substitution with L.
+
 Layout convention for every function: ``L`` is an (n, n) array holding the
 column-major upper-triangular factor, i.e. a C-contiguous array whose ROW j is
 column j of L (so ``L_cm[j, i]`` is L_ij).  Helpers ``to_cm``/``from_cm``
@@ -62,6 +66,8 @@ def _load():
             f.restype = ctypes.c_int
         lib.orc_modify_a.argtypes = [vp, i64, i64, vp, i64, i64, vp, ctypes.POINTER(i64)]
         lib.orc_modify_a.restype = ctypes.c_int
+        lib.orc_solve.argtypes = [vp, i64, i64, vp, i64, i64, ctypes.POINTER(i64)]
+        lib.orc_solve.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -128,6 +134,20 @@ def modify_mixed32(L_cm, V_cm, sigma, n=None, m_rows=None):
     st = _load().orc_modify_mixed32(L_cm.ctypes.data, n, L_cm.shape[1], V_cm.ctypes.data,
                                     V_cm.shape[1], k, sig.ctypes.data,
                                     -1 if m_rows is None else m_rows, ctypes.byref(info))
+    return st, info.value
+
+
+def solve(L_cm, B_cm, n=None):
+    """X = (L^T L)^{-1} B in place on ``B_cm`` (float64): forward substitution
+    with L^T, then back substitution with L (``orc_solve``).
+
+    ``L_cm`` is (n, ld) with row j holding column j of L; ``B_cm`` is
+    (nrhs, ldb) with row r holding column r of B.  Returns (status, info)."""
+    L_cm, B_cm = _prep(L_cm, B_cm, np.float64)
+    n = L_cm.shape[0] if n is None else n
+    info = ctypes.c_int64(-1)
+    st = _load().orc_solve(L_cm.ctypes.data, n, L_cm.shape[1], B_cm.ctypes.data, B_cm.shape[1],
+                           B_cm.shape[0], ctypes.byref(info))
     return st, info.value
 
 

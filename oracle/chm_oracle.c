@@ -202,3 +202,43 @@ int orc_modify_mixed32(float *L, int64_t n, int64_t ld, const float *V, int64_t 
     free(W);
     return ORC_OK;
 }
+
+/*
+ * Solve with the factor.  The factor is maintained so that systems with
+ * A = L^T L can be solved cheaply (Sec. 1); this overwrites the n x nrhs
+ * column-major B (leading dimension ldb) with X = A^{-1} B by the two
+ * textbook triangular solves, in plain double, one column of B at a time:
+ *   forward substitution with L^T (lower):  y_i = (b_i - sum_{j<i} L_ji y_j) / L_ii,
+ *   back substitution with L (upper):       x_i = (y_i - sum_{j>i} L_ij x_j) / L_ii,
+ * each sum accumulated in ascending j.  If some L_ii <= 0 or is not finite
+ * (L is then not a Cholesky factor) it returns ORC_ERR_NOT_PD with *info = i
+ * and leaves B unchanged.
+ */
+int orc_solve(const double *L, int64_t n, int64_t ld, double *B, int64_t ldb, int64_t nrhs,
+              int64_t *info)
+{
+    if (info) *info = -1;
+    if (n < 0 || nrhs < 0 || ld < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return ORC_ERR_ARG;
+    if (n == 0 || nrhs == 0) return ORC_OK;
+    if (!L || !B) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!finite_pos(L[i + i * ld])) {
+            if (info) *info = i;
+            return ORC_ERR_NOT_PD;
+        }
+    }
+    for (int64_t r = 0; r < nrhs; ++r) {
+        double *x = B + r * ldb;
+        for (int64_t i = 0; i < n; ++i) {
+            double s = x[i];
+            for (int64_t j = 0; j < i; ++j) s -= L[j + i * ld] * x[j];
+            x[i] = s / L[i + i * ld];
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {
+            double s = x[i];
+            for (int64_t j = i + 1; j < n; ++j) s -= L[i + j * ld] * x[j];
+            x[i] = s / L[i + i * ld];
+        }
+    }
+    return ORC_OK;
+}

@@ -335,3 +335,88 @@ def test_torch_generator_shapes():
     assert torch.all(L[:, 10:] == 0)
     assert torch.all(torch.triu(L[:, :10], 1) == 0)  # strictly lower part of L is zero
     assert torch.all(torch.diagonal(L[:, :10]) > 0)
+
+
+# ---------------------------------------------------------------- solve with the factor
+
+def _exact_solve(U, B):
+    """X with (U^T U) X = B in exact rational arithmetic (Gauss-Jordan on the
+    normal matrix, independent of triangular substitution)."""
+    from fractions import Fraction
+    n = U.shape[0]
+    Uf = [[Fraction(int(U[i, j])) for j in range(n)] for i in range(n)]
+    A = [[sum(Uf[m][i] * Uf[m][j] for m in range(n)) for j in range(n)] for i in range(n)]
+    M = [A[i] + [Fraction(int(v)) for v in B[i]] for i in range(n)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        inv = 1 / M[c][c]
+        M[c] = [v * inv for v in M[c]]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c]
+                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    return np.array([[float(v) for v in row[n:]] for row in M])
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (2, 3), (5, 2), (9, 4), (12, 1)])
+def test_solve_exact_rational(n, nrhs):
+    rng = np.random.default_rng(500 + n)
+    U = np.triu(rng.integers(-3, 4, (n, n))).astype(np.float64)
+    U[np.diag_indices(n)] = rng.integers(1, 5, n)
+    B = rng.integers(-5, 6, (n, nrhs)).astype(np.float64)
+    exact = _exact_solve(U, B)
+    X = np.array(B.T, order="C", copy=True)  # B.T may be a view for nrhs == 1
+    st, info = oracle.solve(cm_from_upper(U), X)
+    assert st == 0 and info == -1
+    for r in range(nrhs):
+        scale = max(1.0, np.abs(exact[:, r]).max())
+        assert np.abs(X[r] - exact[:, r]).max() <= 1e-12 * scale
+
+
+def test_solve_closed_forms():
+    n = 17
+    d = np.linspace(0.5, 3.0, n)
+    B = np.arange(2 * n, dtype=np.float64).reshape(2, n) - 7.0
+    X = B.copy()
+    assert oracle.solve(cm_from_upper(np.diag(d)), X)[0] == 0
+    np.testing.assert_allclose(X, B / d ** 2, rtol=1e-15)
+    X = B.copy()
+    assert oracle.solve(cm_from_upper(np.eye(n)), X)[0] == 0
+    assert np.array_equal(X, B)
+    X = np.array([[6.0]])
+    assert oracle.solve(np.array([[2.0]]), X)[0] == 0
+    assert X[0, 0] == 1.5
+
+
+@pytest.mark.parametrize("n,nrhs", [(64, 1), (300, 3)])
+def test_solve_residual_and_library(n, nrhs):
+    L = inputs.spd_factor(n, 40 + n).numpy()
+    U = upper_from_cm(L)
+    A = U.T @ U
+    B = np.random.default_rng(n).standard_normal((n, nrhs))
+    X = np.array(B.T, order="C", copy=True)  # B.T may be a view for nrhs == 1
+    assert oracle.solve(L, X)[0] == 0
+    res = np.abs(A @ X.T - B).max() / (np.abs(A).max() * np.abs(X).max())
+    assert res <= 1e-14
+    ref = np.linalg.solve(A, B)
+    assert np.abs(X.T - ref).max() <= 1e-11 * np.abs(ref).max()
+    # solving with L first (the transposed order) gives another answer
+    wrong = np.linalg.solve(U @ U.T, B)
+    assert np.abs(X.T - wrong).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_solve_errors_and_padding():
+    n = 6
+    U = np.eye(n)
+    U[3, 3] = 0.0
+    B = np.ones((1, n))
+    st, info = oracle.solve(cm_from_upper(U), B)
+    assert st == oracle.ERR_NOT_PD and info == 3
+    assert np.array_equal(B, np.ones((1, n)))
+    # leading dimensions beyond n: padding left alone
+    L = inputs.spd_factor(10, 3, ld=13).numpy()
+    Bp = np.full((2, 12), 9.0)
+    Bp[:, :10] = np.random.default_rng(1).standard_normal((2, 10))
+    st, _ = oracle.solve(L, Bp, n=10)
+    assert st == 0 and np.all(Bp[:, 10:] == 9.0)
