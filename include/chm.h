@@ -273,6 +273,30 @@ int chm_server_stats(void *srv, int64_t *out);
 int chm_server_destroy(void *srv);
 
 /*
+ * Solve with a factor: B <- X = (L^T L)^{-1} B, the use a maintained
+ * Cholesky factor serves (Sec. 1: the factor of A is kept so that systems
+ * with A, here the modified matrix, can be solved).  A forward substitution
+ * with L^T followed by a back substitution with L.
+ *   L      upper factor as for chm_update (read only; device memory or
+ *          page-locked host memory), leading dimension ld >= max(1, n)
+ *   n      order, n >= 0 (n == 0 is a no-op)
+ *   B      n x nrhs column-major, leading dimension ldb >= max(1, n),
+ *          overwritten with X (same memory kinds as L); rows n..ldb-1 are
+ *          left unchanged
+ *   nrhs   number of right-hand sides, nrhs >= 0 (0 is a no-op)
+ *   dtype  CHM_F64: double L and B, double arithmetic.  CHM_F32_MIXED: float
+ *          L and B, every product and sum in double, X rounded to float once
+ * Stream-ordered like chm_update (enqueue it after a modification on the
+ * same stream to solve with the modified factor).  Each 32 x 32 diagonal
+ * block is applied through its explicit inverse.  If some L_ii <= 0 or is
+ * not finite, the stream's status word records CHM_ERR_NOT_PD with that row
+ * and X is unspecified.  Uses the stream's workspace (O(n) bytes).
+ * Returns CHM_OK, CHM_ERR_ARG, CHM_ERR_NOMEM or CHM_ERR_CUDA.
+ */
+int chm_solve(const void *L, int64_t n, int64_t ld, void *B, int64_t ldb, int64_t nrhs, int dtype,
+              chm_stream_t stream);
+
+/*
  * Device memory that chm_update / chm_downdate / chm_modify_ex hold for one
  * factor of order n modified by k vectors (the per-stream workspace; the
  * factor and V themselves are the caller's).  It grows as O(n min(k, 64)):

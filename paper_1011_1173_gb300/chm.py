@@ -80,6 +80,7 @@ def load(build_if_missing: bool = False):
         "chm_server_destroy": ([vp], i32),
         "chm_microbench": ([i32, vp, i32], i32),
         "chm_workspace_bytes": ([i64, i64, i32, vp], i32),
+        "chm_solve": ([vp, i64, i64, vp, i64, i64, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +192,10 @@ def chm_microbench(which, out, nout):
     return load().chm_microbench(which, out, nout)
 
 
+def chm_solve(L, n, ld, B, ldb, nrhs, dtype, stream):
+    return load().chm_solve(L, n, ld, B, ldb, nrhs, dtype, stream)
+
+
 def chm_workspace_bytes(n, k, dtype, out):
     return load().chm_workspace_bytes(n, k, dtype, out)
 
@@ -265,6 +270,16 @@ def downdate(L, V, n=None, stream=None) -> int:
         return modify(L, V, -1, n=n, stream=stream)
     return chm_downdate(L.data_ptr(), n, L.shape[1], V.data_ptr(), V.shape[0], dtype_code(L),
                         _stream_handle(stream))
+
+
+def solve(L: torch.Tensor, B: torch.Tensor, n=None, stream=None) -> int:
+    """Enqueue B <- (L^T L)^{-1} B (chm_solve); returns the call's status.
+
+    ``L`` is the (n, ld) factor storage and ``B`` a contiguous (nrhs, ldb)
+    tensor whose row r is right-hand side r."""
+    n = _check_layout(L, B, n)
+    return chm_solve(L.data_ptr(), n, L.shape[1], B.data_ptr(), B.shape[1], B.shape[0], dtype_code(L),
+                     _stream_handle(stream))
 
 
 def status_sync(stream=None):

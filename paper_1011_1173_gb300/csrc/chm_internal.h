@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <vector>
 
 #include "chm_layout.h"
@@ -81,6 +82,10 @@ int scratch_alloc(Scratch *sc, size_t iflags, size_t progress, size_t data);
 int check_reachable(const void *p);
 // Device bytes the single-factor entry points hold for order n, k vectors.
 size_t single_workspace_bytes(long long n, long long k);
+// Runs fn on the current device's workspace for `stream` (the one the plain
+// entry points use, whose status word chm_status_sync reads), grown first to
+// at least `need`, under the workspaces' lock.
+int with_stream_scratch(cudaStream_t stream, const ScratchNeed &need, const std::function<int(const Scratch &)> &fn);
 void scratch_free(Scratch *sc);
 
 }  // namespace chm

@@ -409,21 +409,28 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
     if (rc != CHM_OK) return rc;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
     if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
     const int kw_max = (int)std::min<long long>(k, kMaxWaves);
     const ProbShape sh{n, kw_max};
     const ScratchNeed need = scratch_need(&sh, 1);
+    return with_stream_scratch(stream, need, [&](const Scratch &sc) {
+        return enqueue_single(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info, sc, kw_max, true);
+    });
+}
+
+int with_stream_scratch(cudaStream_t stream, const ScratchNeed &need, const std::function<int(const Scratch &)> &fn)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     Workspace *w = find_workspace(dev, stream, true);
     if (w->sc.iflags_cap < need.iflags || w->sc.progress_cap < need.progress || w->sc.data_bytes < need.data ||
         !w->sc.ctl) {
         // queued work on this stream may still use the old regions
         if (cudaStreamSynchronize(stream) != cudaSuccess) return CHM_ERR_CUDA;
-        rc = scratch_alloc(&w->sc, need.iflags, need.progress, need.data);
+        const int rc = scratch_alloc(&w->sc, need.iflags, need.progress, need.data);
         if (rc != CHM_OK) return rc;
     }
-    return enqueue_single(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info, w->sc, kw_max, true);
+    return fn(w->sc);
 }
 
 // ---------------------------------------------------------------- no-allocation variant

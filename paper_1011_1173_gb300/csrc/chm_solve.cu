@@ -1,0 +1,414 @@
+// Solve with a factor: B <- (L^T L)^{-1} B, the use a maintained Cholesky
+// factor serves (Sec. 1).  A forward substitution with L^T (lower) followed
+// by a back substitution with L (upper), both blocked by kW = 32 rows, in
+// one persistent launch per group of up to four right-hand sides.
+//
+// Tasks, taken in order from a launch-wide counter by blocks of four warps:
+//   t <  nb: forward task for block b = t:  y_b = D_b^{-T} (b_b - sum_{p<b} L_{p,b}^T y_p)
+//   t >= nb: backward task for b = 2nb-1-t: x_b = D_b^{-1} (y_b - sum_{q>b} L_{b,q} x_q)
+// where D_b is the diagonal block and L_{p,b} the 32 x 32 tile in row block
+// p and column block b.  A task waits only on tasks taken before it, so the
+// launch cannot deadlock whatever the number of resident blocks.
+//
+// Each forward task inverts its diagonal block (U_b = D_b^{-1}, one column
+// per lane) while its other warps accumulate the tiles whose y is already
+// published; the backward task of the block reuses U_b.  The only work
+// between one block's result and the next block's is one tile product and
+// one triangular matrix-vector product, each split over the four warps.
+// Results pass between blocks as epoch-tagged doubles (no fence, no flag).
+#include <float.h>
+
+#include <algorithm>
+
+#include "chm.h"
+#include "chm_device.cuh"
+#include "chm_internal.h"
+#include "chm_layout.h"
+
+namespace chm {
+namespace {
+
+constexpr int kSolveThreads = 128;
+constexpr int kSolveWarps = kSolveThreads / 32;
+constexpr int kSolveRhs = 4;                       // right-hand sides per launch (largest)
+constexpr int kRowsPerWarp = kW / kSolveWarps;     // rows of the critical tile per warp
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct SolveArgs {
+    const T *L;
+    long long n, ld;
+    T *B;
+    long long ldb;
+    int nb;           // blocks of kW rows
+    int nr;           // right-hand sides of this launch (1 .. R)
+    double *inv;      // [nb][kW][kW]: U_b = D_b^{-1}, row i at i * kW
+    int *yflag;       // [nb]: y_b and U_b published (== epoch)
+    long long *ytag;  // [nb][kW][R][2]: y_b as tagged doubles
+    long long *xtag;  // [nb][kW][R][2]: x_b as tagged doubles
+    int *ctl;
+    long long *status;
+    long long timeout_ns;
+};
+
+template <int R>
+struct SolveSmem {
+    double D[kW][kW + 1];  // diagonal block (row, column); identity beyond the order
+    double U[kW][kW + 1];  // its inverse
+    double part[kSolveWarps][R][kW];
+    double rd[kW];         // 1 / D_ii
+};
+
+template <int R>
+__device__ __forceinline__ size_t tag_at(int blk, int i, int r)
+{
+    return (((size_t)blk * kW + i) * R + r) * 2;
+}
+
+// The whole warp waits for the R tagged values of block `blk` (lane i gets
+// row i).  A wait that gives up (recorded as a timeout, or the launch is
+// aborted) yields zeros, so that every warp still reaches the block's
+// barriers; the result is then unspecified and the status says so.
+template <int R>
+__device__ __forceinline__ void wait_block(const SyncArgs &sy, const long long *tags, long long ep64, int blk,
+                                           long long who, double *v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (!warp_wait_tagged(sy, tags + tag_at<R>(blk, lane, r), ep64, who, &v[r])) v[r] = 0.0;
+}
+
+// Sum of the four warps' partial products of row `lane`, for each r.
+template <int R>
+__device__ __forceinline__ double part_sum(const SolveSmem<R> &S, int r, int lane)
+{
+    return (S.part[0][r][lane] + S.part[1][r][lane]) + (S.part[2][r][lane] + S.part[3][r][lane]);
+}
+
+template <typename T, int R>
+__device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long long ep64, int b, SolveSmem<R> &S)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ld = a.ld;
+    const long long c0 = (long long)b * kW;
+    const int nc = (int)min((long long)kW, a.n - c0);
+    const bool active = lane < nc;
+    const long long who = b;
+
+    for (int e = threadIdx.x; e < kW * kW; e += kSolveThreads) {
+        const int i = e & (kW - 1), j = e / kW;
+        double v = 0.0;
+        if (j < nc) {
+            if (i <= j) v = (double)__ldg(a.L + c0 + i + (c0 + j) * ld);
+        } else if (i == j) {
+            v = 1.0;
+        }
+        S.D[i][j] = v;
+    }
+    double rhs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) rhs[r] = (active && r < a.nr) ? (double)a.B[c0 + lane + r * a.ldb] : 0.0;
+    __syncthreads();
+
+    if (warp == 0) {
+        double d = S.D[lane][lane];
+        if (!(d > 0.0 && d <= DBL_MAX)) {  // not a Cholesky factor
+            record_error(sy, kStatusNotPD, c0 + lane);
+            d = 1.0;
+        }
+        S.rd[lane] = 1.0 / d;
+        __syncwarp();
+        // column `lane` of U = D^{-1}: back substitution on D u = e_lane
+        double u[kW];
+#pragma unroll
+        for (int i = kW - 1; i >= 0; --i) {
+            double s = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+            for (int m = i + 1; m < kW; ++m) s = fma(-S.D[i][m], u[m], s);
+            u[i] = s * S.rd[i];
+        }
+        double *inv = a.inv + (size_t)b * kW * kW;
+#pragma unroll
+        for (int i = 0; i < kW; ++i) {
+            S.U[i][lane] = u[i];
+            __stcg(inv + i * kW + lane, u[i]);
+        }
+    }
+
+    // tiles p <= b - 2 of column block b, dealt round-robin to the warps (a
+    // fixed order of the sums: results do not depend on timing); lane =
+    // column of the block, the tile's 32 rows read down the column
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    const T *col = a.L + (c0 + (active ? lane : 0)) * ld;
+    for (int p = warp; p <= b - 2; p += kSolveWarps) {
+        const T *src = col + (long long)p * kW;
+        double t[kW];
+#pragma unroll
+        for (int j = 0; j < kW; ++j) t[j] = active ? (double)__ldg(src + j) : 0.0;
+        double yv[R];
+        wait_block<R>(sy, a.ytag, ep64, p, who, yv);
+#pragma unroll
+        for (int j = 0; j < kW; ++j)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(t[j], __shfl_sync(kFull, yv[r], j), acc[r]);
+    }
+    // tile b - 1, whose y is the last to arrive: its rows split over the warps
+    if (b >= 1) {
+        const T *src = col + (long long)(b - 1) * kW + warp * kRowsPerWarp;
+        double t[kRowsPerWarp];
+#pragma unroll
+        for (int jj = 0; jj < kRowsPerWarp; ++jj) t[jj] = active ? (double)__ldg(src + jj) : 0.0;
+        double yv[R];
+        wait_block<R>(sy, a.ytag, ep64, b - 1, who, yv);
+#pragma unroll
+        for (int jj = 0; jj < kRowsPerWarp; ++jj)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                acc[r] = fma(t[jj], __shfl_sync(kFull, yv[r], warp * kRowsPerWarp + jj), acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = acc[r];
+    __syncthreads();
+    double rv[R];  // b_b - sum_p L_{p,b}^T y_p, row `lane`
+#pragma unroll
+    for (int r = 0; r < R; ++r) rv[r] = rhs[r] - part_sum(S, r, lane);
+    __syncthreads();
+    // y_b = U^T r: y_i = sum_{j <= i} U_ji r_j, the j split over the warps
+    double py[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) py[r] = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < kRowsPerWarp; ++jj) {
+        const int j = warp * kRowsPerWarp + jj;
+        const double uji = S.U[j][lane];
+#pragma unroll
+        for (int r = 0; r < R; ++r) py[r] = fma(uji, __shfl_sync(kFull, rv[r], j), py[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = py[r];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) put_tagged(a.ytag + tag_at<R>(b, lane, r), part_sum(S, r, lane), ep64);
+        __syncwarp();
+        // U_b and y_b for this block's backward task
+        if (lane == 0) st_release_gpu(a.yflag + b, sy.epoch);
+    }
+}
+
+template <typename T, int R>
+__device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long long ep64, int b,
+                              SolveSmem<R> &S)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n = a.n, ld = a.ld;
+    const long long c0 = (long long)b * kW;
+    const int nc = (int)min((long long)kW, n - c0);
+    const bool active = lane < nc;
+    const long long who = b;
+
+    (void)__all_sync(kFull, wait_eq(sy, a.yflag + b, sy.epoch, who));
+    __syncwarp();
+    const double *inv = a.inv + (size_t)b * kW * kW;
+    for (int e = threadIdx.x; e < kW * kW; e += kSolveThreads) S.U[e / kW][e & (kW - 1)] = __ldcg(inv + e);
+    double yv[R];
+    wait_block<R>(sy, a.ytag, ep64, b, who, yv);
+    __syncthreads();
+
+    // tiles q >= b + 2 of row block b, from the last one up, dealt
+    // round-robin to the warps; lane = row of the block, so each column of a
+    // tile is one coalesced read
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    const T *row = a.L + c0 + (active ? lane : 0);
+    for (int q = a.nb - 1 - warp; q >= b + 2; q -= kSolveWarps) {
+        const long long q0 = (long long)q * kW;
+        const int ncq = (int)min((long long)kW, n - q0);
+        double t[kW];
+#pragma unroll
+        for (int c = 0; c < kW; ++c) t[c] = (active && c < ncq) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
+        double xv[R];
+        wait_block<R>(sy, a.xtag, ep64, q, who, xv);
+#pragma unroll
+        for (int c = 0; c < kW; ++c)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(t[c], __shfl_sync(kFull, xv[r], c), acc[r]);
+    }
+    // tile b + 1, whose x is the last to arrive: its columns split over the warps
+    if (b + 1 < a.nb) {
+        const long long q0 = (long long)(b + 1) * kW;
+        const int ncq = (int)min((long long)kW, n - q0);
+        double t[kRowsPerWarp];
+#pragma unroll
+        for (int cc = 0; cc < kRowsPerWarp; ++cc) {
+            const int c = warp * kRowsPerWarp + cc;
+            t[cc] = (active && c < ncq) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
+        }
+        double xv[R];
+        wait_block<R>(sy, a.xtag, ep64, b + 1, who, xv);
+#pragma unroll
+        for (int cc = 0; cc < kRowsPerWarp; ++cc)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                acc[r] = fma(t[cc], __shfl_sync(kFull, xv[r], warp * kRowsPerWarp + cc), acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = acc[r];
+    __syncthreads();
+    double rv[R];  // y_b - sum_q L_{b,q} x_q, row `lane`
+#pragma unroll
+    for (int r = 0; r < R; ++r) rv[r] = yv[r] - part_sum(S, r, lane);
+    __syncthreads();
+    // x_b = U r: x_i = sum_{j >= i} U_ij r_j, the j split over the warps
+    double px[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) px[r] = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < kRowsPerWarp; ++jj) {
+        const int j = warp * kRowsPerWarp + jj;
+        const double uij = S.U[lane][j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) px[r] = fma(uij, __shfl_sync(kFull, rv[r], j), px[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = px[r];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const double x = part_sum(S, r, lane);
+            put_tagged(a.xtag + tag_at<R>(b, lane, r), x, ep64);
+            if (active && r < a.nr) a.B[c0 + lane + r * a.ldb] = (T)x;
+        }
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs<T> a)
+{
+    __shared__ SolveSmem<R> S;
+    __shared__ int s_task, s_last;
+    SyncArgs sy;
+    sy.abort_flag = a.ctl + kCtlAbort;
+    sy.status = a.status;
+    sy.user_info = nullptr;
+    sy.epoch = ld_relaxed_gpu(a.ctl + kCtlEpoch);
+    sy.timeout_ns = a.timeout_ns;
+    const long long ep64 = (long long)sy.epoch << 32;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_task = aborted(sy) ? -1 : atomicAdd(a.ctl + kCtlPairNext, 1);
+        __syncthreads();
+        const int t = s_task;
+        if (t < 0 || t >= 2 * a.nb) break;
+        if (t < a.nb) forward_task<T, R>(a, sy, ep64, t, S);
+        else backward_task<T, R>(a, sy, ep64, 2 * a.nb - 1 - t, S);
+        __syncthreads();
+    }
+
+    // The last block to finish zeroes the control words for the next launch
+    // and advances the epoch.
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.ctl + kCtlExited, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int i = threadIdx.x; i < kCtlInts; i += blockDim.x)
+            if (i != kCtlEpoch) a.ctl[i] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            a.ctl[kCtlEpoch] = a.ctl[kCtlEpoch] + 1;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T, int R>
+int launch_solve(const void *L, long long n, long long ld, void *B, long long ldb, int nr, const Scratch &sc,
+                 cudaStream_t stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CHM_ERR_CUDA;
+    static int occ[64] = {0};
+    if (!occ[dev]) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, solve_kernel<T, R>, kSolveThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            return CHM_ERR_CUDA;
+        occ[dev] = b;
+    }
+    const int nb = (int)((n + kW - 1) / kW);
+    SolveArgs<T> a;
+    a.L = static_cast<const T *>(L);
+    a.n = n;
+    a.ld = ld;
+    a.B = static_cast<T *>(B);
+    a.ldb = ldb;
+    a.nb = nb;
+    a.nr = nr;
+    a.inv = reinterpret_cast<double *>(sc.data);
+    a.yflag = sc.iflags;
+    a.ytag = sc.progress;
+    a.xtag = sc.progress + (size_t)nb * kW * R * 2;
+    a.ctl = sc.ctl;
+    a.status = sc.status;
+    a.timeout_ns = timeout_ns();
+    const int grid = (int)std::min<long long>(2ll * nb, (long long)sm_count(dev) * occ[dev]);
+    solve_kernel<T, R><<<grid, kSolveThreads, 0, stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
+}
+
+template <typename T>
+int solve_all(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs, const Scratch &sc,
+              cudaStream_t stream)
+{
+    T *b = static_cast<T *>(B);
+    for (long long r0 = 0; r0 < nrhs; r0 += kSolveRhs) {
+        const int nr = (int)std::min<long long>(kSolveRhs, nrhs - r0);
+        const int rc = nr == 1 ? launch_solve<T, 1>(L, n, ld, b + r0 * ldb, ldb, 1, sc, stream)
+                               : launch_solve<T, kSolveRhs>(L, n, ld, b + r0 * ldb, ldb, nr, sc, stream);
+        if (rc != CHM_OK) return rc;
+    }
+    return CHM_OK;
+}
+
+int solve_dispatch(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs, int dtype,
+                   cudaStream_t stream)
+{
+    if (n < 0 || nrhs < 0 || n > (1ll << 26)) return CHM_ERR_ARG;
+    if (dtype != CHM_F64 && dtype != CHM_F32_MIXED) return CHM_ERR_ARG;
+    if (ld < std::max(1ll, n) || ldb < std::max(1ll, n)) return CHM_ERR_ARG;
+    const size_t elt = dtype == CHM_F64 ? 8 : 4;
+    if (n > 0 && (!L || (uintptr_t)L % elt)) return CHM_ERR_ARG;
+    if (n > 0 && nrhs > 0 && (!B || (uintptr_t)B % elt)) return CHM_ERR_ARG;
+    if (n == 0 || nrhs == 0) return CHM_OK;
+    int rc = check_reachable(L);
+    if (rc == CHM_OK) rc = check_reachable(B);
+    if (rc != CHM_OK) return rc;
+    const size_t nb = (size_t)((n + kW - 1) / kW);
+    ScratchNeed need;
+    need.iflags = (nb + 63) & ~(size_t)63;
+    need.progress = 2 * nb * kW * kSolveRhs * 2;
+    need.data = nb * kW * kW * sizeof(double);
+    return with_stream_scratch(stream, need, [&](const Scratch &sc) {
+        return dtype == CHM_F64 ? solve_all<double>(L, n, ld, B, ldb, nrhs, sc, stream)
+                                : solve_all<float>(L, n, ld, B, ldb, nrhs, sc, stream);
+    });
+}
+
+}  // namespace
+}  // namespace chm
+
+extern "C" int chm_solve(const void *L, int64_t n, int64_t ld, void *B, int64_t ldb, int64_t nrhs, int dtype,
+                         chm_stream_t stream)
+{
+    return chm::solve_dispatch(L, n, ld, B, ldb, nrhs, dtype, (cudaStream_t)stream);
+}

@@ -118,3 +118,19 @@ def test_workspace_bytes_grow_as_n_times_k():
             ws(*bad)
     with pytest.raises(chm.ChmError):
         ws(10, 1, 9)
+
+
+def test_solve_argument_errors_without_gpu():
+    E = chm.CHM_ERR_ARG
+    assert chm.chm_solve(8, -1, 1, 8, 1, 1, chm.CHM_F64, None) == E          # n < 0
+    assert chm.chm_solve(8, 4, 3, 8, 4, 1, chm.CHM_F64, None) == E           # ld < n
+    assert chm.chm_solve(8, 4, 4, 8, 3, 1, chm.CHM_F64, None) == E           # ldb < n
+    assert chm.chm_solve(8, 4, 4, 8, 4, -1, chm.CHM_F64, None) == E          # nrhs < 0
+    assert chm.chm_solve(8, 4, 4, 8, 4, 1, 5, None) == E                     # dtype
+    assert chm.chm_solve(None, 4, 4, 8, 4, 1, chm.CHM_F64, None) == E        # NULL L
+    assert chm.chm_solve(8, 4, 4, None, 4, 1, chm.CHM_F64, None) == E        # NULL B
+    assert chm.chm_solve(12, 4, 4, 8, 4, 1, chm.CHM_F64, None) == E          # misaligned L
+    assert chm.chm_solve(8, 4, 4, 6, 4, 1, chm.CHM_F32_MIXED, None) == E     # misaligned B
+    # nothing to do: no CUDA call
+    assert chm.chm_solve(None, 0, 1, None, 1, 3, chm.CHM_F64, None) == chm.CHM_OK
+    assert chm.chm_solve(8, 5, 5, None, 5, 0, chm.CHM_F64, None) == chm.CHM_OK
