@@ -12,8 +12,12 @@ triangle) + elt*n*k (one read of V).  The L factor (100 MB upper triangle)
 fits in the 126 MB L2, so L2 is flushed (a 512 MB write) between timed steps,
 outside the timed events.
 
-The JSON line also carries the metric's second half, batched and served
-latency against plain per-request launches:
+The JSON line also carries two related timings, each outside the metric:
+  solve          chm_solve with the modified factor (1 and 16 right-hand
+                 sides) beside two cuBLAS triangular solves through torch;
+  host_resident  the same modification with L in page-locked host memory.
+And the metric's second half, batched and served latency against plain
+per-request launches:
   batch  512 independent factors, n log-uniform on [64, 4096], k from
          {1, 4, 16}, random signs whose downdates remove a previously applied
          V, float64, one graph-replayed launch per execution (chm_batch_*)
@@ -56,7 +60,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # kernel from an ncu capture of this workload (profiles/), keyed by the
 # sha256 (first 16 hex digits) of the kernel sources it was taken with; a
 # capture of an older kernel version reads as null.
-NCU_TRAFFIC = {("wave_kernel<double>", "2404bfee59a0b2b4"): 447.46e6}
+NCU_TRAFFIC = {("wave_kernel<double>", "bf8e8d8237392897"): 430.78e6}
 KERNEL_SOURCES = ("paper_1011_1173_gb300/csrc/chm_wave.cuh", "paper_1011_1173_gb300/csrc/chm_device.cuh",
                   "paper_1011_1173_gb300/csrc/chm_layout.h", "paper_1011_1173_gb300/csrc/chm_modify.cu")
 
@@ -89,6 +93,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-host", action="store_true", help="skip the host-resident factor timing")
     ap.add_argument("--no-autotune", action="store_true", help="time the batch plan's default configuration")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-factors", type=int, default=2000)
@@ -196,6 +202,103 @@ def bench_batch(dev, autotune=False, count=512, reps=5):
                       "factor_latency_ms": {"p50": percentile(lat_plain, 50), "p99": percentile(lat_plain, 99)},
                       "launches_per_exec": count},
             "speedup": p_ms / b_ms}
+
+
+def bench_solve(dev, L, reps=5):
+    """chm_solve with the bench factor, X = (L^T L)^{-1} B for 1 and 16
+    right-hand sides, beside the same solve as two torch.linalg.solve_triangular
+    calls (cuBLAS triangular solves).  GB/s counts the upper triangle read
+    twice (forward and back substitution)."""
+    import torch
+
+    from paper_1011_1173_gb300 import chm, inputs
+    n = L.shape[0]
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device=dev).manual_seed(inputs.config_seed(4))
+    U = torch.triu(L.T)
+    tri_bytes = 2 * 8 * n * (n + 1) / 2
+
+    def timed(fn):
+        ts = []
+        for r in range(reps + 2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r >= 2:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    runs = []
+    for nrhs in (1, 16):
+        B = torch.randn((nrhs, n), generator=g, dtype=torch.float64, device=dev)
+        X = B.clone()
+
+        def mine():
+            chm.check(chm.solve(L, X, stream=stream), "solve")
+
+        ms = timed(mine)
+        chm.check(chm.status_sync(stream)[0], "solve status")
+        X.copy_(B)
+        mine()
+        chm.check(chm.status_sync(stream)[0], "solve status")
+        res = float((U.T @ (U @ X.T) - B.T).abs().max() / ((U.T.abs() @ (U.abs() @ X.T.abs())).max()))
+        if not res <= 1e-13:
+            raise RuntimeError("solve residual %g" % res)
+        Bt = B.T.contiguous()
+
+        def library():
+            y = torch.linalg.solve_triangular(U.T, Bt, upper=False)
+            torch.linalg.solve_triangular(U, y, upper=True)
+
+        run = {"nrhs": nrhs, "ms": ms, "GBps": tri_bytes / (ms / 1e3) / 1e9, "residual": res}
+        try:  # context only: torch loads its linear-algebra library lazily
+            run["torch_solve_triangular_x2_ms"] = timed(library)
+        except RuntimeError as e:
+            run["torch_solve_triangular_x2_ms"] = None
+            run["library_error"] = str(e).splitlines()[0][:120]
+        runs.append(run)
+    del U
+    torch.cuda.empty_cache()
+    return {"workload": "solve with the bench factor after the timed steps, n=%d float64" % n, "runs": runs}
+
+
+def bench_host_resident(dev, L0, V, reps=3):
+    """The bench modification with L in page-locked host memory (the kernel
+    reads and writes it across the CPU-GPU link; the device holds only the
+    workspace), against the same factor in device memory."""
+    import torch
+
+    from paper_1011_1173_gb300 import chm
+    n, k = L0.shape[0], V.shape[0]
+    stream = torch.cuda.current_stream()
+    Lh = torch.empty(L0.shape, dtype=L0.dtype, pin_memory=True)
+    Lh.copy_(L0)
+    Ld = L0.clone()
+
+    def timed(L):
+        ts = []
+        for r in range(reps + 1):
+            for sg in (1, -1):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                chm.check(chm.modify(L, V, sg, stream=stream), "modify")
+                b.record(stream)
+                torch.cuda.synchronize()
+                if r > 0:
+                    ts.append(a.elapsed_time(b))
+        chm.check(chm.status_sync(stream)[0], "status")
+        return statistics.median(ts)
+
+    dev_ms = timed(Ld)
+    host_ms = timed(Lh)
+    ab = alg_bytes(n, k)
+    return {"workload": "rank-%d modification n=%d float64, L in page-locked host memory" % (k, n),
+            "ms": host_ms, "GBps": ab / (host_ms / 1e3) / 1e9, "device_resident_ms": dev_ms,
+            "device_workspace_bytes": chm.workspace_bytes(n, k)}
 
 
 def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30)):
@@ -521,7 +624,11 @@ def main():
                 "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash())),
                 "kernel_source_hash": kernel_source_hash()}
 
-    batch = serve = None
+    batch = serve = solve = host = None
+    if rank == 0 and not args.no_solve:
+        solve = bench_solve(dev, L)
+    if rank == 0 and not args.no_host:
+        host = bench_host_resident(dev, L0, V)
     if rank == 0 and not args.no_batch:
         batch = bench_batch(dev, autotune=not args.no_autotune)
     if rank == 0 and not args.no_serve:
@@ -542,7 +649,7 @@ def main():
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
-                "batched": batch, "served": serve,
+                "batched": batch, "served": serve, "solve": solve, "host_resident": host,
                 "gpu_launches": 2 * args.steps * ((k + 63) // 64),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -332,6 +332,9 @@ int chm_version(void);
  *     CHM_MB_FP64_RATE / CHM_MB_FP32_RATE  {T FMA/s for the GPU, per SM}
  *     CHM_MB_FP64_WARP       {cycles per FP64 FMA of one warp issuing
  *                             independent FMAs, cycles per dependent FMA}
+ *     CHM_MB_FP64_LANES      {cycles per dependent FP64 FMA of one warp with
+ *                             one active lane, the same for each of four
+ *                             warps of one block with all lanes active}
  *     CHM_MB_SHFL_SPLIT      {cycles of 32 dependent shuffles in a converged
  *                             warp, the same after a wait run by lane 0 alone}
  *     CHM_MB_HBM_COPY        {GB/s of a 2 GiB device copy (read + write), ms}
@@ -345,7 +348,8 @@ typedef enum {
     CHM_MB_FP64_WARP = 2,
     CHM_MB_SHFL_SPLIT = 3,
     CHM_MB_HBM_COPY = 4,
-    CHM_MB_FLAG_ROUND_TRIP = 5
+    CHM_MB_FLAG_ROUND_TRIP = 5,
+    CHM_MB_FP64_LANES = 6
 } chm_microbench_kind;
 int chm_microbench(int which, double *out, int nout);
 

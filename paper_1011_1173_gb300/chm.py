@@ -208,7 +208,7 @@ def workspace_bytes(n, k, dtype=CHM_F64) -> int:
 
 
 MICROBENCH = {"fp64_rate": 0, "fp32_rate": 1, "fp64_warp": 2, "shfl_split": 3, "hbm_copy": 4,
-              "flag_round_trip": 5}
+              "flag_round_trip": 5, "fp64_lanes": 6}
 
 
 def microbench(name):

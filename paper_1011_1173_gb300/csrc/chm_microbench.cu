@@ -6,6 +6,8 @@
 // bounded.  Diagnostics only; no part of the up/downdate calls these.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "chm.h"
 
 namespace chm {
@@ -48,6 +50,23 @@ __global__ void fp64_warp(double *out, long long *cyc, int iters, int dependent)
     const long long t1 = clock64() + (s == 12345.0 ? 1 : 0);
     out[1 + threadIdx.x] = s;
     if (threadIdx.x == 0) cyc[0] = t1 - t0;
+}
+
+// Warps of one block running dependent FP64 FMA chains on their first
+// `active` lanes; cycles per instruction of warp w in cyc[w].
+__global__ void fp64_lanes(double *out, long long *cyc, int iters, int active)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double a0 = 1.0 + threadIdx.x * 1e-3;
+    const double m = 0.999999 + out[0] * 1e-30, c = 1e-9;
+    __syncwarp();
+    const long long t0 = clock64();
+    if (lane < active)
+        for (int i = 0; i < iters; ++i) a0 = fma(a0, m, c);
+    __syncwarp();
+    const long long t1 = clock64() + (a0 == 12345.0 ? 1 : 0);
+    out[1 + threadIdx.x] = a0;
+    if (lane == 0) cyc[warp] = t1 - t0;
 }
 
 // The shape of wait that split warps in an earlier version of the kernel: a
@@ -206,6 +225,23 @@ extern "C" int chm_microbench(int which, double *out, int nout)
         fp64_warp<<<1, 32>>>(buf, cyc, iters, 1);
         cudaMemcpy(&h, cyc, 8, cudaMemcpyDeviceToHost);
         out[1] = (double)h / iters;  // cycles per FP64 instruction, dependent (latency)
+        cudaFree(buf);
+        cudaFree(cyc);
+        break;
+    }
+    case CHM_MB_FP64_LANES: {
+        double *buf = nullptr;
+        long long *cyc = nullptr;
+        if (cudaMalloc(&buf, 8 * (1 + 128)) != cudaSuccess || cudaMalloc(&cyc, 4 * 8) != cudaSuccess) { rc = CHM_ERR_NOMEM; break; }
+        cudaMemset(buf, 0, 8 * (1 + 128));
+        long long h[4] = {0, 0, 0, 0};
+        const int iters = 4096;
+        fp64_lanes<<<1, 32>>>(buf, cyc, iters, 1);
+        cudaMemcpy(h, cyc, 8, cudaMemcpyDeviceToHost);
+        out[0] = (double)h[0] / iters;  // one warp, one active lane
+        fp64_lanes<<<1, 128>>>(buf, cyc, iters, 32);
+        cudaMemcpy(h, cyc, sizeof(h), cudaMemcpyDeviceToHost);
+        out[1] = (double)std::max(std::max(h[0], h[1]), std::max(h[2], h[3])) / iters;  // four warps, one SM
         cudaFree(buf);
         cudaFree(cyc);
         break;

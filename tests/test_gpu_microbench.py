@@ -25,9 +25,12 @@ def test_microbenchmarks():
     conv, split = chm.microbench("shfl_split")
     hbm, ms = chm.microbench("hbm_copy")
     rt, failed = chm.microbench("flag_round_trip")
+    one_lane, four_warps = chm.microbench("fp64_lanes")
     print("FP64 %.3f T FMA/s (%.2f G/SM); FP32 %.2f T FMA/s; one warp: %.1f cycles per independent FP64 FMA, "
-          "%.1f per dependent; 32 shuffles %d cycles converged, %d after a lane-0 wait; HBM copy %.0f GB/s; "
-          "flag round trip %.2f us" % (fp64, fp64_sm * 1e3, fp32, issue, lat, conv, split, hbm, rt))
+          "%.1f per dependent, %.1f with one active lane, %.1f each for four warps of one SM; 32 shuffles %d "
+          "cycles converged, %d after a lane-0 wait; HBM copy %.0f GB/s; flag round trip %.2f us"
+          % (fp64, fp64_sm * 1e3, fp32, issue, lat, one_lane, four_warps, conv, split, hbm, rt))
+    assert one_lane >= 1.0 and four_warps >= 1.0
     assert 0.05 < fp64 < 10.0
     assert fp32 > 5 * fp64
     assert issue >= 1.0 and lat >= 4.0
