@@ -865,9 +865,18 @@ __device__ __forceinline__ void task_range(const Launch<T> &P, int j, int *first
 }
 
 // Take one sweep task: the warp's own group first, then the other groups'
-// current pairs.  Each ticket word is read before it is incremented, so a
-// group whose pair has no task left is not counted up.  Returns the pair
-// (or -1) and the column block; all lanes get the same answer.
+// current pairs.  Stealing cannot stall the launch: pairs are taken in
+// increasing order and a pair's tasks wait only on lower pairs, so a task
+// stolen from a running pair never waits on the pair its warp's group takes
+// next, and the lowest running pair always has its group's warps free for
+// it.  Each ticket word is read before it is incremented, so a group whose pair
+// has no task left is not counted up.  The ticket the increment returns is
+// the one taken, whatever pair it belongs to: the group may have moved to
+// its next pair between the read and the increment, and a ticket of that
+// pair counted up here must be run here, or its column block would never be
+// rotated.  A count on a word without a pair (none yet, or the group is
+// done) is erased when the group takes its next pair.  Returns the pair (or
+// -1) and the column block; all lanes get the same answer.
 template <typename T>
 __device__ __forceinline__ int take_task(const Launch<T> &P, int group, int *block)
 {
@@ -886,8 +895,11 @@ __device__ __forceinline__ int take_task(const Launch<T> &P, int group, int *blo
         unsigned long long v2 = 0;
         if (lane == 0) v2 = atomicAdd(gts + g, 1ull);
         v2 = __shfl_sync(0xffffffffu, v2, 0);
-        if ((unsigned)(v2 >> 32) == hi && (long long)(unsigned)v2 + first < nb) {
-            j = (int)hi - 1;
+        const unsigned hi2 = (unsigned)(v2 >> 32);
+        if (hi2 == 0u || hi2 == kGroupDone) continue;
+        if (hi2 != hi) task_range(P, (int)hi2 - 1, &first, &nb);
+        if ((long long)(unsigned)v2 + first < nb) {
+            j = (int)hi2 - 1;
             b = (int)(unsigned)v2 + first;
         }
     }
