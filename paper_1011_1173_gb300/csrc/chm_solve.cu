@@ -11,11 +11,13 @@
 // launch cannot deadlock whatever the number of resident blocks.
 //
 // Each forward task inverts its diagonal block (U_b = D_b^{-1}, one column
-// per lane) while its other warps accumulate the tiles whose y is already
-// published; the backward task of the block reuses U_b.  The only work
-// between one block's result and the next block's is one tile product and
-// one triangular matrix-vector product, each split over the four warps.
-// Results pass between blocks as epoch-tagged doubles (no fence, no flag).
+// per lane) and forms G_b = U_b^T L_{b-1,b}^T while its warps accumulate the
+// tiles whose y is already published, and z_b = U_b^T (b_b - sum over
+// p <= b-2) once y_{b-2} is in; then y_b = z_b - G_b y_{b-1}.  The backward
+// task reuses U_b and forms H_b = U_b L_{b,b+1}: x_b = z'_b - H_b x_{b+1}.
+// Between one block's result and the next block's there is one 32 x 32
+// product (eight FMAs per warp), one barrier and a four-way sum.  Results
+// pass between blocks as epoch-tagged doubles (no fence, no flag).
 #include <float.h>
 
 #include <algorithm>
@@ -31,7 +33,7 @@ namespace {
 constexpr int kSolveThreads = 128;
 constexpr int kSolveWarps = kSolveThreads / 32;
 constexpr int kSolveRhs = 4;                       // right-hand sides per launch (largest)
-constexpr int kRowsPerWarp = kW / kSolveWarps;     // rows of the critical tile per warp
+constexpr int kRowsPerWarp = kW / kSolveWarps;     // rows (or columns) of a split tile per warp
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T>
@@ -55,7 +57,8 @@ template <int R>
 struct SolveSmem {
     double D[kW][kW + 1];  // diagonal block (row, column); identity beyond the order
     double U[kW][kW + 1];  // its inverse
-    double part[kSolveWarps][R][kW];
+    double T[kW][kW + 1];  // the tile next to the diagonal block (see the tasks)
+    double part[2][kSolveWarps][R][kW];
     double rd[kW];         // 1 / D_ii
 };
 
@@ -66,24 +69,53 @@ __device__ __forceinline__ size_t tag_at(int blk, int i, int r)
 }
 
 // The whole warp waits for the R tagged values of block `blk` (lane i gets
-// row i).  A wait that gives up (recorded as a timeout, or the launch is
-// aborted) yields zeros, so that every warp still reaches the block's
-// barriers; the result is then unspecified and the status says so.
+// row i).  `next_step` marks the wait on the previous block's result, the
+// one step of the chain: it polls at short fixed intervals (only the next
+// block's four warps wait on a fresh result, and each step gains the time a
+// longer sleep would add); every other wait backs off up to 256 ns, since
+// hundreds of warps may be waiting on older results at once.  A wait that
+// gives up (recorded as a timeout, or the launch is aborted) yields zeros,
+// so that every warp still reaches the block's barriers; the result is then
+// unspecified and the status says so.
 template <int R>
 __device__ __forceinline__ void wait_block(const SyncArgs &sy, const long long *tags, long long ep64, int blk,
-                                           long long who, double *v)
+                                           long long who, double *v, bool next_step = false)
 {
     const int lane = threadIdx.x & 31;
+    const long long *w = tags + tag_at<R>(blk, lane, 0);
+    const long long t0 = global_ns();
+    unsigned ns = next_step ? 32 : 16;
+    for (unsigned it = 0;; ++it) {
+        bool ok = true;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (!warp_wait_tagged(sy, tags + tag_at<R>(blk, lane, r), ep64, who, &v[r])) v[r] = 0.0;
+        for (int r = 0; r < R; ++r) ok = get_tagged(w + 2 * r, ep64, &v[r]) && ok;
+        if (__all_sync(kFull, ok)) return;
+        if ((it & 15u) == 15u) {
+            int stop = 0;
+            if (lane == 0) {
+                if (aborted(sy)) {
+                    stop = 1;
+                } else if (global_ns() - t0 > sy.timeout_ns || it > (1u << 28)) {
+                    record_error(sy, kStatusTimeout, who);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(kFull, stop, 0)) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = 0.0;
+                return;
+            }
+        }
+        __nanosleep(ns);
+        if (!next_step && ns < 256) ns <<= 1;
+    }
 }
 
 // Sum of the four warps' partial products of row `lane`, for each r.
 template <int R>
-__device__ __forceinline__ double part_sum(const SolveSmem<R> &S, int r, int lane)
+__device__ __forceinline__ double part_sum(const SolveSmem<R> &S, int buf, int r, int lane)
 {
-    return (S.part[0][r][lane] + S.part[1][r][lane]) + (S.part[2][r][lane] + S.part[3][r][lane]);
+    return (S.part[buf][0][r][lane] + S.part[buf][1][r][lane]) + (S.part[buf][2][r][lane] + S.part[buf][3][r][lane]);
 }
 
 template <typename T, int R>
@@ -96,6 +128,8 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
     const bool active = lane < nc;
     const long long who = b;
 
+    // the diagonal block (identity beyond the order) and the tile above it,
+    // S.T[j][m] = L[(b-1) kW + j, c0 + m]
     for (int e = threadIdx.x; e < kW * kW; e += kSolveThreads) {
         const int i = e & (kW - 1), j = e / kW;
         double v = 0.0;
@@ -105,6 +139,7 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
             v = 1.0;
         }
         S.D[i][j] = v;
+        if (b >= 1) S.T[i][j] = (j < nc) ? (double)__ldg(a.L + c0 - kW + i + (c0 + j) * ld) : 0.0;
     }
     double rhs[R];
 #pragma unroll
@@ -136,14 +171,29 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
         }
     }
 
-    // tiles p <= b - 2 of column block b, dealt round-robin to the warps (a
+    __syncthreads();  // U in shared memory
+
+    // G = U^T S.T^T, the rows j of S.T split over the warps:
+    // g[jj] = G[lane][warp * 8 + jj] = sum_m U[m][lane] S.T[warp * 8 + jj][m]
+    double g[kRowsPerWarp];
+#pragma unroll
+    for (int jj = 0; jj < kRowsPerWarp; ++jj) g[jj] = 0.0;
+    if (b >= 1) {
+#pragma unroll
+        for (int m = 0; m < kW; ++m) {
+            const double um = S.U[m][lane];
+#pragma unroll
+            for (int jj = 0; jj < kRowsPerWarp; ++jj) g[jj] = fma(um, S.T[warp * kRowsPerWarp + jj][m], g[jj]);
+        }
+    }
+    // tiles p <= b - 3 of column block b, dealt round-robin to the warps (a
     // fixed order of the sums: results do not depend on timing); lane =
     // column of the block, the tile's 32 rows read down the column
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0;
     const T *col = a.L + (c0 + (active ? lane : 0)) * ld;
-    for (int p = warp; p <= b - 2; p += kSolveWarps) {
+    for (int p = warp; p <= b - 3; p += kSolveWarps) {
         const T *src = col + (long long)p * kW;
         double t[kW];
 #pragma unroll
@@ -155,14 +205,14 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = fma(t[j], __shfl_sync(kFull, yv[r], j), acc[r]);
     }
-    // tile b - 1, whose y is the last to arrive: its rows split over the warps
-    if (b >= 1) {
-        const T *src = col + (long long)(b - 1) * kW + warp * kRowsPerWarp;
+    // tile b - 2: its rows split over the warps
+    if (b >= 2) {
+        const T *src = col + (long long)(b - 2) * kW + warp * kRowsPerWarp;
         double t[kRowsPerWarp];
 #pragma unroll
         for (int jj = 0; jj < kRowsPerWarp; ++jj) t[jj] = active ? (double)__ldg(src + jj) : 0.0;
         double yv[R];
-        wait_block<R>(sy, a.ytag, ep64, b - 1, who, yv);
+        wait_block<R>(sy, a.ytag, ep64, b - 2, who, yv);
 #pragma unroll
         for (int jj = 0; jj < kRowsPerWarp; ++jj)
 #pragma unroll
@@ -170,29 +220,48 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
                 acc[r] = fma(t[jj], __shfl_sync(kFull, yv[r], warp * kRowsPerWarp + jj), acc[r]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = acc[r];
+    for (int r = 0; r < R; ++r) S.part[0][warp][r][lane] = acc[r];
     __syncthreads();
-    double rv[R];  // b_b - sum_p L_{p,b}^T y_p, row `lane`
+    double rv[R];  // b_b - sum_{p <= b-2} L_{p,b}^T y_p, row `lane`
 #pragma unroll
-    for (int r = 0; r < R; ++r) rv[r] = rhs[r] - part_sum(S, r, lane);
-    __syncthreads();
-    // y_b = U^T r: y_i = sum_{j <= i} U_ji r_j, the j split over the warps
-    double py[R];
+    for (int r = 0; r < R; ++r) rv[r] = rhs[r] - part_sum(S, 0, r, lane);
+    // z_b = U^T r: z_i = sum_{j <= i} U_ji r_j, the j split over the warps
+    double pz[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) py[r] = 0.0;
+    for (int r = 0; r < R; ++r) pz[r] = 0.0;
 #pragma unroll
     for (int jj = 0; jj < kRowsPerWarp; ++jj) {
         const int j = warp * kRowsPerWarp + jj;
         const double uji = S.U[j][lane];
 #pragma unroll
-        for (int r = 0; r < R; ++r) py[r] = fma(uji, __shfl_sync(kFull, rv[r], j), py[r]);
+        for (int r = 0; r < R; ++r) pz[r] = fma(uji, __shfl_sync(kFull, rv[r], j), pz[r]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = py[r];
+    for (int r = 0; r < R; ++r) S.part[1][warp][r][lane] = pz[r];
+    __syncthreads();
+    double z[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[r] = part_sum(S, 1, r, lane);
+    __syncthreads();  // part[0] free again
+    // y_b = z_b - G_b y_{b-1}: the step that waits on the previous block
+    double py[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) py[r] = 0.0;
+    if (b >= 1) {
+        double yv[R];
+        wait_block<R>(sy, a.ytag, ep64, b - 1, who, yv, true);
+#pragma unroll
+        for (int jj = 0; jj < kRowsPerWarp; ++jj)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                py[r] = fma(g[jj], __shfl_sync(kFull, yv[r], warp * kRowsPerWarp + jj), py[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.part[0][warp][r][lane] = py[r];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) put_tagged(a.ytag + tag_at<R>(b, lane, r), part_sum(S, r, lane), ep64);
+        for (int r = 0; r < R; ++r) put_tagged(a.ytag + tag_at<R>(b, lane, r), z[r] - part_sum(S, 0, r, lane), ep64);
         __syncwarp();
         // U_b and y_b for this block's backward task
         if (lane == 0) st_release_gpu(a.yflag + b, sy.epoch);
@@ -209,23 +278,45 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
     const int nc = (int)min((long long)kW, n - c0);
     const bool active = lane < nc;
     const long long who = b;
+    const bool has_next = b + 1 < a.nb;
 
     (void)__all_sync(kFull, wait_eq(sy, a.yflag + b, sy.epoch, who));
     __syncwarp();
+    // U_b, and the tile to its right, S.T[m][j] = L[c0 + m, (b+1) kW + j]
     const double *inv = a.inv + (size_t)b * kW * kW;
-    for (int e = threadIdx.x; e < kW * kW; e += kSolveThreads) S.U[e / kW][e & (kW - 1)] = __ldcg(inv + e);
+    const long long q1 = (long long)(b + 1) * kW;
+    const int nc1 = has_next ? (int)min((long long)kW, n - q1) : 0;
+    for (int e = threadIdx.x; e < kW * kW; e += kSolveThreads) {
+        const int i = e / kW, j = e & (kW - 1);
+        S.U[i][j] = __ldcg(inv + e);
+        S.T[j][i] = (has_next && j < nc && i < nc1) ? (double)__ldg(a.L + c0 + j + (q1 + i) * ld) : 0.0;
+    }
     double yv[R];
     wait_block<R>(sy, a.ytag, ep64, b, who, yv);
     __syncthreads();
 
-    // tiles q >= b + 2 of row block b, from the last one up, dealt
+    // H = U S.T, the columns j of S.T split over the warps:
+    // h[jj] = H[lane][warp * 8 + jj] = sum_m U[lane][m] S.T[m][warp * 8 + jj]
+    double h[kRowsPerWarp];
+#pragma unroll
+    for (int jj = 0; jj < kRowsPerWarp; ++jj) h[jj] = 0.0;
+    if (has_next) {
+#pragma unroll
+        for (int m = 0; m < kW; ++m) {
+            const double um = S.U[lane][m];
+#pragma unroll
+            for (int jj = 0; jj < kRowsPerWarp; ++jj) h[jj] = fma(um, S.T[m][warp * kRowsPerWarp + jj], h[jj]);
+        }
+    }
+
+    // tiles q >= b + 3 of row block b, from the last one up, dealt
     // round-robin to the warps; lane = row of the block, so each column of a
     // tile is one coalesced read
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0;
     const T *row = a.L + c0 + (active ? lane : 0);
-    for (int q = a.nb - 1 - warp; q >= b + 2; q -= kSolveWarps) {
+    for (int q = a.nb - 1 - warp; q >= b + 3; q -= kSolveWarps) {
         const long long q0 = (long long)q * kW;
         const int ncq = (int)min((long long)kW, n - q0);
         double t[kW];
@@ -238,9 +329,9 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = fma(t[c], __shfl_sync(kFull, xv[r], c), acc[r]);
     }
-    // tile b + 1, whose x is the last to arrive: its columns split over the warps
-    if (b + 1 < a.nb) {
-        const long long q0 = (long long)(b + 1) * kW;
+    // tile b + 2: its columns split over the warps
+    if (b + 2 < a.nb) {
+        const long long q0 = (long long)(b + 2) * kW;
         const int ncq = (int)min((long long)kW, n - q0);
         double t[kRowsPerWarp];
 #pragma unroll
@@ -249,7 +340,7 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
             t[cc] = (active && c < ncq) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
         }
         double xv[R];
-        wait_block<R>(sy, a.xtag, ep64, b + 1, who, xv);
+        wait_block<R>(sy, a.xtag, ep64, b + 2, who, xv);
 #pragma unroll
         for (int cc = 0; cc < kRowsPerWarp; ++cc)
 #pragma unroll
@@ -257,30 +348,49 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
                 acc[r] = fma(t[cc], __shfl_sync(kFull, xv[r], warp * kRowsPerWarp + cc), acc[r]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = acc[r];
+    for (int r = 0; r < R; ++r) S.part[0][warp][r][lane] = acc[r];
     __syncthreads();
-    double rv[R];  // y_b - sum_q L_{b,q} x_q, row `lane`
+    double rv[R];  // y_b - sum_{q >= b+2} L_{b,q} x_q, row `lane`
 #pragma unroll
-    for (int r = 0; r < R; ++r) rv[r] = yv[r] - part_sum(S, r, lane);
-    __syncthreads();
-    // x_b = U r: x_i = sum_{j >= i} U_ij r_j, the j split over the warps
-    double px[R];
+    for (int r = 0; r < R; ++r) rv[r] = yv[r] - part_sum(S, 0, r, lane);
+    // z'_b = U r: z_i = sum_{j >= i} U_ij r_j, the j split over the warps
+    double pz[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) px[r] = 0.0;
+    for (int r = 0; r < R; ++r) pz[r] = 0.0;
 #pragma unroll
     for (int jj = 0; jj < kRowsPerWarp; ++jj) {
         const int j = warp * kRowsPerWarp + jj;
         const double uij = S.U[lane][j];
 #pragma unroll
-        for (int r = 0; r < R; ++r) px[r] = fma(uij, __shfl_sync(kFull, rv[r], j), px[r]);
+        for (int r = 0; r < R; ++r) pz[r] = fma(uij, __shfl_sync(kFull, rv[r], j), pz[r]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) S.part[warp][r][lane] = px[r];
+    for (int r = 0; r < R; ++r) S.part[1][warp][r][lane] = pz[r];
+    __syncthreads();
+    double z[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[r] = part_sum(S, 1, r, lane);
+    __syncthreads();  // part[0] free again
+    // x_b = z'_b - H_b x_{b+1}: the step that waits on the previous block
+    double px[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) px[r] = 0.0;
+    if (has_next) {
+        double xv[R];
+        wait_block<R>(sy, a.xtag, ep64, b + 1, who, xv, true);
+#pragma unroll
+        for (int jj = 0; jj < kRowsPerWarp; ++jj)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                px[r] = fma(h[jj], __shfl_sync(kFull, xv[r], warp * kRowsPerWarp + jj), px[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.part[0][warp][r][lane] = px[r];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const double x = part_sum(S, r, lane);
+            const double x = z[r] - part_sum(S, 0, r, lane);
             put_tagged(a.xtag + tag_at<R>(b, lane, r), x, ep64);
             if (active && r < a.nr) a.B[c0 + lane + r * a.ldb] = (T)x;
         }
