@@ -27,7 +27,9 @@ per-request launches:
          Poisson arrivals of requests with k uniform on [1, 32], factor
          Zipf(1.1), 70 % updates and 30 % downdates of the factor's latest
          update, through chm_server_* against plain launches serialised on
-         one stream, both fed the same arrival sequence.
+         one stream, both fed the same arrival sequence (offered load 0.9 x
+         the plain path's saturation rate; --serve-loads gives others).
+The batch runs in float64 and again in float32 storage with float64 Compute.
 
 Arms:
   default          the CUDA library through its C ABI (this repository)
@@ -98,6 +100,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="time the batch plan's default configuration")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-factors", type=int, default=2000)
+    ap.add_argument("--serve-loads", default="0.9",
+                    help="offered loads as fractions of the plain path's saturation rate, comma separated")
+    ap.add_argument("--no-batch-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -119,8 +124,9 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else None
 
 
-def bench_batch(dev, autotune=False, count=512, reps=5):
-    """Batched launch (chm_batch_*) against one plain launch per factor."""
+def bench_batch(dev, autotune=False, count=512, reps=5, mixed=False):
+    """Batched launch (chm_batch_*) against one plain launch per factor
+    (float64, or float32 storage with float64 Compute when ``mixed``)."""
     import numpy as np
     import torch
 
@@ -129,22 +135,25 @@ def bench_batch(dev, autotune=False, count=512, reps=5):
     ns = np.exp(rng.uniform(np.log(64), np.log(4096), count)).astype(int)
     ks = rng.choice([1, 4, 16], count)
     sg = rng.choice([1, -1], count)
+    dt = torch.float32 if mixed else torch.float64
+    code = chm.CHM_F32_MIXED if mixed else chm.CHM_F64
+    elt = 4 if mixed else 8
     Ls, Vs = [], []
     for i in range(count):
         n, k = int(ns[i]), int(ks[i])
-        Ls.append(inputs.random_factor(n, 10000 + i, device=dev))
-        Vs.append(inputs.update_block(n, k, 10000 + i, device=dev))
+        Ls.append(inputs.random_factor(n, 10000 + i, device=dev, dtype=dt))
+        Vs.append(inputs.update_block(n, k, 10000 + i, device=dev, dtype=dt))
     stream = torch.cuda.current_stream()
     # downdates remove a previously applied V: apply those first (untimed)
     pre = chm.BatchPlan(ns.tolist(), ns.tolist(), [int(k) if s < 0 else 0 for k, s in zip(ks, sg)],
-                        [1] * count)
+                        [1] * count, code)
     chm.check(pre.execute(Ls, Vs, stream), "batch pre-update")
-    fwd = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), sg.tolist())
-    inv = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), (-sg).tolist())
+    fwd = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), sg.tolist(), code)
+    inv = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), (-sg).tolist(), code)
     if autotune:
         chm.check(fwd.autotune(stream), "autotune")
         chm.check(inv.autotune(stream), "autotune")
-    bytes_exec = float(sum(alg_bytes(int(n), int(k)) for n, k in zip(ns, ks)))
+    bytes_exec = float(sum(alg_bytes(int(n), int(k), elt) for n, k in zip(ns, ks)))
 
     def timed(fn, reps):
         ts = []
@@ -192,7 +201,8 @@ def bench_batch(dev, autotune=False, count=512, reps=5):
     b_ms = statistics.median(bt)
     p_ms = statistics.median(plain_ms)
     return {"workload": "%d factors, n log-uniform [64, 4096], k in {1,4,16}, random signs (downdates "
-                        "remove an applied V), float64" % count,
+                        "remove an applied V), %s" % (count, "float32 storage + float64 Compute" if mixed
+                                                      else "float64"),
             "alg_bytes_per_exec": bytes_exec,
             "batch": {"ms_per_exec": b_ms, "GBps": bytes_exec / (b_ms / 1e3) / 1e9,
                       "factor_latency_ms": {"p50": percentile(bt, 50), "p99": percentile(bt, 99)},
@@ -301,8 +311,10 @@ def bench_host_resident(dev, L0, V, reps=3):
             "device_workspace_bytes": chm.workspace_bytes(n, k)}
 
 
-def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30)):
-    """Served requests (chm_server_*) against plain launches serialised on one stream."""
+def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.9,)):
+    """Served requests (chm_server_*) against plain launches serialised on one
+    stream, at each offered load (a fraction of the plain path's measured
+    saturation rate); the same request sequence is replayed at every load."""
     import numpy as np
     import torch
 
@@ -311,7 +323,6 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30)):
     ns = np.exp(rng.uniform(np.log(256), np.log(8192), nfactors)).astype(int)
     dt = torch.float32
     srv = chm.Server(budget, chm.CHM_F32_MIXED, max_inflight=2)
-    plainL = {}
     perm = rng.permutation(nfactors)
     for i in range(nfactors):
         L = inputs.random_factor(int(ns[i]), 20000 + i, device=dev, dtype=dt)
@@ -331,71 +342,84 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30)):
             hist.setdefault(f, []).append(V)
         reqs.append((f, V, s))
     used = sorted(set(f for f, _, _ in reqs))
-    for f in used:  # plain comparator's copies of the factors touched
-        plainL[f] = inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt)
+
+    def plain_copies():  # plain comparator's copies of the factors touched
+        return {f: inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt) for f in used}
+
     bytes_req = [alg_bytes(int(ns[f]), V.shape[0], 4) for f, V, _ in reqs]
+    tot = float(sum(bytes_req))
     # plain saturation rate: back-to-back launches on one stream
     stream = torch.cuda.current_stream()
+    plainL = plain_copies()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for f, V, s in reqs[:200]:
         chm.check(chm.modify(plainL[f], V, s, stream=stream), "plain")
     torch.cuda.synchronize()
     sat = 200 / (time.perf_counter() - t0)
-    rate = 0.9 * sat
-    gaps = rng.exponential(1.0 / rate, nreq)
-    arrivals = np.cumsum(gaps)
-    # undo the 200 requests on the plain copies: regenerate them
-    for f in used:
-        plainL[f] = inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt)
-    torch.cuda.synchronize()
 
-    # served run: the host submits at the arrival times
-    t_start = time.perf_counter()
-    for j, (f, V, s) in enumerate(reqs):
-        while time.perf_counter() - t_start < arrivals[j]:
-            pass
-        srv.submit(f, V, s)
-    chm.check(srv.drain(600.0), "serve drain")
-    t_serve = time.perf_counter() - t_start
-    done = srv.poll(nreq + 16)
-    lat_srv = [d[2] * 1e3 for d in done]
-    bad = sum(1 for d in done if d[1] != chm.CHM_OK)
-    st = srv.stats()
-    srv.close()
+    results = []
+    for load in loads:
+        rate = load * sat
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        plainL = plain_copies()
+        torch.cuda.synchronize()
+        st0 = srv.stats()
+        # served run: the host submits at the arrival times
+        t_start = time.perf_counter()
+        for j, (f, V, s) in enumerate(reqs):
+            while time.perf_counter() - t_start < arrivals[j]:
+                pass
+            srv.submit(f, V, s)
+        chm.check(srv.drain(600.0), "serve drain")
+        t_serve = time.perf_counter() - t_start
+        done = srv.poll(nreq + 16)
+        lat_srv = [d[2] * 1e3 for d in done]
+        bad = sum(1 for d in done if d[1] != chm.CHM_OK)
+        st = srv.stats()
 
-    # plain run: same arrivals, one launch per request on one stream; a
-    # request completes at its event, timed from an event recorded when the
-    # arrival clock starts (the stream is idle then)
-    evs = []
-    a0 = torch.cuda.Event(enable_timing=True)
-    t_start = time.perf_counter()
-    a0.record(stream)
-    for j, (f, V, s) in enumerate(reqs):
-        while time.perf_counter() - t_start < arrivals[j]:
-            pass
-        chm.check(chm.modify(plainL[f], V, s, stream=stream), "plain")
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)
-        evs.append(e)
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t_start
-    chm.check(chm.status_sync(stream)[0], "plain status")
-    del plainL, reqs, hist
-    torch.cuda.empty_cache()
-    tot = float(sum(bytes_req))
-    lat_plain = [a0.elapsed_time(e) - arrivals[j] * 1e3 for j, e in enumerate(evs)]
-    t_plain = max(t_plain, a0.elapsed_time(evs[-1]) / 1e3)
-    return {"workload": "%d resident factors, n log-uniform [256, 8192], float32 storage + float64 Compute, "
-                        "%d requests, k ~ U{1..32}, factor Zipf(1.1), 70%% updates / 30%% downdates, Poisson "
-                        "arrivals at 0.9 x the plain path's saturation rate" % (nfactors, nreq),
-            "offered_rate_rps": rate, "plain_saturation_rps": sat,
+        # plain run: same arrivals, one launch per request on one stream; a
+        # request completes at its event, timed from an event recorded when
+        # the arrival clock starts (the stream is idle then)
+        evs = []
+        a0 = torch.cuda.Event(enable_timing=True)
+        t_start = time.perf_counter()
+        a0.record(stream)
+        for j, (f, V, s) in enumerate(reqs):
+            while time.perf_counter() - t_start < arrivals[j]:
+                pass
+            chm.check(chm.modify(plainL[f], V, s, stream=stream), "plain")
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs.append(e)
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t_start
+        chm.check(chm.status_sync(stream)[0], "plain status")
+        lat_plain = [a0.elapsed_time(e) - arrivals[j] * 1e3 for j, e in enumerate(evs)]
+        t_plain = max(t_plain, a0.elapsed_time(evs[-1]) / 1e3)
+        del plainL
+        results.append({
+            "offered_load": load, "offered_rate_rps": rate,
             "served": {"rps": nreq / t_serve, "GBps": tot / t_serve / 1e9,
                        "latency_ms": {"p50": percentile(lat_srv, 50), "p99": percentile(lat_srv, 99)},
-                       "failed": bad, "launches": st["launches"], "max_concurrent": st["max_concurrent"]},
+                       "failed": bad, "launches": st["launches"] - st0["launches"],
+                       "max_concurrent": st["max_concurrent"]},
             "plain": {"rps": nreq / t_plain, "GBps": tot / t_plain / 1e9,
                       "latency_ms": {"p50": percentile(lat_plain, 50), "p99": percentile(lat_plain, 99)},
-                      "launches": nreq}}
+                      "launches": nreq}})
+    srv.close()
+    del reqs, hist
+    torch.cuda.empty_cache()
+    out = {"workload": "%d resident factors, n log-uniform [256, 8192], float32 storage + float64 Compute, "
+                       "%d requests, k ~ U{1..32}, factor Zipf(1.1), 70%% updates / 30%% downdates, Poisson "
+                       "arrivals at %s x the plain path's saturation rate"
+                       % (nfactors, nreq, "/".join("%g" % x for x in loads)),
+           "plain_saturation_rps": sat}
+    if len(results) == 1:
+        out.update(results[0])
+    else:
+        out["by_load"] = results
+    return out
 
 
 class ClockSampler:
@@ -624,15 +648,18 @@ def main():
                 "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash())),
                 "kernel_source_hash": kernel_source_hash()}
 
-    batch = serve = solve = host = None
+    batch = batch_mixed = serve = solve = host = None
     if rank == 0 and not args.no_solve:
         solve = bench_solve(dev, L)
     if rank == 0 and not args.no_host:
         host = bench_host_resident(dev, L0, V)
     if rank == 0 and not args.no_batch:
         batch = bench_batch(dev, autotune=not args.no_autotune)
+    if rank == 0 and not args.no_batch and not args.no_batch_mixed:
+        batch_mixed = bench_batch(dev, autotune=not args.no_autotune, mixed=True)
     if rank == 0 and not args.no_serve:
-        serve = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests)
+        loads = [float(x) for x in args.serve_loads.split(",") if x.strip()]
+        serve = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests, loads=loads)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -649,7 +676,7 @@ def main():
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
-                "batched": batch, "served": serve, "solve": solve, "host_resident": host,
+                "batched": batch, "batched_mixed": batch_mixed, "served": serve, "solve": solve, "host_resident": host,
                 "gpu_launches": 2 * args.steps * ((k + 63) // 64),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -46,6 +46,8 @@ std::vector<int> carve(const ProbShape *shapes, int count, const Scratch &sc, Pr
         p.nb = nb;
         p.k = k;
         p.pair0 = pair;
+        p.blk0 = 0;
+        p.blk1 = nb;
         p.iflags = sc.iflags + fi;
         p.progress = sc.progress + fp;
         p.data = sc.data + fd;

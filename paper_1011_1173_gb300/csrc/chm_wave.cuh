@@ -73,6 +73,7 @@ struct Wave {
     const T *V;                 // column q of the problem's V
     long long n, ld;
     int nb, q, pair;
+    int blk0, blk1;             // the launch's window of column blocks
     bool has_next;
     bool unscale;               // the problem's final pass: rows times the last wave's scale
     double sg;                  // +1 update, -1 downdate
@@ -82,6 +83,7 @@ struct Wave {
     ChainRow *chain0;           // [nb][kW] original factor's row data (wave 0 writes)
     double *tend, *rdiag, *rtile;
     double *rdiag_next, *rtile_next;  // the next wave's (null without one)
+    double *carry;              // chain state at the window's end: T, 1/T, p of the last block
     int *pflag, *dflag, *rflag0;
     const int *dflag_prev;
     long long *progress;
@@ -109,6 +111,8 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.nb = nb;
     w.q = q;
     w.pair = j;
+    w.blk0 = pr.blk0;
+    w.blk1 = pr.blk1;
     w.has_next = q + 1 < pr.k;
     w.unscale = q == pr.k;  // the pair after the last wave; it owns no scratch of its own
     w.sg = ((pr.down_mask >> q) & 1ull) ? -1.0 : 1.0;
@@ -119,6 +123,7 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.tend = reinterpret_cast<double *>(d + rc.tend);
     w.rdiag = reinterpret_cast<double *>(d + rc.rdiag);
     w.rtile = reinterpret_cast<double *>(d + rc.rtile);
+    w.carry = reinterpret_cast<double *>(d + rc.carry);
     w.rdiag_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rdiag) : nullptr;
     w.rtile_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rtile) : nullptr;
     int *f = pr.iflags + (size_t)q * 2 * nb;
@@ -393,7 +398,8 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
 #pragma unroll
             for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         }
-        CHM_WARP_WAIT(wait_eq(sy, w.pflag + p, epoch, who));
+        // panels before the window were published by an earlier launch
+        if (p >= w.blk0) CHM_WARP_WAIT(wait_eq(sy, w.pflag + p, epoch, who));
         if (lastTile) CHM_TRACE(1);
         cf[lane] = ld_coef(w.coef + (size_t)p * kW + lane);
         if (lastTile && w.has_next) ch[lane] = ld_chain(w.chain + (size_t)p * kW + lane);
@@ -508,7 +514,7 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
     const long long n = w.n, ld = w.ld;
     const int epoch = sy.epoch;
     const long long who = -1;
-    for (int b = warp; b < w.nb; b += 4) {
+    for (int b = w.blk0 + warp; b < w.blk1; b += 4) {
         const long long c0 = (long long)b * kW;
         const int ncols = (int)min((long long)kW, n - c0);
         CHM_WARP_WAIT(wait_eq(sy, w.dflag_prev + b, epoch, who));
@@ -522,8 +528,9 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
     }
     // the pair is done only when its column tasks are: idle sweep warps stop
     // once every pair is done, so none of those tasks may still be unclaimed
-    if (warp == 0 && w.nb > 1) {
-        const long long want = ((long long)epoch << 32) + (w.nb - 1);
+    const int ntasks = w.blk1 - max(w.blk0, 1);
+    if (warp == 0 && ntasks > 0) {
+        const long long want = ((long long)epoch << 32) + ntasks;
         CHM_WARP_WAIT(wait_ge(sy, w.final_done, want, who));
     }
 }
@@ -552,10 +559,11 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
     const int epoch = sy.epoch;
     const long long ep64 = (long long)epoch << 32;
     volatile int *cdone = &S.cdone;
-    int next_fetch = 0, next_fin = 0;
+    int next_fetch = w.blk0, next_fin = w.blk0;
+    const int nb_end = w.blk1;
     long long idle_since = -1;
     unsigned idle_iters = 0;
-    while (next_fin < nb) {
+    while (next_fin < nb_end) {
         bool progressed = false;
         // finish block next_fin once warp C has rotated it
         if (next_fin < next_fetch && __shfl_sync(FULL, *cdone > next_fin ? 1 : 0, 0)) {
@@ -587,7 +595,7 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
             progressed = true;
         }
         // fetch the inputs of block next_fetch once they are published and its slot is free
-        if (next_fetch < nb && next_fetch - next_fin < kSlots) {
+        if (next_fetch < nb_end && next_fetch - next_fin < kSlots) {
             const int b = next_fetch, s = b % kSlots;
             int ready = 1;
             if (lane == 0) {
@@ -654,7 +662,7 @@ __device__ void wave_chain(const Wave<T> &w, WaveSmem<T> &S)
     const unsigned FULL = 0xffffffffu;
     const SyncArgs &sy = w.sync;
     const long long who = -1;
-    for (int b = 0; b < w.nb; ++b) {
+    for (int b = w.blk0; b < w.blk1; ++b) {
         CHM_SEQ_WAIT(&S.zseq, b + 1);
         CHM_WTRACE(b, 8);
         double(*R)[kW] = S.R[b % kSlots];
@@ -686,8 +694,14 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
     const long long who = -1;
     double pprev = 0.0;  // p of the block last chained, row `lane`
     double Tend = 1.0, iTend = 1.0;
+    if (w.blk0 > 0) {    // the chain state where the previous window ended
+        Tend = __ldcg(w.carry);
+        iTend = __ldcg(w.carry + 1);
+        pprev = __ldcg(w.carry + 2 + lane);
+    }
     int pending = -1;    // block chained (or being chained) but not yet published
-    int next = 0;        // next block whose chain input is to be formed
+    int next = w.blk0;   // next block whose chain input is to be formed
+    const int nb_end = w.blk1;
     bool ok = true;
     auto wait_seq = [&](int *seq, int want) -> bool {
         int v = seq_wait(sy, seq, want, &S.bail, who) ? 1 : 0;  // all lanes: see CHM_WARP_WAIT
@@ -759,7 +773,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
         iTend = __shfl_sync(FULL, iTn, rows - 1);
     };
 
-    while (ok && (next < nb || pending >= 0)) {
+    while (ok && (next < nb_end || pending >= 0)) {
         if (pending < 0) {
             // nothing is being chained: form the next input (waiting for it)
             if (!wait_seq(&S.dseq, next + 1)) return;
@@ -774,7 +788,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
             const long long c0 = (long long)done * kW;
             pprev = (c0 + lane < n) ? S.cbox[lane] * S.rowd[done % kSlots][lane].id1 : 0.0;
         }
-        if (next < nb) {
+        if (next < nb_end) {
             const int ready = __shfl_sync(FULL, *reinterpret_cast<volatile int *>(&S.dseq) >= next + 1 ? 1 : 0, 0);
             if (ready) {
                 __threadfence_block();
@@ -783,6 +797,14 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
             }
         }
         publish(done, pprev);
+    }
+    // the chain state for this wave's next window
+    if (w.blk1 < nb) {
+        if (lane == 0) {
+            __stcg(w.carry, Tend);
+            __stcg(w.carry + 1, iTend);
+        }
+        __stcg(w.carry + 2 + lane, pprev);
     }
 }
 
@@ -854,14 +876,22 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
 constexpr int kRoleIdle = 0, kRoleWave = 1, kRoleSweep = 2;
 __device__ __forceinline__ int role_code(int role, int group) { return role | (group << 4); }
 
-// Column blocks of pair j that carry sweep tasks: [first, nb).
+// Column blocks of pair j that carry sweep tasks: [first, nb) within the
+// launch's window.
 template <typename T>
 __device__ __forceinline__ void task_range(const Launch<T> &P, int j, int *first, int *nb)
 {
     const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
     const Prob *pr = P.probs ? P.probs + i : &P.prob0;
-    *first = j > pr->pair0 ? 1 : 0;  // block 0 of a later wave has no off-diagonal tile
-    *nb = pr->nb;
+    *first = max(j > pr->pair0 ? 1 : 0, pr->blk0);  // block 0 of a later wave has no off-diagonal tile
+    *nb = pr->blk1;
+}
+// First column block of pair j's window.
+template <typename T>
+__device__ __forceinline__ int window_start(const Launch<T> &P, int j)
+{
+    const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
+    return P.probs ? P.probs[i].blk0 : P.prob0.blk0;
 }
 
 // Take one sweep task: the warp's own group first, then the other groups'
@@ -911,7 +941,7 @@ template <typename T>
 __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
 {
     extern __shared__ __align__(16) unsigned char chm_smem[];
-    __shared__ int s_role, s_pair, s_last;
+    __shared__ int s_role, s_pair, s_last, s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *ctl = P.ctl;
     SyncArgs sy;  // launch-level waits
@@ -973,7 +1003,10 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
                     __threadfence();
                     atomicExch(gt, (unsigned long long)kGroupDone << 32);
                 } else {
-                    S.dseq = S.zseq = S.cseq = S.bseq = S.cdone = S.fseq = S.bail = 0;
+                    // sequence counters count blocks; the window starts at s0
+                    const int s0 = window_start(P, j);
+                    S.dseq = S.zseq = S.cseq = S.bseq = S.cdone = S.fseq = s0;
+                    S.bail = 0;
                     __threadfence();
                     atomicExch(gt, (unsigned long long)(j + 1) << 32);
                 }
@@ -1033,6 +1066,18 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
     __syncthreads();
     if (s_last) {
         __threadfence();
+        // A wait that ran out aborted the whole launch: every problem that
+        // recorded nothing stopped unfinished, so it is marked too (info -5:
+        // stopped by another problem's failure) and none reads as complete.
+        if (threadIdx.x == 0) s_abort = ld_relaxed_gpu(ctl + kCtlAbort);
+        __syncthreads();
+        if (s_abort) {
+            for (int i = threadIdx.x; i < P.nprobs; i += blockDim.x) {
+                long long *info = P.probs ? P.probs[i].info : P.prob0.info;
+                if (info) record_one(info, kStatusTimeout, -5);
+            }
+        }
+        __syncthreads();
         for (int i = threadIdx.x; i < kCtlInts; i += blockDim.x)
             if (i != kCtlEpoch) ctl[i] = 0;
         __syncthreads();

@@ -33,11 +33,13 @@ CHILD = textwrap.dedent("""
     # 1. panel of block 3 never released: the launch must end by timeout
     L = L0.cuda()
     t0 = time.time()
-    assert chm.modify(L, V.cuda(), 1) == chm.CHM_OK
+    d_info = torch.full((2,), 99, dtype=torch.int64, device="cuda")
+    assert chm.modify(L, V.cuda(), 1, d_info=d_info) == chm.CHM_OK
     st, info = chm.status_sync()
     dt = time.time() - t0
-    print("timeout run: status", st, "info", info, "seconds %%.3f" %% dt)
+    print("timeout run: status", st, "info", info, "seconds %%.3f" %% dt, "per-call", d_info.tolist())
     assert st == chm.CHM_ERR_TIMEOUT, st
+    assert int(d_info[0]) == chm.CHM_ERR_TIMEOUT   # the call's own word says so too
     assert dt < 30.0
     # 2. the next launch is normal and correct
     L = L0.cuda()
