@@ -62,7 +62,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # kernel from an ncu capture of this workload (profiles/), keyed by the
 # sha256 (first 16 hex digits) of the kernel sources it was taken with; a
 # capture of an older kernel version reads as null.
-NCU_TRAFFIC = {("wave_kernel<double>", "2aa93a099476245b"): 433.42e6}
+NCU_TRAFFIC = {("wave_kernel<double>", "51eacc54f4d4c362"): 385.52e6}
 KERNEL_SOURCES = ("paper_1011_1173_gb300/csrc/chm_wave.cuh", "paper_1011_1173_gb300/csrc/chm_device.cuh",
                   "paper_1011_1173_gb300/csrc/chm_layout.h", "paper_1011_1173_gb300/csrc/chm_modify.cu")
 
@@ -148,6 +148,7 @@ def bench_batch(dev, autotune=False, count=512, reps=5, mixed=False):
     pre = chm.BatchPlan(ns.tolist(), ns.tolist(), [int(k) if s < 0 else 0 for k, s in zip(ks, sg)],
                         [1] * count, code)
     chm.check(pre.execute(Ls, Vs, stream), "batch pre-update")
+    chm.check(pre.status()[0], "batch pre-update status")
     fwd = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), sg.tolist(), code)
     inv = chm.BatchPlan(ns.tolist(), ns.tolist(), ks.tolist(), (-sg).tolist(), code)
     if autotune:

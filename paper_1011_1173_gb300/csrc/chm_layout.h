@@ -77,9 +77,14 @@ CHM_HD inline size_t prob_iflags(int nb, int k) { return ((size_t)(2 * k + 1) * 
 // [nb][kW][2] the carry u_hat at the diagonal block (payload: the high and
 // the low half of a double).  A reader takes a carry once both halves carry
 // the current epoch, so the writer needs no fence.
-// The last word counts the final pass's finished column tasks (payload).
+// Then one word counts the final pass's finished column tasks (payload),
+// and one word per pair (its k waves, then the final pass) counts the
+// pair's column tasks handed out (payload); the wave block that takes the
+// pair sets it to (epoch << 32) before announcing the pair.
 constexpr int kTagsPerBlock = 1 + 4 * kW;
-CHM_HD inline size_t prob_progress(int nb, int k) { return ((size_t)k * nb * kTagsPerBlock + 1 + 31) & ~(size_t)31; }
+CHM_HD inline size_t prob_final_done(int nb, int k) { return (size_t)k * nb * kTagsPerBlock; }
+CHM_HD inline size_t prob_ticket(int nb, int k, int q) { return prob_final_done(nb, k) + 1 + (size_t)q; }
+CHM_HD inline size_t prob_progress(int nb, int k) { return (prob_ticket(nb, k, k + 1) + 31) & ~(size_t)31; }
 
 // One problem of a launch (L and V of the launch's element type).
 struct Prob {
@@ -110,7 +115,7 @@ constexpr int kCtlStarted = 3;    // blocks started
 constexpr int kCtlExited = 4;     // blocks finished
 constexpr int kCtlEpoch = 8;      // launch counter; flags of this launch equal it
 constexpr int kCtlAbort = 32;     // non-zero once a wait has timed out
-constexpr int kCtlGroupTicket = 64;                                  // u64 [kMaxGroups]: (pair + 1) << 32 | task
+constexpr int kCtlGroupTicket = 64;                                  // u64 [kMaxGroups]: (current pair + 1) << 32
 constexpr int kCtlGroupSweepers = kCtlGroupTicket + 2 * kMaxGroups;  // [kMaxGroups] sweep SMs per group
 constexpr int kCtlSmSlot = kCtlGroupSweepers + kMaxGroups;           // [kMaxSm] arrivals per SM
 constexpr int kCtlSmRole = kCtlSmSlot + kMaxSm;                      // [kMaxSm] 1 + role of the SM

@@ -135,7 +135,7 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.progress_prev = q > 0 ? w.progress - nb : nullptr;
     w.ztag = pr.progress + (size_t)pr.k * nb + (size_t)q * nb * kW * 2;
     w.ctag = pr.progress + (size_t)pr.k * nb * (1 + kW * 2) + (size_t)q * nb * kW * 2;
-    w.final_done = pr.progress + (size_t)pr.k * nb * kTagsPerBlock;
+    w.final_done = pr.progress + prob_final_done(nb, pr.k);
     if (P.trace) {
         const size_t row = (size_t)j * P.nbmax * kTracePoints;
         w.trace_sweep = P.trace + row;
@@ -877,14 +877,15 @@ constexpr int kRoleIdle = 0, kRoleWave = 1, kRoleSweep = 2;
 __device__ __forceinline__ int role_code(int role, int group) { return role | (group << 4); }
 
 // Column blocks of pair j that carry sweep tasks: [first, nb) within the
-// launch's window.
+// launch's window; returns the pair's ticket word.
 template <typename T>
-__device__ __forceinline__ void task_range(const Launch<T> &P, int j, int *first, int *nb)
+__device__ __forceinline__ unsigned long long *task_range(const Launch<T> &P, int j, int *first, int *nb)
 {
     const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
     const Prob *pr = P.probs ? P.probs + i : &P.prob0;
     *first = max(j > pr->pair0 ? 1 : 0, pr->blk0);  // block 0 of a later wave has no off-diagonal tile
     *nb = pr->blk1;
+    return reinterpret_cast<unsigned long long *>(pr->progress + prob_ticket(pr->nb, pr->k, j - pr->pair0));
 }
 // First column block of pair j's window.
 template <typename T>
@@ -894,42 +895,58 @@ __device__ __forceinline__ int window_start(const Launch<T> &P, int j)
     return P.probs ? P.probs[i].blk0 : P.prob0.blk0;
 }
 
-// Take one sweep task: the warp's own group first, then the other groups'
-// current pairs.  Stealing cannot stall the launch: pairs are taken in
-// increasing order and a pair's tasks wait only on lower pairs, so a task
-// stolen from a running pair never waits on the pair its warp's group takes
-// next, and the lowest running pair always has its group's warps free for
-// it.  Each ticket word is read before it is incremented, so a group whose pair
-// has no task left is not counted up.  The ticket the increment returns is
-// the one taken, whatever pair it belongs to: the group may have moved to
-// its next pair between the read and the increment, and a ticket of that
-// pair counted up here must be run here, or its column block would never be
-// rotated.  A count on a word without a pair (none yet, or the group is
-// done) is erased when the group takes its next pair.  Returns the pair (or
-// -1) and the column block; all lanes get the same answer.
+// Take one sweep task: from the own group's current pair first, then, when
+// it has no task left, from another group's pair that is lower than the own
+// group's current pair; a warp whose group has no pair yet takes nothing,
+// and one whose group takes no more pairs may take from any pair.  A group
+// word names the group's current pair; a pair's tasks are handed out by its
+// own ticket word, so an increment always yields a task of the pair that
+// was looked at (or nothing), whatever the groups do meanwhile.
+//
+// Why the launch cannot stall: every warp holds only tasks of pairs up to
+// its group's current pair (tasks of that pair, or of lower pairs).  A
+// pair's tasks wait only on lower pairs, so the lowest running pair's group
+// holds tasks of finished pairs (which end without waiting) or of its own
+// pair, and its warps always come back to its pair's remaining tasks.
+// Without the bound the launch can stall: groups take pairs from the
+// counter in one order and name them in another, so warps of the group that
+// took pair j but has not named it yet can all take tasks of pair j + 1,
+// which wait for pair j's first tasks, which only those warps would take.
+// (Seen on the GPU: no task of wave 0 started, every warp held a task of a
+// later wave, the launch ended in CHM_ERR_TIMEOUT.)
+//
+// A ticket word is read first, so that an exhausted pair is not counted up;
+// one whose epoch tag is not this launch's is not yet set up and is looked
+// at again later.  Returns the pair (or -1) and the column block; all lanes
+// get the same answer.
 template <typename T>
-__device__ __forceinline__ int take_task(const Launch<T> &P, int group, int *block)
+__device__ __forceinline__ int take_task(const Launch<T> &P, int group, long long ep64, int *block)
 {
-    unsigned long long *gts = reinterpret_cast<unsigned long long *>(P.ctl + kCtlGroupTicket);
+    const long long *gts = reinterpret_cast<const long long *>(P.ctl + kCtlGroupTicket);
     const int lane = threadIdx.x & 31;
+    const long long tagmask = ~0xffffffffll;
     int j = -1, b = -1;
+    const unsigned own = (unsigned)((unsigned long long)ld_relaxed_gpu(gts + group) >> 32);  // pair + 1
+    if (own == 0u) {  // no pair yet: nothing may be taken
+        *block = -1;
+        return -1;
+    }
+    const bool bounded = own != kGroupDone;
     for (int d = 0; d < P.ngroups && j < 0; ++d) {
         int g = group + d;
         if (g >= P.ngroups) g -= P.ngroups;
-        const unsigned long long v = (unsigned long long)ld_relaxed_gpu(reinterpret_cast<const long long *>(gts + g));
-        const unsigned hi = (unsigned)(v >> 32);
+        const unsigned hi = d == 0 ? own : (unsigned)((unsigned long long)ld_relaxed_gpu(gts + g) >> 32);
         if (hi == 0u || hi == kGroupDone) continue;
+        if (d > 0 && bounded && hi >= own) continue;  // only pairs below the own group's
         int first = 0, nb = 0;
-        task_range(P, (int)hi - 1, &first, &nb);
-        if ((long long)(unsigned)v + first >= nb) continue;
-        unsigned long long v2 = 0;
-        if (lane == 0) v2 = atomicAdd(gts + g, 1ull);
+        unsigned long long *tk = task_range(P, (int)hi - 1, &first, &nb);
+        const long long v = ld_relaxed_gpu(reinterpret_cast<const long long *>(tk));
+        if ((v & tagmask) != ep64 || (long long)(unsigned)v + first >= nb) continue;
+        long long v2 = 0;
+        if (lane == 0) v2 = (long long)atomicAdd(tk, 1ull);
         v2 = __shfl_sync(0xffffffffu, v2, 0);
-        const unsigned hi2 = (unsigned)(v2 >> 32);
-        if (hi2 == 0u || hi2 == kGroupDone) continue;
-        if (hi2 != hi) task_range(P, (int)hi2 - 1, &first, &nb);
-        if ((long long)(unsigned)v2 + first < nb) {
-            j = (int)hi2 - 1;
+        if ((v2 & tagmask) == ep64 && (long long)(unsigned)v2 + first < nb) {
+            j = (int)hi - 1;
             b = (int)(unsigned)v2 + first;
         }
     }
@@ -981,6 +998,8 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
     __syncthreads();
     const int role = s_role & 15, group = s_role >> 4;
     unsigned long long *gt = reinterpret_cast<unsigned long long *>(ctl + kCtlGroupTicket) + group;
+    // this launch's tag (the epoch changes only when the launch's last block ends)
+    const long long ep64 = (long long)ld_relaxed_gpu(ctl + kCtlEpoch) << 32;
 
     if (role == kRoleWave) {
         WaveSmem<T> &S = *reinterpret_cast<WaveSmem<T> *>(chm_smem);
@@ -1007,6 +1026,9 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
                     const int s0 = window_start(P, j);
                     S.dseq = S.zseq = S.cseq = S.bseq = S.cdone = S.fseq = s0;
                     S.bail = 0;
+                    // the pair's ticket word starts at this launch's tag before the pair is named
+                    int f_ = 0, n_ = 0;
+                    st_relaxed_gpu(reinterpret_cast<long long *>(task_range(P, j, &f_, &n_)), ep64);
                     __threadfence();
                     atomicExch(gt, (unsigned long long)(j + 1) << 32);
                 }
@@ -1034,7 +1056,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
         for (;;) {
             if (aborted(sy)) break;
             int b = -1;
-            const int j = take_task(P, group, &b);
+            const int j = take_task(P, group, ep64, &b);
             if (j >= 0) {
                 const Wave<T> w = make_wave(P, j);
                 if (w.unscale) unscale_task<T>(w, b);

@@ -1,12 +1,13 @@
 """Many launches in a row must all finish without a device-side error.
 
-The launch schedules sweep tasks from per-group ticket words while the
-groups take (factor, wave) pairs in order; a lost ticket or a task taken in
-an order that waits on its own warp's next pair would stall the launch until
-its bounded waits run out (CHM_ERR_TIMEOUT).  Such races are rare per
-launch, so this runs a few hundred launches of shapes with many pairs per
-launch and checks every status, and that an even number of alternating
-update/downdate launches returns close to the start."""
+The launch hands out sweep tasks from per-pair ticket words while SM groups
+take (factor, wave) pairs in order; a lost ticket, or warps filling up with
+tasks of a pair whose previous wave's tasks then find no warp, would stall
+the launch until its bounded waits run out (CHM_ERR_TIMEOUT).  Such a stall
+depends on timing and shows in some launches only, so this runs a few
+hundred launches of single factors and of many-factor batches and checks
+every status, and that an even number of alternating update/downdate
+launches returns close to the start."""
 from __future__ import annotations
 
 import numpy as np
@@ -43,3 +44,30 @@ def test_repeated_launches_all_finish(n, k, dtype, reps):
     tol = 1e-9 if dtype == torch.float64 else 1e-3
     m = min(n, 512)
     assert colscaled_err(L[:m, :m].double().cpu().numpy(), L0[:m, :m].double().cpu().numpy()) <= tol
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_repeated_many_factor_batches_all_finish(dtype):
+    """The batched workload's shape (many factors of uneven order in one
+    launch, the default many-group configuration): every execution of a
+    run of update and downdate batches must finish."""
+    rng = np.random.default_rng(31)
+    count = 256
+    ns = np.exp(rng.uniform(np.log(64), np.log(4096), count)).astype(int).tolist()
+    ks = rng.choice([1, 4, 16], count).tolist()
+    Ls = [inputs.random_factor(n, 900 + i, device="cuda", dtype=dtype) for i, n in enumerate(ns)]
+    Vs = [inputs.update_block(n, k, 900 + i, device="cuda", scale=0.3 / np.sqrt(n * k)).to(dtype)
+          for i, (n, k) in enumerate(zip(ns, ks))]
+    code = chm.CHM_F64 if dtype == torch.float64 else chm.CHM_F32_MIXED
+    up = chm.BatchPlan(ns, ns, ks, [1] * count, code)
+    down = chm.BatchPlan(ns, ns, ks, [-1] * count, code)
+    bad = []
+    for r in range(24):
+        plan = up if r % 2 == 0 else down
+        assert plan.execute(Ls, Vs) == chm.CHM_OK
+        st, infos = plan.status()
+        if st != chm.CHM_OK:
+            bad.append((r, st, sorted(set(tuple(x) for x in infos))[:4]))
+    up.close()
+    down.close()
+    assert not bad, bad[:3]
