@@ -22,10 +22,12 @@ constexpr int kMaxSm = 1024;
 constexpr int kMaxGroups = 128;
 constexpr int kTracePoints = 16;
 
-// Sweep coefficients of one row of one wave, in the Apply type T.
+// Sweep coefficients of one row of one wave, in the Apply type T: the
+// rotation's a and b, the new row scale e1, and g = e p (the row's old scale
+// times the chain's p), with which a column's carry z drops the row's term.
 template <typename T>
 struct CoefRow {
-    T a, b, e1, pad;
+    T a, b, e1, g;
 };
 
 // Row data of one wave (double): new row scale and its inverse, new

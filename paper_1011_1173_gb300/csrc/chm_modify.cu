@@ -116,15 +116,18 @@ int wave_occupancy(int dtype, int dev, int *ctas_per_sm)
     return dtype == CHM_F64 ? occupancy<double>(dev, ctas_per_sm) : occupancy<float>(dev, ctas_per_sm);
 }
 
-// Groups: one per concurrently running wave.  One problem: about eight sweep
-// SMs per group (its waves share the sweep work of one factor); many
-// independent problems: two sweep SMs per group, since more chains in flight
-// matter more than sweep capacity per chain (measured on the batched
-// workload: 50 groups 31 ms, 16 groups 59 ms).
+// Groups: one per concurrently running wave.  One problem: about seven sweep
+// SMs per group (its waves share the sweep work of one factor), and up to
+// nsm / 8 groups, so that a rank-16 modification runs all its waves and its
+// final pass at once (measured at n = 5000, k = 16: 17 groups 1.88 ms, 16
+// groups 1.99 ms, 12 groups 2.43 ms); many independent problems: two sweep
+// SMs per group, since more chains in flight matter more than sweep
+// capacity per chain (measured on the batched workload: 50 groups 31 ms,
+// 16 groups 59 ms).
 int default_groups(int npairs, int nsm, int nprobs)
 {
     int g = env_int("CHM_GROUPS");
-    if (g <= 0) g = std::max(1, nprobs > 1 ? nsm / 3 : nsm / 9);
+    if (g <= 0) g = std::max(1, nprobs > 1 ? nsm / 3 : nsm / 8);
     return std::max(1, std::min(std::min(g, npairs), std::min(kMaxGroups, nsm / 2)));
 }
 

@@ -29,9 +29,10 @@
 //       B  the 32-row dot product that carries the previous block's p into
 //          this block, then p, T and the rotation coefficients, and the
 //          publication of the block's panel;
-//       C  the wave's rotations inside the diagonal block, the next wave's
-//          ratio matrix of that block, and its store;
-//       D  prefetch of the next block's inputs (cp.async).
+//       C  the wave's rotations inside the diagonal block and the next
+//          wave's ratio matrix of that block;
+//       D  prefetch of the next blocks' inputs (cp.async), the store of
+//          each rotated diagonal tile and the block's release.
 //   * every warp of the group's sweep blocks takes tasks (column block b of
 //     the group's current pair) from the group's ticket word and rotates the
 //     block's off-diagonal tiles with the pair's panels, the update vector
@@ -168,7 +169,6 @@ struct WaveSmem {
     CoefRow<T> cf[kSlots][kW];  // B -> C: sweep coefficients of the block
     ChainRow cnew[kSlots][kW];  // B -> C, D: row data after this wave
     T DT[kW][kW + 1];           // C -> D: the rotated diagonal tile, [c][r]
-    double F[kW];               // D: -e'_r / D'_r of the block being finished
     int dseq;                   // D: inputs of blocks < dseq fetched
     int zseq;                   // B: chain inputs of blocks < zseq formed
     int cseq;                   // A: blocks < cseq chained
@@ -206,11 +206,11 @@ __device__ __forceinline__ void st_coef(CoefRow<double> *p, const CoefRow<double
 {
     double2 *q = reinterpret_cast<double2 *>(p);
     __stcg(q, make_double2(c.a, c.b));
-    __stcg(q + 1, make_double2(c.e1, c.pad));
+    __stcg(q + 1, make_double2(c.e1, c.g));
 }
 __device__ __forceinline__ void st_coef(CoefRow<float> *p, const CoefRow<float> &c)
 {
-    __stcg(reinterpret_cast<float4 *>(p), make_float4(c.a, c.b, c.e1, c.pad));
+    __stcg(reinterpret_cast<float4 *>(p), make_float4(c.a, c.b, c.e1, c.g));
 }
 __device__ __forceinline__ ChainRow ld_chain(const ChainRow *p)
 {
@@ -386,6 +386,7 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
     // stores are issued, when the previous wave has released it, so that its
     // load overlaps the acknowledgement the progress release waits for.
     bool staged = false;
+    double tz = 1.0;  // T after block b - 3 (1 before the first block): the scale of the carry z
     for (int p = 0; p < b; ++p) {
         const bool lastTile = p == b - 1;
         if (!staged) {
@@ -403,11 +404,21 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
         if (lastTile) CHM_TRACE(1);
         cf[lane] = ld_coef(w.coef + (size_t)p * kW + lane);
         if (lastTile && w.has_next) ch[lane] = ld_chain(w.chain + (size_t)p * kW + lane);
-        const double tnext = (p == b - 2) ? __ldcg(w.tend + p) : 0.0;
+        if (p == b - 3) tz = __ldcg(w.tend + p);
         __syncwarp();
         T S[kW];
 #pragma unroll
         for (int r = 0; r < kW; ++r) S[r] = tile[lane][r];
+        if (p == b - 2) {
+            // the wave block's carry for block b, z after rows < (b - 1) kW, put
+            // before this tile's rotations: T u_hat after the rows above the
+            // tile, less the tile rows' terms F_rj p_r = g_r S_rj
+            T zt = T(0);
+#pragma unroll
+            for (int r = 0; r < kW; ++r) zt = fma(cf[r].g, S[r], zt);
+            put_tagged(w.ztag + ((size_t)b * kW + lane) * 2, active ? tz * (double)uh - (double)zt : 0.0, ep64);
+            CHM_TRACE(4);
+        }
         if (active) {
 #pragma unroll
             for (int r = 0; r < kW; ++r) {
@@ -416,8 +427,6 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
                 uh = fma(-c.b, S[r], uh);
             }
         }
-        if (p == b - 2)  // the wave block's carry for block b: z = T u_hat after rows < (b-1) kW
-            put_tagged(w.ztag + ((size_t)b * kW + lane) * 2, active ? tnext * (double)uh : 0.0, ep64);
         if (lastTile) {  // u_hat entering the diagonal block, for the wave block's rotations there
             put_tagged(w.ctag + ((size_t)b * kW + lane) * 2, active ? (double)uh : 0.0, ep64);
             CHM_TRACE(2);
@@ -545,9 +554,11 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
 
 // Warp D: the wave block's memory traffic.  It fetches each block's inputs
 // for warps A, B and C into slot b % kSlots (up to kSlots - 1 blocks ahead)
-// and finishes each block warp C has rotated: the next wave's chain ratios,
-// the store of the diagonal tile and the release of the block to the next
-// wave.  Neither job blocks the other: the warp polls both.
+// and finishes each block warp C has rotated: the store of the diagonal
+// tile and the release of the block to the next wave.  Neither job blocks
+// the other: the warp polls both, and the finish is short (the FP64 work of
+// a block stays with warp C) so that a fetch on the critical path is not
+// held up behind it.
 template <typename T>
 __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
 {
@@ -568,22 +579,9 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
         // finish block next_fin once warp C has rotated it
         if (next_fin < next_fetch && __shfl_sync(FULL, *cdone > next_fin ? 1 : 0, 0)) {
             __threadfence_block();
-            const int b = next_fin, s = b % kSlots;
+            const int b = next_fin;
             const long long c0 = (long long)b * kW;
             const int ncols = (int)min((long long)kW, n - c0);
-            const bool active = lane < ncols;
-            if (w.has_next) {
-                // next wave's chain ratios for this block: S'_rc (-e'_r / D'_r), r < c
-                const ChainRow cn = S.cnew[s][lane];
-                S.F[lane] = -cn.e1 * cn.id1;
-                __syncwarp();
-                double *rd = w.rdiag_next + (size_t)b * kW * kW;
-#pragma unroll
-                for (int r = 0; r < kW; ++r) {
-                    const double v = (r < lane && active) ? (double)S.DT[lane][r] * S.F[r] : 0.0;
-                    __stcg(rd + (size_t)r * kW + lane, v);
-                }
-            }
 #pragma unroll
             for (int c = 0; c < kW; ++c)
                 if (lane <= c && c < ncols) __stcg(w.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
@@ -753,7 +751,7 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
         const double ratio = Tn * iTp;           // c^2
         const double rc = rsqrt_refined(ratio);  // 1/c
         const double c = ratio * rc;
-        const CoefRow<T> cr{(T)(sgd * p * rowd.ie1), (T)(p * rowd.e1 * iTn), (T)(rowd.e1 * rc), T(0)};
+        const CoefRow<T> cr{(T)(sgd * p * rowd.ie1), (T)(p * rowd.e1 * iTn), (T)(rowd.e1 * rc), (T)(p * rowd.e1)};
         const ChainRow nrow{rowd.e1 * rc, rowd.ie1 * c, rowd.d1 * c, rowd.id1 * rc};
         // the block's global row data first: everything warps C and D later
         // release at GPU scope (the next wave's inputs) is ordered after it
@@ -808,8 +806,8 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
     }
 }
 
-// Warp C: the wave's rotations inside each diagonal block; warp D stores
-// the result.
+// Warp C: the wave's rotations inside each diagonal block and the next
+// wave's chain ratios of the block; warp D stores the rotated tile.
 template <typename T>
 __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
 {
@@ -864,8 +862,20 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
 #pragma unroll
         for (int r = 0; r < kW; ++r)
             if (r < lane) S.DT[lane][r] = Sv[r];
-        if (active) S.DT[lane][lane] = (T)S.cnew[s][lane].d1;
+        const ChainRow cn = S.cnew[s][lane];
+        if (active) S.DT[lane][lane] = (T)cn.d1;
         __syncwarp();
+        if (w.has_next) {
+            // next wave's chain ratios for this block: S'_rc (-e'_r / D'_r), r < c;
+            // warp D's release of the block orders these stores for the next wave
+            const double f = -cn.e1 * cn.id1;
+            double *rd = w.rdiag_next + (size_t)b * kW * kW;
+#pragma unroll
+            for (int r = 0; r < kW; ++r) {
+                const double fr = __shfl_sync(0xffffffffu, f, r);
+                __stcg(rd + (size_t)r * kW + lane, (r < lane && active) ? (double)Sv[r] * fr : 0.0);
+            }
+        }
         if (lane == 0) seq_post(&S.cdone, b + 1);
     }
 }
