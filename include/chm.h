@@ -129,11 +129,12 @@ int chm_modify_ex(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, in
 
 /*
  * Same operation and arguments as chm_modify_ex, for callers that cannot
- * allocate device memory: code running where cudaMalloc is not permitted or
- * must not be called (inside CUDA-graph stream capture, from a real-time or
- * memory-budgeted host thread that owns all device memory itself, or under an
- * allocator that forbids allocations outside its own pool).  It calls no
- * cudaMalloc, cudaFree or allocating library routine.  The paper has no
+ * allocate device memory: code that must not call cudaMalloc, such as a
+ * real-time or memory-budgeted host thread whose process has handed all
+ * device memory to its own allocator, or an application whose allocator
+ * forbids allocations outside its own pool (cudaMalloc can block, fail under
+ * the budget, or synchronise the device).  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.  The paper has no
  * counterpart; this is a deployment variant of the same computation.
  *
  * Scratch: a file-scope device array of 16 MiB that every GPU which loads

@@ -1,8 +1,8 @@
 """The no-allocation entry point, chm_modify_noalloc.
 
-Some callers cannot allocate device memory (inside CUDA-graph capture,
-under an allocator that owns all device memory, from budgeted real-time
-threads).  chm_modify_noalloc serves them from a fixed device array; these
+Some callers cannot allocate device memory (under an allocator that owns
+all device memory, or from budgeted real-time threads where cudaMalloc can
+block, fail or synchronise the device).  chm_modify_noalloc serves them from a fixed device array; these
 tests call it through the C ABI and check its factor against chm_modify_ex's
 on two calls in a row.  This file is collected last so that a run stopping
 at the first failure has already run every other test.
