@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="time the batch plan's default configuration")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-factors", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=0,
+                    help="served requests before the measured ones (left out of rates and latencies)")
     ap.add_argument("--serve-loads", default="0.9",
                     help="offered loads as fractions of the plain path's saturation rate, comma separated")
     ap.add_argument("--no-batch-mixed", action="store_true")
@@ -312,10 +314,12 @@ def bench_host_resident(dev, L0, V, reps=3):
             "device_workspace_bytes": chm.workspace_bytes(n, k)}
 
 
-def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.9,)):
+def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.9,), warm=0):
     """Served requests (chm_server_*) against plain launches serialised on one
     stream, at each offered load (a fraction of the plain path's measured
-    saturation rate); the same request sequence is replayed at every load."""
+    saturation rate); the same request sequence is replayed at every load.
+    The first ``warm`` requests of each run are served but left out of the
+    reported rates and latencies."""
     import numpy as np
     import torch
 
@@ -332,7 +336,8 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
     # request sequence: factor Zipf(1.1) over a permutation, k ~ U{1..32},
     # 70 % updates with a fresh V, 30 % downdates of the latest applied V
     reqs, hist = [], {}
-    for r in range(nreq):
+    total = warm + nreq
+    for r in range(total):
         f = int(perm[min(nfactors - 1, rng.zipf(1.1) - 1)])
         n = int(ns[f])
         if rng.random() < 0.3 and hist.get(f):
@@ -348,7 +353,7 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
         return {f: inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt) for f in used}
 
     bytes_req = [alg_bytes(int(ns[f]), V.shape[0], 4) for f, V, _ in reqs]
-    tot = float(sum(bytes_req))
+    tot = float(sum(bytes_req[warm:]))
     # plain saturation rate: back-to-back launches on one stream
     stream = torch.cuda.current_stream()
     plainL = plain_copies()
@@ -362,20 +367,23 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
     results = []
     for load in loads:
         rate = load * sat
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
         plainL = plain_copies()
         torch.cuda.synchronize()
         st0 = srv.stats()
         # served run: the host submits at the arrival times
         t_start = time.perf_counter()
+        measured = set()
         for j, (f, V, s) in enumerate(reqs):
             while time.perf_counter() - t_start < arrivals[j]:
                 pass
-            srv.submit(f, V, s)
+            rid = srv.submit(f, V, s)
+            if j >= warm:
+                measured.add(rid)
         chm.check(srv.drain(600.0), "serve drain")
-        t_serve = time.perf_counter() - t_start
-        done = srv.poll(nreq + 16)
-        lat_srv = [d[2] * 1e3 for d in done]
+        t_serve = time.perf_counter() - t_start - (arrivals[warm] if warm else 0.0)
+        done = srv.poll(total + 16)
+        lat_srv = [d[2] * 1e3 for d in done if d[0] in measured]
         bad = sum(1 for d in done if d[1] != chm.CHM_OK)
         st = srv.stats()
 
@@ -396,8 +404,8 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
         torch.cuda.synchronize()
         t_plain = time.perf_counter() - t_start
         chm.check(chm.status_sync(stream)[0], "plain status")
-        lat_plain = [a0.elapsed_time(e) - arrivals[j] * 1e3 for j, e in enumerate(evs)]
-        t_plain = max(t_plain, a0.elapsed_time(evs[-1]) / 1e3)
+        lat_plain = [a0.elapsed_time(e) - arrivals[j] * 1e3 for j, e in enumerate(evs)][warm:]
+        t_plain = max(t_plain, a0.elapsed_time(evs[-1]) / 1e3) - (arrivals[warm] if warm else 0.0)
         del plainL
         results.append({
             "offered_load": load, "offered_rate_rps": rate,
@@ -412,9 +420,9 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
     del reqs, hist
     torch.cuda.empty_cache()
     out = {"workload": "%d resident factors, n log-uniform [256, 8192], float32 storage + float64 Compute, "
-                       "%d requests, k ~ U{1..32}, factor Zipf(1.1), 70%% updates / 30%% downdates, Poisson "
-                       "arrivals at %s x the plain path's saturation rate"
-                       % (nfactors, nreq, "/".join("%g" % x for x in loads)),
+                       "%d requests after %d warm-up requests, k ~ U{1..32}, factor Zipf(1.1), 70%% updates / "
+                       "30%% downdates, Poisson arrivals at %s x the plain path's saturation rate"
+                       % (nfactors, nreq, warm, "/".join("%g" % x for x in loads)),
            "plain_saturation_rps": sat}
     if len(results) == 1:
         out.update(results[0])
@@ -660,7 +668,8 @@ def main():
         batch_mixed = bench_batch(dev, autotune=not args.no_autotune, mixed=True)
     if rank == 0 and not args.no_serve:
         loads = [float(x) for x in args.serve_loads.split(",") if x.strip()]
-        serve = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests, loads=loads)
+        serve = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests, loads=loads,
+                            warm=args.serve_warmup)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
