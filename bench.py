@@ -54,6 +54,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N, K, DTYPE = 5000, 16, "f64"
+WORKLOAD = "rank-%d update+downdate n=%d float64 (paper headline shape)"
 METRIC = "rank-k up/downdate effective HBM GB/s"
 UNIT = "GB/s"
 # Nominal FP64 rate of the part: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
@@ -525,8 +526,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
             "data": "synthetic",
-            "config": {"workload": "rank-%d update+downdate n=%d float64" % (K, N), "n": N, "k": K,
-                       "l2": "n/a (host)"},
+            "config": {"workload": WORKLOAD % (K, N), "n": N, "k": K, "ld": N,
+                       "l2": "n/a (host)", "parallelism": "single"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -681,8 +682,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
-                "config": {"workload": "rank-%d update+downdate n=%d float64 (paper headline shape)"
-                                       % (k, n), "n": n, "k": k, "ld": n,
+                "config": {"workload": WORKLOAD % (k, n), "n": n, "k": k, "ld": n,
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
