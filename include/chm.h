@@ -47,7 +47,10 @@
  *     chm_status_sync: CHM_ERR_NOT_PD (a Compute step found L_ii <= 0 or
  *     L_ii^2 + sigma V_i^2 <= 0 or a non-finite value; info = the 0-based
  *     row) and CHM_ERR_TIMEOUT (a wait between thread blocks exceeded its
- *     bound; info = the column block).  After either, L is unspecified.
+ *     bound; info = the column block whose wait ran out, or a negative code
+ *     for the launch's other waits, -5 for a problem of a batch or server
+ *     launch that stopped because another problem's wait ran out).  After
+ *     either, L is unspecified.
  *   - Memory.  The library keeps a workspace per (device, stream): per
  *     vector of a launch (at most 64 per launch) rotation panels, ratio
  *     tiles and flags of about 19 KB per 32 rows, and the status word
