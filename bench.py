@@ -54,16 +54,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N, K, DTYPE = 5000, 16, "f64"
-WORKLOAD = "rank-%d update+downdate n=%d float64 (paper headline shape)"
+
+
+def workload_name(n, k, dtype):
+    if dtype == "f32":
+        return "rank-%d update+downdate n=%d float32 storage + float64 Compute" % (k, n)
+    return "rank-%d update+downdate n=%d float64%s" % (k, n, " (paper headline shape)" if (n, k) == (N, K) else "")
 METRIC = "rank-k up/downdate effective HBM GB/s"
 UNIT = "GB/s"
 # Nominal FP64 rate of the part: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from an ncu capture of this workload (profiles/), keyed by the
-# sha256 (first 16 hex digits) of the kernel sources it was taken with; a
-# capture of an older kernel version reads as null.
-NCU_TRAFFIC = {("wave_kernel<double>", "4ab9131a4a9fb172"): 210.58e6}
+# kernel from an ncu capture of the workload (profiles/), keyed by the kernel,
+# the sha256 (first 16 hex digits) of the kernel sources it was taken with and
+# the shape (n, k); a capture of an older kernel version reads as null.
+NCU_TRAFFIC = {("wave_kernel<double>", "4ab9131a4a9fb172", 5000, 16): 210.58e6,
+               ("wave_kernel<float>", "4ab9131a4a9fb172", 8192, 16): 307.99e6}
 KERNEL_SOURCES = ("paper_1011_1173_gb300/csrc/chm_wave.cuh", "paper_1011_1173_gb300/csrc/chm_device.cuh",
                   "paper_1011_1173_gb300/csrc/chm_layout.h", "paper_1011_1173_gb300/csrc/chm_modify.cu")
 
@@ -75,6 +81,16 @@ def kernel_source_hash():
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth of the GB300s (GB/s) and its
+    source; the earlier measurement of 6800 GB/s when the file is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured: copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback: 6800 GB/s, an earlier GB300 copy measurement"
 
 
 def alg_bytes(n, k, elt=8):
@@ -92,6 +108,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chm", choices=["chm", "reference"])
+    ap.add_argument("--n", type=int, default=N, help="order of the factor (default: the paper's headline shape)")
+    ap.add_argument("--k", type=int, default=K, help="update vectors per modification")
+    ap.add_argument("--dtype", default=DTYPE, choices=["f64", "f32"],
+                    help="f64, or f32 storage with float64 Compute (then the solve and host-resident "
+                         "timings are skipped)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -486,22 +507,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n, k, budget_s=12.0, max_steps=None):
-    """Time the oracle (serial C, one core) on whole steps of the workload."""
+def cpu_baseline(n, k, budget_s=12.0, max_steps=None, dtype="f64", L0=None, V=None):
+    """Time the oracle (serial C, one core) on whole steps of the workload:
+    CholeskyModifyB in float64, or its float32-storage emulation for
+    ``dtype == "f32"``.  L0 and V (host arrays) default to the workload's
+    inputs drawn on the host."""
     import numpy as np
 
     import oracle
     from paper_1011_1173_gb300 import inputs
 
-    L0 = inputs.spd_factor(n, inputs.config_seed(1)).numpy()
-    V = inputs.update_block(n, k, inputs.config_seed(1)).numpy()
-    L = L0.copy()
+    mixed = dtype == "f32"
+    np_dt = np.float32 if mixed else np.float64
+    if L0 is None:
+        L0 = inputs.spd_factor(n, inputs.config_seed(1)).numpy()
+    if V is None:
+        V = inputs.update_block(n, k, inputs.config_seed(1)).numpy()
+    L = np.array(L0, dtype=np_dt, copy=True)
+    V = np.ascontiguousarray(V, dtype=np_dt)
+    fn = oracle.modify_mixed32 if mixed else oracle.modify_b
     times = []
     t_start = time.perf_counter()
     while True:
         t0 = time.perf_counter()
-        st1, _ = oracle.modify_b(L, V, 1)
-        st2, _ = oracle.modify_b(L, V, -1)
+        st1, _ = fn(L, V, 1)
+        st2, _ = fn(L, V, -1)
         times.append(time.perf_counter() - t0)
         assert st1 == 0 and st2 == 0
         if max_steps is not None and len(times) >= max_steps:
@@ -509,24 +539,26 @@ def cpu_baseline(n, k, budget_s=12.0, max_steps=None):
         if max_steps is None and time.perf_counter() - t_start >= budget_s:
             break
     per_step = sum(times) / len(times)
-    value = 2 * alg_bytes(n, k) / per_step / 1e9
+    value = 2 * alg_bytes(n, k, 4 if mixed else 8) / per_step / 1e9
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d whole step(s) (rank-%d update + downdate, n=%d, float64), serial C "
-                      "oracle CholeskyModifyB, %.2f s/step" % (len(times), k, n, per_step)}, per_step
+            "sample": "%d whole step(s) (rank-%d update + downdate, n=%d, %s), serial C oracle "
+                      "CholeskyModifyB%s, %.2f s/step"
+                      % (len(times), k, n, "float32 storage" if mixed else "float64",
+                         " (float32-storage emulation)" if mixed else "", per_step)}, per_step
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     # warm-up steps, then timed steps of the oracle
-    cb, _ = cpu_baseline(N, K, max_steps=args.warmup)
-    cb, per_step = cpu_baseline(N, K, max_steps=args.steps)
+    cb, _ = cpu_baseline(args.n, args.k, max_steps=args.warmup, dtype=args.dtype)
+    cb, per_step = cpu_baseline(args.n, args.k, max_steps=args.steps, dtype=args.dtype)
     value = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD % (K, N), "n": N, "k": K, "ld": N,
+            "config": {"workload": workload_name(args.n, args.k, args.dtype), "n": args.n, "k": args.k, "ld": args.n,
                        "l2": "n/a (host)", "parallelism": "single"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -553,10 +585,13 @@ def main():
     dev = torch.device("cuda", local)
     chm.load(build_if_missing=True)
 
-    n, k = N, K
+    n, k = args.n, args.k
+    mixed = args.dtype == "f32"
+    tdt = torch.float32 if mixed else torch.float64
+    elt = 4 if mixed else 8
     seed = inputs.config_seed(1)
-    L0 = inputs.spd_factor(n, seed, device=dev)
-    V = inputs.update_block(n, k, seed, device=dev)
+    L0 = inputs.spd_factor(n, seed, device=dev).to(tdt)
+    V = inputs.update_block(n, k, seed, device=dev).to(tdt)
     L = L0.clone()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -607,7 +642,7 @@ def main():
 
     ms = sum(a.elapsed_time(b) for a, b in step_ev) / len(step_ev)
     launch_ms = sum(a.elapsed_time(b) for a, b in launch_ev) / len(launch_ev)
-    bytes_step = 2 * alg_bytes(n, k)
+    bytes_step = 2 * alg_bytes(n, k, elt)
     value, ms_max = aggregate(ms, bytes_step, world, dev)
 
     # End to end through the public API with host buffers: pinned host L and
@@ -648,20 +683,27 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Lh_out.numel() * Lh_out.element_size(),
                "ms_per_step": e2e_max}
 
-    kernel = "wave_kernel<double>"
-    achieved = alg_flops(n, k) / (launch_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64)",
-                "launch_ms": launch_ms,
-                "hbm_gbs": alg_bytes(n, k) / (launch_ms / 1e3) / 1e9,
-                "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash())),
-                "kernel_source_hash": kernel_source_hash()}
+    kernel = "wave_kernel<float>" if mixed else "wave_kernel<double>"
+    hbm_gbs = alg_bytes(n, k, elt) / (launch_ms / 1e3) / 1e9
+    if mixed:
+        # float Apply on the FP32 pipes: the bytes of the factor bound it
+        peak, src = measured_hbm_gbs()
+        roofline = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
+                    "frac": hbm_gbs / peak, "peak_source": src}
+    else:
+        achieved = alg_flops(n, k) / (launch_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64)",
+                    "hbm_gbs": hbm_gbs}
+    roofline.update({"launch_ms": launch_ms,
+                     "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash(), n, k)),
+                     "kernel_source_hash": kernel_source_hash()})
 
     batch = batch_mixed = serve = solve = host = None
-    if rank == 0 and not args.no_solve:
+    if rank == 0 and not args.no_solve and not mixed:
         solve = bench_solve(dev, L)
-    if rank == 0 and not args.no_host:
+    if rank == 0 and not args.no_host and not mixed:
         host = bench_host_resident(dev, L0, V)
     if rank == 0 and not args.no_batch:
         batch = bench_batch(dev, autotune=not args.no_autotune)
@@ -674,15 +716,15 @@ def main():
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(n, k)
+        cb, _ = cpu_baseline(n, k, dtype=args.dtype, L0=L0.cpu().numpy(), V=V.cpu().numpy())
 
     if world > 1:
         dist.barrier()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
-                "config": {"workload": WORKLOAD % (k, n), "n": n, "k": k, "ld": n,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": workload_name(n, k, args.dtype), "n": n, "k": k, "ld": n,
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
