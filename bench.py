@@ -31,6 +31,10 @@ per-request launches:
          the plain path's saturation rate; --serve-loads gives others).
 The batch runs in float64 and again in float32 storage with float64 Compute.
 
+Other shapes: --n, --k and --dtype f32 (float32 storage with float64
+Compute) time another single-factor workload; a float32-storage line reports
+an HBM roofline against the measured copy bandwidth.
+
 Arms:
   default          the CUDA library through its C ABI (this repository)
   --impl reference the serial CPU oracle on the host cores, same workload and metric
