@@ -61,11 +61,19 @@ def spd_factor(n: int, seed: int, ld: int | None = None, device="cpu",
     A.diagonal().add_(1.0)
     # torch's lower factor G (A = G G^T) in row-major order has exactly the
     # memory image of the column-major upper factor L = G^T.  Orders up to
-    # 8192 are factored on the host (LAPACK), larger ones on the device.
+    # 8192 are factored on the host (LAPACK), larger ones on the device, or
+    # on the host when the device factorisation is unavailable (torch loads
+    # its device linear-algebra library lazily, and a profiler's process
+    # environment can keep it from loading).
     if n <= 8192:
         G = torch.linalg.cholesky(A.cpu())
     else:
-        G = torch.linalg.cholesky(A)
+        try:
+            G = torch.linalg.cholesky(A)
+        except RuntimeError:
+            if A.device.type == "cpu":
+                raise
+            G = torch.linalg.cholesky(A.cpu())
     del A
     out[:, :n].copy_(G)
     return out
