@@ -150,7 +150,9 @@ int chm_modify_ex(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, in
  * contents: calls whose work overlaps on the GPU (different streams, or
  * different host threads without ordering) race and give wrong results.
  * Device-side errors (CHM_ERR_NOT_PD, CHM_ERR_TIMEOUT) are reported only
- * through d_info; chm_status_sync does not see this variant's status.
+ * through d_info; chm_status_sync does not see this variant's status, so
+ * d_info is required here whenever n > 0 and k > 0 (NULL returns
+ * CHM_ERR_ARG).
  * Returns CHM_OK or CHM_ERR_ARG / CHM_ERR_BUDGET / CHM_ERR_CUDA.
  */
 int chm_modify_noalloc(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k,
@@ -243,10 +245,14 @@ int chm_batch_plan_destroy(void *plan);
  *   ...).  Synchronous.  CHM_ERR_BUDGET if it does not fit the budget.
  * chm_server_submit: queues L_fid <- modification by V (n x k column-major,
  *   leading dimension n, HOST or DEVICE memory, 1 <= k <= 64) with sign
- *   sigma = +1 or -1.  V is copied (the caller may reuse it on return) and
- *   the call does not wait for the GPU.  req_id receives the request id
- *   (1, 2, ...).  CHM_ERR_BUDGET if the block does not fit the budget or a
- *   launch slot's scratch.
+ *   sigma = +1 or -1.  V must hold its final values when the call is made:
+ *   the server copies it on a stream of its own, which is not ordered after
+ *   the caller's streams, so a V written by GPU work must have that work
+ *   synchronised first.  The call returns once the copy has read V (the
+ *   caller may then reuse or free it); it does not wait for the modification
+ *   or for other GPU work.  req_id receives the request id (1, 2, ...).
+ *   CHM_ERR_BUDGET if the block does not fit the budget or a launch slot's
+ *   scratch.
  * chm_server_poll: moves up to `max` completed requests into req_ids[],
  *   status[] (CHM_OK, CHM_ERR_NOT_PD, CHM_ERR_TIMEOUT, or CHM_ERR_STATE for a
  *   request on a factor invalidated by an earlier failure) and latency_s[]
@@ -356,6 +362,21 @@ typedef enum {
     CHM_MB_FP64_LANES = 6
 } chm_microbench_kind;
 int chm_microbench(int which, double *out, int nout);
+
+/*
+ * Self-test of the reciprocal and reciprocal square root the kernels use in
+ * double precision (a hardware approximation refined by one third-order
+ * Newton-Raphson step, with IEEE division and square root outside
+ * [2^-1020, 2^1020] so that no input or result is flushed to zero).  For
+ * each x[i] it evaluates, on the current device,
+ *   out[4i] = the library's 1/x,  out[4i+1] = the library's 1/sqrt(x),
+ *   out[4i+2] = CUDA's 1.0/x,     out[4i+3] = CUDA's 1.0/sqrt(x)
+ * (the last two correctly rounded).  x and out are HOST arrays of count and
+ * 4 count doubles.  Allocates and frees its own device buffers,
+ * synchronises.  Diagnostics; returns CHM_OK, CHM_ERR_ARG, CHM_ERR_NOMEM or
+ * CHM_ERR_CUDA.
+ */
+int chm_selftest_reciprocals(const double *x, int64_t count, double *out);
 
 /*
  * Diagnostics.  When the environment variable CHM_TRACE is set to 1 before

@@ -79,6 +79,7 @@ def load(build_if_missing: bool = False):
         "chm_server_stats": ([vp, vp], i32),
         "chm_server_destroy": ([vp], i32),
         "chm_microbench": ([i32, vp, i32], i32),
+        "chm_selftest_reciprocals": ([vp, i64, vp], i32),
         "chm_workspace_bytes": ([i64, i64, i32, vp], i32),
         "chm_solve": ([vp, i64, i64, vp, i64, i64, i32, vp], i32),
     }
@@ -190,6 +191,10 @@ def chm_server_destroy(srv):
 
 def chm_microbench(which, out, nout):
     return load().chm_microbench(which, out, nout)
+
+
+def chm_selftest_reciprocals(x, count, out):
+    return load().chm_selftest_reciprocals(x, count, out)
 
 
 def chm_solve(L, n, ld, B, ldb, nrhs, dtype, stream):
@@ -370,7 +375,12 @@ class Server:
         return fid.value
 
     def submit(self, fid, V: torch.Tensor, sigma=1) -> int:
-        """V: contiguous (k, n) tensor (host or device).  Returns the request id or raises."""
+        """V: contiguous (k, n) tensor (host or device).  Returns the request id or raises.
+
+        The server copies V on its own stream before returning, so a device V
+        is first made complete on the current stream (the one that wrote it)."""
+        if V.is_cuda:
+            torch.cuda.current_stream(V.device).synchronize()
         rid = ctypes.c_int64()
         st = chm_server_submit(self.handle, int(fid), V.data_ptr(), V.shape[0], int(sigma), ctypes.byref(rid))
         if st != CHM_OK:

@@ -142,6 +142,37 @@ __device__ __forceinline__ bool wait_ge(const SyncArgs &s, const long long *p, l
 }
 
 
+// Reciprocal and reciprocal square root of a double to within 1 ulp (checked
+// against IEEE division and square root over the whole exponent range by
+// chm_selftest_reciprocals): the hardware's coarse approximations refined by
+// one third-order Newton-Raphson (Householder) step,
+//   1/x:       e = 1 - x y,    y' = y (1 + e + e^2),
+//   1/sqrt(x): e = 1 - x y^2,  y' = y (1 + e/2 + 3 e^2 / 8).
+// The PTX seeds exist only in a flush-to-zero form, which treats a subnormal
+// input as zero (and would flush a subnormal result): outside
+// [2^-1020, 2^1020] the IEEE quotient and square root are taken instead, so
+// no input is flushed.  That branch is never taken by normal data.
+__device__ __forceinline__ double rcp_refined(double x)
+{
+    const double ax = fabs(x);
+    if (!(ax >= 0x1p-1020 && ax <= 0x1p1020)) return 1.0 / x;
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    const double t = fma(e, e, e);
+    return fma(y, t, y);
+}
+__device__ __forceinline__ double rsqrt_refined(double x)
+{
+    if (!(x >= 0x1p-1020 && x <= 0x1p1020)) return 1.0 / sqrt(x);
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double xy = x * y;
+    const double e = fma(-xy, y, 1.0);
+    const double h = fma(0.375, e, 0.5);
+    return fma(y * e, h, y);
+}
+
 // A double published as two tagged words, (epoch << 32) | high half and
 // (epoch << 32) | low half: each 8-byte store is single-copy atomic, so a
 // reader that sees both tags equal to the current epoch has the value, and

@@ -49,7 +49,6 @@ struct PairRec {
     size_t tend;   // [nb]     T after the block's last row
     size_t rdiag;  // [nb][kW][kW] -S_rc e_r / D_r, r < c (diagonal block), for this wave
     size_t rtile;  // [nb][kW][kW] -S_rc e_r (rows of block b, cols of b+1), for this wave
-    size_t carry;  // [2 + kW] the wave's chain state after its window: T, 1/T, p of the last block
     size_t bytes;
 };
 CHM_HD inline PairRec pair_rec(int nb)
@@ -62,7 +61,6 @@ CHM_HD inline PairRec pair_rec(int nb)
     r.tend = x;  x = align256(x + (size_t)nb * sizeof(double));
     r.rdiag = x; x += rows * kW * sizeof(double);
     r.rtile = x; x += rows * kW * sizeof(double);
-    r.carry = x; x += (2 + kW) * sizeof(double);
     r.bytes = align256(x);
     return r;
 }
@@ -96,11 +94,6 @@ struct Prob {
     int k;                         // waves of this problem in the launch (<= kMaxWaves)
     int nb;                        // column blocks of kW columns
     int pair0;                     // index of its first pair (k waves, then the final pass)
-    int blk0, blk1;                // the launch's window of column blocks [blk0, blk1): the
-                                   // blocks before it were modified by earlier launches over
-                                   // the same scratch (whose panels, row data and chain
-                                   // state it reads); 0 and nb for a whole factor
-    int pad_;
     unsigned long long down_mask;  // bit q set: wave q is a downdate
     char *data;                    // prob_data_bytes(nb, k), 256-byte aligned
     int *iflags;                   // prob_iflags(nb, k) ints

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "chm.h"
+#include "chm_device.cuh"
 
 namespace chm {
 namespace {
@@ -175,8 +176,44 @@ float time_ms(cudaEvent_t a, cudaEvent_t b)
     return ms;
 }
 
+// The library's reciprocal and reciprocal square root (chm_device.cuh) of
+// each x, beside CUDA's IEEE-rounded 1 / x and 1 / sqrt(x).
+__global__ void reciprocals(const double *x, long long count, double *out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        out[4 * i] = rcp_refined(v);
+        out[4 * i + 1] = rsqrt_refined(v);
+        out[4 * i + 2] = 1.0 / v;
+        out[4 * i + 3] = 1.0 / sqrt(v);
+    }
+}
+
 }  // namespace
 }  // namespace chm
+
+extern "C" int chm_selftest_reciprocals(const double *x, int64_t count, double *out)
+{
+    using namespace chm;
+    if (count < 0 || (count > 0 && (!x || !out))) return CHM_ERR_ARG;
+    if (count == 0) return CHM_OK;
+    double *dx = nullptr, *dout = nullptr;
+    int rc = CHM_OK;
+    if (cudaMalloc(&dx, (size_t)count * 8) != cudaSuccess || cudaMalloc(&dout, (size_t)count * 32) != cudaSuccess)
+        rc = CHM_ERR_NOMEM;
+    if (rc == CHM_OK && cudaMemcpy(dx, x, (size_t)count * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = CHM_ERR_CUDA;
+    if (rc == CHM_OK) {
+        const int grid = (int)std::min<long long>(1024, (count + 255) / 256);
+        reciprocals<<<grid, 256>>>(dx, (long long)count, dout);
+        if (cudaGetLastError() != cudaSuccess) rc = CHM_ERR_CUDA;
+    }
+    if (rc == CHM_OK && cudaMemcpy(out, dout, (size_t)count * 32, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = CHM_ERR_CUDA;
+    cudaFree(dx);
+    cudaFree(dout);
+    return rc;
+}
 
 extern "C" int chm_microbench(int which, double *out, int nout)
 {

@@ -46,8 +46,6 @@ std::vector<int> carve(const ProbShape *shapes, int count, const Scratch &sc, Pr
         p.nb = nb;
         p.k = k;
         p.pair0 = pair;
-        p.blk0 = 0;
-        p.blk1 = nb;
         p.iflags = sc.iflags + fi;
         p.progress = sc.progress + fp;
         p.data = sc.data + fd;
@@ -509,6 +507,9 @@ static int modify_noalloc(void *L, long long n, long long ld, const void *V, lon
 {
     int rc = check_args(L, n, ld, V, ldv, k, sigma, sign, dtype);
     if (rc != CHM_OK) return rc;
+    // this variant's status word lives in the shared array, which
+    // chm_status_sync does not read: without d_info an error would be lost
+    if (n > 0 && k > 0 && !d_info) return CHM_ERR_ARG;
     if (n > kNoAllocMaxN) return CHM_ERR_BUDGET;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
     if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;

@@ -425,6 +425,10 @@ int submit(Server *s, long long fid, const void *V, long long k, int sigma, long
     if (rc == CHM_OK && (cudaEventCreateWithFlags(&r->v_ready, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventRecord(r->v_ready, s->copy_stream) != cudaSuccess))
         rc = CHM_ERR_CUDA;
+    // the caller may reuse or free V once this returns, so the copy must have
+    // read it: wait for it (it runs on the server's own copy stream, behind no
+    // other work, so this is the copy's own time)
+    if (rc == CHM_OK && cudaEventSynchronize(r->v_ready) != cudaSuccess) rc = CHM_ERR_CUDA;
     std::lock_guard<std::mutex> lock(s->mu);
     if (rc != CHM_OK) {
         if (r->V) cudaFreeAsync(r->V, s->copy_stream);

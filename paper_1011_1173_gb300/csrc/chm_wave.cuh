@@ -74,7 +74,6 @@ struct Wave {
     const T *V;                 // column q of the problem's V
     long long n, ld;
     int nb, q, pair;
-    int blk0, blk1;             // the launch's window of column blocks
     bool has_next;
     bool unscale;               // the problem's final pass: rows times the last wave's scale
     double sg;                  // +1 update, -1 downdate
@@ -84,7 +83,6 @@ struct Wave {
     ChainRow *chain0;           // [nb][kW] original factor's row data (wave 0 writes)
     double *tend, *rdiag, *rtile;
     double *rdiag_next, *rtile_next;  // the next wave's (null without one)
-    double *carry;              // chain state at the window's end: T, 1/T, p of the last block
     int *pflag, *dflag, *rflag0;
     const int *dflag_prev;
     long long *progress;
@@ -112,8 +110,6 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.nb = nb;
     w.q = q;
     w.pair = j;
-    w.blk0 = pr.blk0;
-    w.blk1 = pr.blk1;
     w.has_next = q + 1 < pr.k;
     w.unscale = q == pr.k;  // the pair after the last wave; it owns no scratch of its own
     w.sg = ((pr.down_mask >> q) & 1ull) ? -1.0 : 1.0;
@@ -124,7 +120,6 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.tend = reinterpret_cast<double *>(d + rc.tend);
     w.rdiag = reinterpret_cast<double *>(d + rc.rdiag);
     w.rtile = reinterpret_cast<double *>(d + rc.rtile);
-    w.carry = reinterpret_cast<double *>(d + rc.carry);
     w.rdiag_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rdiag) : nullptr;
     w.rtile_next = w.has_next ? reinterpret_cast<double *>(d + rc.bytes + rc.rtile) : nullptr;
     int *f = pr.iflags + (size_t)q * 2 * nb;
@@ -223,28 +218,6 @@ __device__ __forceinline__ void st_chain(ChainRow *p, const ChainRow &c)
     double2 *q = reinterpret_cast<double2 *>(p);
     __stcg(q, make_double2(c.e1, c.ie1));
     __stcg(q + 1, make_double2(c.d1, c.id1));
-}
-
-// Reciprocal and reciprocal square root to ~1 ulp: the hardware's coarse
-// approximations refined by one third-order Newton-Raphson (Householder)
-// step, e = 1 - x y: y' = y (1 + e + e^2) for 1/x; e = 1 - x y^2:
-// y' = y (1 + e/2 + 3 e^2 / 8) for 1/sqrt(x).
-__device__ __forceinline__ double rcp_refined(double x)
-{
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double e = fma(-x, y, 1.0);
-    const double t = fma(e, e, e);
-    return fma(y, t, y);
-}
-__device__ __forceinline__ double rsqrt_refined(double x)
-{
-    double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double xy = x * y;
-    const double e = fma(-xy, y, 1.0);
-    const double h = fma(0.375, e, 0.5);
-    return fma(y * e, h, y);
 }
 
 // Shared-memory sequence counters between the warps of a wave block.  The
@@ -399,8 +372,7 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
 #pragma unroll
             for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         }
-        // panels before the window were published by an earlier launch
-        if (p >= w.blk0) CHM_WARP_WAIT(wait_eq(sy, w.pflag + p, epoch, who));
+        CHM_WARP_WAIT(wait_eq(sy, w.pflag + p, epoch, who));
         if (lastTile) CHM_TRACE(1);
         cf[lane] = ld_coef(w.coef + (size_t)p * kW + lane);
         if (lastTile && w.has_next) ch[lane] = ld_chain(w.chain + (size_t)p * kW + lane);
@@ -523,7 +495,7 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
     const long long n = w.n, ld = w.ld;
     const int epoch = sy.epoch;
     const long long who = -1;
-    for (int b = w.blk0 + warp; b < w.blk1; b += 4) {
+    for (int b = warp; b < w.nb; b += 4) {
         const long long c0 = (long long)b * kW;
         const int ncols = (int)min((long long)kW, n - c0);
         CHM_WARP_WAIT(wait_eq(sy, w.dflag_prev + b, epoch, who));
@@ -537,7 +509,7 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
     }
     // the pair is done only when its column tasks are: idle sweep warps stop
     // once every pair is done, so none of those tasks may still be unclaimed
-    const int ntasks = w.blk1 - max(w.blk0, 1);
+    const int ntasks = w.nb - 1;
     if (warp == 0 && ntasks > 0) {
         const long long want = ((long long)epoch << 32) + ntasks;
         CHM_WARP_WAIT(wait_ge(sy, w.final_done, want, who));
@@ -570,8 +542,8 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
     const int epoch = sy.epoch;
     const long long ep64 = (long long)epoch << 32;
     volatile int *cdone = &S.cdone;
-    int next_fetch = w.blk0, next_fin = w.blk0;
-    const int nb_end = w.blk1;
+    int next_fetch = 0, next_fin = 0;
+    const int nb_end = nb;
     long long idle_since = -1;
     unsigned idle_iters = 0;
     while (next_fin < nb_end) {
@@ -660,7 +632,7 @@ __device__ void wave_chain(const Wave<T> &w, WaveSmem<T> &S)
     const unsigned FULL = 0xffffffffu;
     const SyncArgs &sy = w.sync;
     const long long who = -1;
-    for (int b = w.blk0; b < w.blk1; ++b) {
+    for (int b = 0; b < w.nb; ++b) {
         CHM_SEQ_WAIT(&S.zseq, b + 1);
         CHM_WTRACE(b, 8);
         double(*R)[kW] = S.R[b % kSlots];
@@ -692,14 +664,9 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
     const long long who = -1;
     double pprev = 0.0;  // p of the block last chained, row `lane`
     double Tend = 1.0, iTend = 1.0;
-    if (w.blk0 > 0) {    // the chain state where the previous window ended
-        Tend = __ldcg(w.carry);
-        iTend = __ldcg(w.carry + 1);
-        pprev = __ldcg(w.carry + 2 + lane);
-    }
     int pending = -1;    // block chained (or being chained) but not yet published
-    int next = w.blk0;   // next block whose chain input is to be formed
-    const int nb_end = w.blk1;
+    int next = 0;        // next block whose chain input is to be formed
+    const int nb_end = nb;
     bool ok = true;
     auto wait_seq = [&](int *seq, int want) -> bool {
         int v = seq_wait(sy, seq, want, &S.bail, who) ? 1 : 0;  // all lanes: see CHM_WARP_WAIT
@@ -796,14 +763,6 @@ __device__ void wave_coef(const Wave<T> &w, WaveSmem<T> &S)
         }
         publish(done, pprev);
     }
-    // the chain state for this wave's next window
-    if (w.blk1 < nb) {
-        if (lane == 0) {
-            __stcg(w.carry, Tend);
-            __stcg(w.carry + 1, iTend);
-        }
-        __stcg(w.carry + 2 + lane, pprev);
-    }
 }
 
 // Warp C: the wave's rotations inside each diagonal block and the next
@@ -886,25 +845,17 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
 constexpr int kRoleIdle = 0, kRoleWave = 1, kRoleSweep = 2;
 __device__ __forceinline__ int role_code(int role, int group) { return role | (group << 4); }
 
-// Column blocks of pair j that carry sweep tasks: [first, nb) within the
-// launch's window; returns the pair's ticket word.
+// Column blocks of pair j that carry sweep tasks: [first, nb); returns the
+// pair's ticket word.
 template <typename T>
 __device__ __forceinline__ unsigned long long *task_range(const Launch<T> &P, int j, int *first, int *nb)
 {
     const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
     const Prob *pr = P.probs ? P.probs + i : &P.prob0;
-    *first = max(j > pr->pair0 ? 1 : 0, pr->blk0);  // block 0 of a later wave has no off-diagonal tile
-    *nb = pr->blk1;
+    *first = j > pr->pair0 ? 1 : 0;  // block 0 of a later wave has no off-diagonal tile
+    *nb = pr->nb;
     return reinterpret_cast<unsigned long long *>(pr->progress + prob_ticket(pr->nb, pr->k, j - pr->pair0));
 }
-// First column block of pair j's window.
-template <typename T>
-__device__ __forceinline__ int window_start(const Launch<T> &P, int j)
-{
-    const int i = P.pair_prob ? __ldg(P.pair_prob + j) : 0;
-    return P.probs ? P.probs[i].blk0 : P.prob0.blk0;
-}
-
 // Take one sweep task: from the own group's current pair first, then, when
 // it has no task left, from another group's pair that is lower than the own
 // group's current pair; a warp whose group has no pair yet takes nothing,
@@ -1032,9 +983,8 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
                     __threadfence();
                     atomicExch(gt, (unsigned long long)kGroupDone << 32);
                 } else {
-                    // sequence counters count blocks; the window starts at s0
-                    const int s0 = window_start(P, j);
-                    S.dseq = S.zseq = S.cseq = S.bseq = S.cdone = S.fseq = s0;
+                    // sequence counters count blocks
+                    S.dseq = S.zseq = S.cseq = S.bseq = S.cdone = S.fseq = 0;
                     S.bail = 0;
                     // the pair's ticket word starts at this launch's tag before the pair is named
                     int f_ = 0, n_ = 0;

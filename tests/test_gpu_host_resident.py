@@ -119,7 +119,9 @@ def test_pageable_host_memory_is_rejected_before_any_work():
     Ld = L.cuda()
     st = chm.chm_update(Ld.data_ptr(), n, n, V.data_ptr(), k, chm.CHM_F64, stream)
     assert st == chm.CHM_ERR_ARG
-    st = chm.chm_modify_noalloc(L.data_ptr(), n, n, Vd.data_ptr(), n, k, None, 1, chm.CHM_F64, stream, None)
+    info = torch.zeros(2, dtype=torch.int64, device="cuda")
+    st = chm.chm_modify_noalloc(L.data_ptr(), n, n, Vd.data_ptr(), n, k, None, 1, chm.CHM_F64, stream,
+                                info.data_ptr())
     assert st == chm.CHM_ERR_ARG
     plan = chm.BatchPlan([n], [n], [k])
     assert plan.execute([L], [Vd]) == chm.CHM_ERR_ARG

@@ -31,16 +31,29 @@ def _call(fn, L, V, sigma, d_info=None):
 
 
 def test_noalloc_rejects_too_large_without_work():
-    # the size check comes before any CUDA call, so this needs no GPU
-    st = chm.chm_modify_noalloc(8, 8193, 8193, 8, 8193, 1, None, 1, chm.CHM_F64, None, None)
+    # the size and argument checks come before any CUDA call, so this needs no GPU
+    info = 16  # an aligned address that is never dereferenced
+    st = chm.chm_modify_noalloc(8, 8193, 8193, 8, 8193, 1, None, 1, chm.CHM_F64, None, info)
     assert st == chm.CHM_ERR_BUDGET
-    st = chm.chm_modify_noalloc(8, 10, 9, 8, 10, 1, None, 1, chm.CHM_F64, None, None)
+    st = chm.chm_modify_noalloc(8, 10, 9, 8, 10, 1, None, 1, chm.CHM_F64, None, info)
     assert st == chm.CHM_ERR_ARG
+
+
+def test_noalloc_requires_status_pointer_without_work():
+    # its status word is in the shared array, which chm_status_sync does not
+    # read: without d_info a failed modification could not be seen
+    st = chm.chm_modify_noalloc(8, 10, 10, 8, 10, 1, None, 1, chm.CHM_F64, None, None)
+    assert st == chm.CHM_ERR_ARG
+    # nothing to do: no status is needed
+    assert chm.chm_modify_noalloc(8, 10, 10, 8, 10, 0, None, 1, chm.CHM_F64, None, None) == chm.CHM_OK
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("n,k,dtype", [(1500, 16, torch.float64), (4100, 40, torch.float64),
-                                       (700, 9, torch.float32)])
+                                       (700, 9, torch.float32),
+                                       # the documented limit: the array holds few vectors per
+                                       # launch at this order, so k is split over many launches
+                                       (8192, 64, torch.float64)])
 def test_noalloc_matches_allocating_path_twice(n, k, dtype):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
