@@ -364,6 +364,41 @@ typedef enum {
 int chm_microbench(int which, double *out, int nout);
 
 /*
+ * Library-wide settings of the single-factor entry points (chm_update,
+ * chm_downdate, chm_modify_ex), for tuning and tests; they take effect on
+ * the next call and may be changed at any time from one thread.
+ *   "path"     0 automatic (default), 1 the wave kernel, 2 the pass kernels
+ *   "pass_kb"  update vectors per pass of the pass kernels, 1..16 (0: 16)
+ *   "pass_d"   lookahead of the pass kernels' forward-substitution chain in
+ *              row blocks, clamped to 2..12 (float) or 2..4 (double); 0 is
+ *              the default per type (8 float, 3 double)
+ * The two paths compute the same factor by the same method (Algorithm 1's
+ * rotations, restated exactly) with different work splits:
+ *   wave  one persistent launch per 64 vectors; each vector is a wave that
+ *         sweeps the factor, its forward-substitution chain driven by the
+ *         sweep's carries.  Fastest while the factor stays in L2.
+ *   pass  per block of up to 16 vectors (Sec. 4.1's blocking): a forward
+ *         substitution P = L^{-T} V run by one chain block with lookahead,
+ *         every rotation's coefficients from prefix Grams of P (the Compute,
+ *         in double), and one sweep that reads and writes each tile of the
+ *         factor once for the whole block of vectors.
+ * The automatic rule takes the pass kernels when the factor's upper
+ * triangle is at least 32 MB (float) or 256 MB with k <= 2 (double).
+ * chm_config_get also answers "pass_d_f32" and "pass_d_f64" (the values in
+ * effect).  Host only.  Returns CHM_OK or CHM_ERR_ARG (unknown key or value
+ * out of range).
+ */
+int chm_config_set(const char *key, int64_t value);
+int chm_config_get(const char *key, int64_t *value);
+
+/*
+ * The path (1 wave kernel, 2 pass kernels) a single-factor modification of
+ * order n by k vectors takes under the current settings.  Host only.
+ * Returns CHM_OK or CHM_ERR_ARG.
+ */
+int chm_path_for(int64_t n, int64_t k, int dtype, int *path);
+
+/*
  * Self-test of the reciprocal and reciprocal square root the kernels use in
  * double precision (a hardware approximation refined by one third-order
  * Newton-Raphson step, with IEEE division and square root outside

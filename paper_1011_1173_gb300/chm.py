@@ -80,6 +80,9 @@ def load(build_if_missing: bool = False):
         "chm_server_destroy": ([vp], i32),
         "chm_microbench": ([i32, vp, i32], i32),
         "chm_selftest_reciprocals": ([vp, i64, vp], i32),
+        "chm_config_set": ([ctypes.c_char_p, i64], i32),
+        "chm_config_get": ([ctypes.c_char_p, vp], i32),
+        "chm_path_for": ([i64, i64, i32, vp], i32),
         "chm_workspace_bytes": ([i64, i64, i32, vp], i32),
         "chm_solve": ([vp, i64, i64, vp, i64, i64, i32, vp], i32),
     }
@@ -191,6 +194,37 @@ def chm_server_destroy(srv):
 
 def chm_microbench(which, out, nout):
     return load().chm_microbench(which, out, nout)
+
+
+def chm_config_set(key, value):
+    return load().chm_config_set(key.encode() if isinstance(key, str) else key, int(value))
+
+
+def chm_config_get(key, value):
+    return load().chm_config_get(key.encode() if isinstance(key, str) else key, value)
+
+
+def chm_path_for(n, k, dtype, path):
+    return load().chm_path_for(n, k, dtype, path)
+
+
+PATH_AUTO, PATH_WAVE, PATH_PASS = 0, 1, 2
+
+
+def config_set(key, value):
+    check(chm_config_set(key, value), "chm_config_set(%s)" % key)
+
+
+def config_get(key) -> int:
+    v = ctypes.c_int64()
+    check(chm_config_get(key, ctypes.byref(v)), "chm_config_get(%s)" % key)
+    return int(v.value)
+
+
+def path_for(n, k, dtype=CHM_F64) -> int:
+    p = ctypes.c_int()
+    check(chm_path_for(int(n), int(k), int(dtype), ctypes.byref(p)), "chm_path_for")
+    return int(p.value)
 
 
 def chm_selftest_reciprocals(x, count, out):

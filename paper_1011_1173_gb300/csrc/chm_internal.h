@@ -88,4 +88,29 @@ size_t single_workspace_bytes(long long n, long long k);
 int with_stream_scratch(cudaStream_t stream, const ScratchNeed &need, const std::function<int(const Scratch &)> &fn);
 void scratch_free(Scratch *sc);
 
+// ---------------------------------------------------------------- pass path
+
+// Workspace of the pass kernels (chm_pass.cuh) of one (device, stream): one
+// buffer, carved per pass, whose flag words are zeroed when it is allocated,
+// and the epoch that tags each pass's flags (earlier passes' flags hold
+// smaller epochs, so no flag needs clearing between passes).
+struct PassSpace {
+    char *buf = nullptr;
+    size_t bytes = 0;
+    int epoch = 0;
+};
+size_t pass_workspace_bytes(long long n, int dtype);
+size_t pass_flag_bytes(long long n, int dtype);
+// True if a single-factor modification of this shape runs on the pass
+// kernels (the library setting "path", else the size rule).
+bool use_pass_path(long long n, long long k, int dtype);
+// Runs fn on the stream's status word and pass workspace, grown first to
+// at least `bytes`, under the workspaces' lock.
+int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtype,
+                        const std::function<int(const Scratch &, PassSpace &)> &fn);
+// Enqueue the passes of one modification (kb <= 16 vectors each).
+int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
+                 const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
+                 const Scratch &sc, PassSpace &ps);
+
 }  // namespace chm

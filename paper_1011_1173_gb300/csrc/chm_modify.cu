@@ -286,6 +286,7 @@ struct Workspace {
     int device = -1;
     cudaStream_t stream = nullptr;
     Scratch sc;
+    PassSpace ps;
 };
 
 static std::mutex g_mu;
@@ -412,12 +413,45 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
     if (rc != CHM_OK) return rc;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
     if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;
+    if (use_pass_path(n, k, dtype)) {
+        return with_pass_workspace(stream, pass_workspace_bytes(n, dtype), n, dtype,
+                                   [&](const Scratch &sc, PassSpace &ps) {
+                                       return pass_enqueue(L, n, ld, V, ldv, k, sigma, sign, dtype, stream,
+                                                           d_info, sc, ps);
+                                   });
+    }
     const int kw_max = (int)std::min<long long>(k, kMaxWaves);
     const ProbShape sh{n, kw_max};
     const ScratchNeed need = scratch_need(&sh, 1);
     return with_stream_scratch(stream, need, [&](const Scratch &sc) {
         return enqueue_single(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info, sc, kw_max, true);
     });
+}
+
+int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtype,
+                        const std::function<int(const Scratch &, PassSpace &)> &fn)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *w = find_workspace(dev, stream, true);
+    if (!w->sc.ctl) {  // the control words and the stream's status word
+        const int rc = scratch_alloc(&w->sc, 0, 0, 0);
+        if (rc != CHM_OK) return rc;
+    }
+    if (w->ps.bytes < bytes) {
+        // queued work on this stream may still use the old buffer
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return CHM_ERR_CUDA;
+        cudaFree(w->ps.buf);
+        w->ps.buf = nullptr;
+        w->ps.bytes = 0;
+        if (cudaMalloc(&w->ps.buf, bytes) != cudaSuccess) return CHM_ERR_NOMEM;
+        // the flag and control words lead the buffer; zero flags match no epoch
+        if (cudaMemset(w->ps.buf, 0, pass_flag_bytes(n, dtype)) != cudaSuccess) return CHM_ERR_CUDA;
+        w->ps.bytes = bytes;
+        w->ps.epoch = 0;
+    }
+    return fn(w->sc, w->ps);
 }
 
 int with_stream_scratch(cudaStream_t stream, const ScratchNeed &need, const std::function<int(const Scratch &)> &fn)
@@ -561,7 +595,10 @@ int chm_workspace_bytes(int64_t n, int64_t k, int dtype, size_t *bytes)
 {
     if (!bytes || n < 0 || k < 0 || n > (1ll << 26)) return CHM_ERR_ARG;
     if (dtype != CHM_F64 && dtype != CHM_F32_MIXED) return CHM_ERR_ARG;
-    *bytes = chm::single_workspace_bytes(n, k);
+    if (n > 0 && k > 0 && chm::use_pass_path(n, k, dtype))
+        *bytes = chm::kCtlInts * sizeof(int) + 2 * sizeof(long long) + chm::pass_workspace_bytes(n, dtype);
+    else
+        *bytes = chm::single_workspace_bytes(n, k);
     return CHM_OK;
 }
 

@@ -14,21 +14,41 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL_F64 = 1e-11
 
 
-def colscaled_err(got_cm, ref_cm, n=None):
+def colscaled_err(got_cm, ref_cm, n=None, chunk=2048):
     """Max over the upper triangle of |got - ref| / max(|ref_ij|, max_r |ref_rj|).
 
-    Both arrays use the (n, ld) storage of the C ABI: row j is column j of L."""
-    got = np.asarray(got_cm, dtype=np.float64)
-    ref = np.asarray(ref_cm, dtype=np.float64)
-    n = ref.shape[0] if n is None else n
-    g = got[:n, :n]
-    r = ref[:n, :n]
-    mask = np.tril(np.ones((n, n), dtype=bool))  # row j, entries i <= j
-    colmax = np.max(np.where(mask, np.abs(r), 0.0), axis=1, keepdims=True)
-    scale = np.maximum(np.abs(r), colmax)
-    scale = np.where(scale == 0, 1.0, scale)
-    err = np.where(mask, np.abs(g - r) / scale, 0.0)
-    return float(err.max()) if n else 0.0
+    Both arrays use the (n, ld) storage of the C ABI: row j is column j of L.
+    Works through the storage rows in chunks, so that a factor of order 32768
+    needs no full-size temporaries."""
+    n = np.asarray(ref_cm).shape[0] if n is None else n
+    worst = 0.0
+    for j0 in range(0, n, chunk):
+        j1 = min(n, j0 + chunk)
+        g = np.asarray(got_cm[j0:j1, :n], dtype=np.float64)
+        r = np.asarray(ref_cm[j0:j1, :n], dtype=np.float64)
+        mask = np.arange(n)[None, :] <= np.arange(j0, j1)[:, None]  # row j, entries i <= j
+        colmax = np.max(np.where(mask, np.abs(r), 0.0), axis=1, keepdims=True)
+        scale = np.maximum(np.abs(r), colmax)
+        scale = np.where(scale == 0, 1.0, scale)
+        err = np.where(mask, np.abs(g - r) / scale, 0.0)
+        worst = max(worst, float(err.max()))
+    return worst
+
+
+def elementwise_rel_err(got_cm, ref_cm, n=None, floor=1e-300, chunk=2048):
+    """Max over the upper triangle of |got - ref| / max(|ref_ij|, floor): the
+    plain elementwise relative error (entries below `floor` in magnitude are
+    compared absolutely against it)."""
+    n = np.asarray(ref_cm).shape[0] if n is None else n
+    worst = 0.0
+    for j0 in range(0, n, chunk):
+        j1 = min(n, j0 + chunk)
+        g = np.asarray(got_cm[j0:j1, :n], dtype=np.float64)
+        r = np.asarray(ref_cm[j0:j1, :n], dtype=np.float64)
+        mask = np.arange(n)[None, :] <= np.arange(j0, j1)[:, None]
+        err = np.where(mask, np.abs(g - r) / np.maximum(np.abs(r), floor), 0.0)
+        worst = max(worst, float(err.max()))
+    return worst
 
 
 def upper_from_cm(L_cm, n=None):

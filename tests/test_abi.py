@@ -107,17 +107,64 @@ def test_workspace_bytes_grow_as_n_times_k():
     memory needs only this much device memory)."""
     ws = chm.workspace_bytes
     n = 1 << 16
-    assert ws(0, 5) == 0 and ws(n, 0) == 0
-    assert 1.95 <= ws(2 * n, 8) / ws(n, 8) <= 2.05
-    assert 1.9 <= ws(n, 16) / ws(n, 8) <= 2.05
-    assert ws(n, 100) == ws(n, 64)
-    assert ws(n, 16) < 8 * n * n / 40
-    assert ws(n, 16, chm.CHM_F32_MIXED) == ws(n, 16)
-    for bad in ((-1, 1), (1, -1), (1 << 27, 1)):
+    chm.config_set("path", chm.PATH_WAVE)
+    try:
+        assert ws(0, 5) == 0 and ws(n, 0) == 0
+        assert 1.95 <= ws(2 * n, 8) / ws(n, 8) <= 2.05
+        assert 1.9 <= ws(n, 16) / ws(n, 8) <= 2.05
+        assert ws(n, 100) == ws(n, 64)
+        assert ws(n, 16) < 8 * n * n / 40
+        assert ws(n, 16, chm.CHM_F32_MIXED) == ws(n, 16)
+        for bad in ((-1, 1), (1, -1), (1 << 27, 1)):
+            with pytest.raises(chm.ChmError):
+                ws(*bad)
         with pytest.raises(chm.ChmError):
-            ws(*bad)
-    with pytest.raises(chm.ChmError):
-        ws(10, 1, 9)
+            ws(10, 1, 9)
+    finally:
+        chm.config_set("path", chm.PATH_AUTO)
+
+
+def test_pass_workspace_is_linear_in_n_and_independent_of_k():
+    """The pass kernels' workspace is sized for one pass of up to 16
+    vectors: O(n), the same for every k."""
+    ws = chm.workspace_bytes
+    n = 1 << 15
+    chm.config_set("path", chm.PATH_PASS)
+    try:
+        assert ws(n, 1) == ws(n, 16) == ws(n, 100)
+        assert 1.95 <= ws(2 * n, 8) / ws(n, 8) <= 2.05
+        assert ws(n, 16) < 8 * n * n / 40
+        assert ws(n, 4, chm.CHM_F32_MIXED) < ws(n, 4)
+        assert ws(0, 3) == 0
+    finally:
+        chm.config_set("path", chm.PATH_AUTO)
+
+
+def test_path_settings_and_automatic_rule():
+    """Host-only: the settings interface and the size rule that picks the
+    pass kernels (float: upper triangle >= 32 MB; double: >= 256 MB and k <= 2)."""
+    F32, F64 = chm.CHM_F32_MIXED, chm.CHM_F64
+    assert chm.config_get("path") == chm.PATH_AUTO
+    assert chm.path_for(2048, 4, F32) == chm.PATH_WAVE
+    assert chm.path_for(4096, 4, F32) == chm.PATH_PASS
+    assert chm.path_for(32768, 64, F32) == chm.PATH_PASS
+    assert chm.path_for(5000, 16, F64) == chm.PATH_WAVE
+    assert chm.path_for(8192, 1, F64) == chm.PATH_PASS
+    assert chm.path_for(32768, 3, F64) == chm.PATH_WAVE
+    for p in (chm.PATH_WAVE, chm.PATH_PASS):
+        chm.config_set("path", p)
+        assert chm.path_for(100, 1, F64) == p and chm.path_for(40000, 1, F32) == p
+    chm.config_set("path", chm.PATH_AUTO)
+    chm.config_set("pass_kb", 5)
+    assert chm.config_get("pass_kb") == 5
+    chm.config_set("pass_kb", 0)
+    assert chm.config_get("pass_kb") == 16
+    chm.config_set("pass_d", 100 // 10)
+    assert chm.config_get("pass_d_f32") == 10 and chm.config_get("pass_d_f64") == 4
+    chm.config_set("pass_d", 0)
+    assert chm.config_get("pass_d_f32") == 8 and chm.config_get("pass_d_f64") == 3
+    for key, val in (("path", 3), ("pass_kb", 17), ("pass_kb", -1), ("nope", 1)):
+        assert chm.chm_config_set(key, val) == chm.CHM_ERR_ARG
 
 
 def test_solve_argument_errors_without_gpu():

@@ -1,4 +1,5 @@
-"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, on
+both paths of the single-factor entry points (wave kernel, pass kernels).
 
 Float64: elementwise, column-scaled relative error <= 1e-11 (see
 ``tests/common.py``).  Mixed precision (float storage and Apply, double
@@ -23,12 +24,17 @@ pytestmark = pytest.mark.gpu
 TOL_MIXED = 1e-4
 
 
-@pytest.fixture(scope="module", autouse=True)
-def _device():
+@pytest.fixture(scope="module", autouse=True, params=["wave", "pass"])
+def _device(request):
+    """Every test of this file runs once on each path of the single-factor
+    entry points (the wave kernel and the pass kernels)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     chm.load(build_if_missing=True)
     torch.cuda.set_device(0)
+    chm.config_set("path", chm.PATH_WAVE if request.param == "wave" else chm.PATH_PASS)
+    yield request.param
+    chm.config_set("path", chm.PATH_AUTO)
 
 
 def gpu_modify(L_cm, V_cm, sigma, dtype=torch.float64, n=None):
