@@ -97,6 +97,38 @@ def measured_hbm_gbs():
         return 6800.0, "fallback: 6800 GB/s, an earlier GB300 copy measurement"
 
 
+_ALU = {}
+
+
+def measured_fp64_tflops():
+    """FP64 peak in TFLOP/s measured in this run by the library's own FMA-rate
+    microbenchmark (chm_microbench, all SMs, independent FMA chains; 2 flops
+    per FMA), and its source."""
+    if "f64" not in _ALU:
+        from paper_1011_1173_gb300 import chm
+        _ALU["f64"] = 2.0 * chm.microbench("fp64_rate")[0]
+    return _ALU["f64"], "measured in this run: chm_microbench FP64 FMA rate x 2 flop"
+
+
+def measured_fp32_tflops():
+    if "f32" not in _ALU:
+        from paper_1011_1173_gb300 import chm
+        _ALU["f32"] = 2.0 * chm.microbench("fp32_rate")[0]
+    return _ALU["f32"]
+
+
+def launches_per_modification(path, k):
+    """Kernels of this library one modification launches: the wave kernel once
+    per 64 vectors; the pass kernels six per pass of up to 16 vectors (the
+    inverse diagonal blocks, the forward substitution, the block Grams, their
+    prefix, the coefficients, the sweep)."""
+    from paper_1011_1173_gb300 import chm
+    if path == chm.PATH_PASS:
+        kb = chm.config_get("pass_kb")
+        return 6 * ((k + kb - 1) // kb)
+    return (k + 63) // 64
+
+
 def alg_bytes(n, k, elt=8):
     return elt * n * (n + 1) + elt * n * k
 
@@ -131,6 +163,8 @@ def parse():
     ap.add_argument("--serve-loads", default="0.9",
                     help="offered loads as fractions of the plain path's saturation rate, comma separated")
     ap.add_argument("--no-batch-mixed", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the n = 32768 single-factor cases (k = 1, 16; float64 and float32 storage)")
     return ap.parse_args()
 
 
@@ -302,6 +336,74 @@ def bench_solve(dev, L, reps=5):
     del U
     torch.cuda.empty_cache()
     return {"workload": "solve with the bench factor after the timed steps, n=%d float64" % n, "runs": runs}
+
+
+def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n=32768, reps=4):
+    """The large single-factor configuration (n = 32768, an update by U then
+    the cancellation-stressed downdate by 0.9 U, the factor built on the
+    device from its seed) through the same C ABI call as the main line, on
+    the path the library picks; per case the median time of one
+    modification (CUDA events), GB/s, the fraction of measured HBM and of the
+    binding roofline.  L is restored from a device copy before each pair."""
+    import torch
+
+    from paper_1011_1173_gb300 import chm, inputs
+    stream = torch.cuda.current_stream()
+    peak_hbm, hbm_src = measured_hbm_gbs()
+    fp64_tflops, fp64_src = measured_fp64_tflops()
+    fp32_tflops = measured_fp32_tflops()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    seed = inputs.config_seed(2)
+    base = inputs.spd_factor(n, seed, device=dev)  # float64
+    out = []
+    for k, dt in cases:
+        tdt = torch.float32 if dt == "f32" else torch.float64
+        elt = 4 if dt == "f32" else 8
+        L0 = base.to(tdt)
+        U = inputs.update_block(n, k, seed + k, device=dev).to(tdt)
+        U9 = (0.9 * U).contiguous()
+        L = L0.clone()
+        ts = []
+        for r in range(reps + 1):
+            L.copy_(L0)
+            for V, sg in ((U, 1), (U9, -1)):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                chm.check(chm.modify(L, V, sg, stream=stream), "large")
+                b.record(stream)
+                torch.cuda.synchronize()
+                if r > 0:
+                    ts.append(a.elapsed_time(b))
+        st, info = chm.status_sync(stream)
+        chm.check(st, "large status (info %d)" % info)
+        ms = statistics.median(ts)
+        gbs = alg_bytes(n, k, elt) / (ms / 1e3) / 1e9
+        flops = alg_flops(n, k) / (ms / 1e3) / 1e12
+        path = chm.path_for(n, k, chm.CHM_F32_MIXED if dt == "f32" else chm.CHM_F64)
+        # the binding roofline: HBM for float storage (float Apply is far
+        # below the FP32 rate), the FP64 FMA rate for float64 (2 FMAs per
+        # element and vector at the measured rate take longer than the bytes)
+        t_hbm = alg_bytes(n, k, elt) / (peak_hbm * 1e9)
+        alu_peak = fp32_tflops if dt == "f32" else fp64_tflops
+        t_alu = alg_flops(n, k) / (alu_peak * 1e12)
+        bound = "hbm" if t_hbm >= t_alu else "alu"
+        out.append({
+            "n": n, "k": k, "dtype": dt, "path": "pass" if path == chm.PATH_PASS else "wave",
+            "ms_per_modification": ms, "GBps": gbs, "hbm_frac": gbs / peak_hbm,
+            "TFLOPs": flops, "alu_frac": flops / alu_peak,
+            "bound": bound, "binding_frac": max(t_hbm, t_alu) / (ms / 1e3),
+            "launches_per_modification": launches_per_modification(path, k)})
+        del L, L0, U, U9
+        torch.cuda.empty_cache()
+    del base, flush
+    torch.cuda.empty_cache()
+    return {"workload": "n=%d, update by U then downdate by 0.9 U (U ~ N(0, 1/n)), factor of B^T B / n + I "
+                        "built on the device" % n,
+            "hbm_peak_GBps": peak_hbm, "hbm_peak_source": hbm_src,
+            "fp64_peak_TFLOPs": fp64_tflops, "fp64_peak_source": fp64_src,
+            "fp32_peak_TFLOPs": fp32_tflops, "cases": out}
 
 
 def bench_host_resident(dev, L0, V, reps=3):
@@ -687,24 +789,32 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Lh_out.numel() * Lh_out.element_size(),
                "ms_per_step": e2e_max}
 
-    kernel = "wave_kernel<float>" if mixed else "wave_kernel<double>"
+    path = chm.path_for(n, k, chm.CHM_F32_MIXED if mixed else chm.CHM_F64)
+    if path == chm.PATH_PASS:
+        kernel = "pass kernels<%s>" % ("float" if mixed else "double")
+    else:
+        kernel = "wave_kernel<float>" if mixed else "wave_kernel<double>"
     hbm_gbs = alg_bytes(n, k, elt) / (launch_ms / 1e3) / 1e9
+    peak_hbm, hbm_src = measured_hbm_gbs()
     if mixed:
         # float Apply on the FP32 pipes: the bytes of the factor bound it
-        peak, src = measured_hbm_gbs()
-        roofline = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
-                    "frac": hbm_gbs / peak, "peak_source": src}
+        roofline = {"bound": "hbm", "kernel": kernel, "achieved": hbm_gbs, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": hbm_gbs / peak_hbm, "peak_source": hbm_src, "hbm_frac": hbm_gbs / peak_hbm}
     else:
+        fp64_peak, fp64_src = measured_fp64_tflops()
         achieved = alg_flops(n, k) / (launch_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64)",
-                    "hbm_gbs": hbm_gbs}
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "peak_source": fp64_src,
+                    "nominal_fp64_TFLOPs": FP64_PEAK_TFLOPS,
+                    "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peak_hbm, "hbm_peak_source": hbm_src}
     roofline.update({"launch_ms": launch_ms,
                      "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash(), n, k)),
                      "kernel_source_hash": kernel_source_hash()})
 
-    batch = batch_mixed = serve = solve = host = None
+    batch = batch_mixed = serve = solve = host = large = None
+    if rank == 0 and not args.no_large:
+        large = bench_large(dev)
     if rank == 0 and not args.no_solve and not mixed:
         solve = bench_solve(dev, L)
     if rank == 0 and not args.no_host and not mixed:
@@ -732,8 +842,9 @@ def main():
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "large": large,
                 "batched": batch, "batched_mixed": batch_mixed, "served": serve, "solve": solve, "host_resident": host,
-                "gpu_launches": 2 * args.steps * ((k + 63) // 64),
+                "gpu_launches": 2 * args.steps * launches_per_modification(path, k),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

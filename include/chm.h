@@ -370,8 +370,10 @@ int chm_microbench(int which, double *out, int nout);
  *   "path"     0 automatic (default), 1 the wave kernel, 2 the pass kernels
  *   "pass_kb"  update vectors per pass of the pass kernels, 1..16 (0: 16)
  *   "pass_d"   lookahead of the pass kernels' forward-substitution chain in
- *              row blocks, clamped to 2..12 (float) or 2..4 (double); 0 is
- *              the default per type (8 float, 3 double)
+ *              row blocks, clamped to 2..12 (float) or 2..5 (double) and
+ *              further by what the chain block's shared memory holds for
+ *              the pass's vectors; 0 is the default per type (6 float,
+ *              4 double)
  * The two paths compute the same factor by the same method (Algorithm 1's
  * rotations, restated exactly) with different work splits:
  *   wave  one persistent launch per 64 vectors; each vector is a wave that

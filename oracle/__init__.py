@@ -60,10 +60,10 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(build())
         i64, vp = ctypes.c_int64, ctypes.c_void_p
-        for name in ("orc_modify_b", "orc_modify_mixed32"):
-            f = getattr(lib, name)
-            f.argtypes = [vp, i64, i64, vp, i64, i64, vp, i64, ctypes.POINTER(i64)]
-            f.restype = ctypes.c_int
+        lib.orc_modify_b.argtypes = [vp, i64, i64, vp, i64, i64, vp, i64, ctypes.POINTER(i64)]
+        lib.orc_modify_b.restype = ctypes.c_int
+        lib.orc_modify_mixed32.argtypes = [vp, i64, i64, vp, i64, i64, vp, i64, i64, ctypes.POINTER(i64)]
+        lib.orc_modify_mixed32.restype = ctypes.c_int
         lib.orc_modify_a.argtypes = [vp, i64, i64, vp, i64, i64, vp, ctypes.POINTER(i64)]
         lib.orc_modify_a.restype = ctypes.c_int
         lib.orc_solve.argtypes = [vp, i64, i64, vp, i64, i64, ctypes.POINTER(i64)]
@@ -124,8 +124,12 @@ def modify_a(L_cm, V_cm, sigma, n=None):
     return st, info.value
 
 
-def modify_mixed32(L_cm, V_cm, sigma, n=None, m_rows=None):
-    """Mixed precision: float32 storage and Apply, float64 Compute."""
+def modify_mixed32(L_cm, V_cm, sigma, n=None, m_rows=None, group=None):
+    """Mixed precision: float32 storage and Apply, float64 Compute.
+
+    ``group`` is the number of consecutive vectors whose new diagonals are
+    carried in double before being rounded to float (one launch or pass of
+    the GPU path); None means all k vectors in one group."""
     L_cm, V_cm = _prep(L_cm, V_cm, np.float32)
     n = L_cm.shape[0] if n is None else n
     k = V_cm.shape[0]
@@ -133,7 +137,8 @@ def modify_mixed32(L_cm, V_cm, sigma, n=None, m_rows=None):
     info = ctypes.c_int64(-1)
     st = _load().orc_modify_mixed32(L_cm.ctypes.data, n, L_cm.shape[1], V_cm.ctypes.data,
                                     V_cm.shape[1], k, sig.ctypes.data,
-                                    -1 if m_rows is None else m_rows, ctypes.byref(info))
+                                    -1 if m_rows is None else m_rows,
+                                    0 if group is None else int(group), ctypes.byref(info))
     return st, info.value
 
 

@@ -158,48 +158,73 @@ int orc_modify_a(double *L, int64_t n, int64_t ld, const double *V, int64_t ldv,
 
 /*
  * Mixed precision (FP32 storage and Apply, FP64 Compute): L and V are float.
- * For row i and column p, Compute runs in double on the promoted float
- * values of L_ii and V_i^p; the new diagonal is stored rounded to float; c
- * and s are rounded to float; Apply is Algorithm 1's Apply evaluated in
- * float arithmetic, one rounding per operation, in the order printed.
- * Order of rows and columns as orc_modify_b.
+ * The k columns of V are taken in groups of `kgroup` consecutive columns
+ * (kgroup <= 0: one group), the vectors one launch or one pass of the GPU
+ * path handles.  Each group is CholeskyModifyB restricted to its columns:
+ * for each row i, for each column p of the group in order,
+ *   Compute in double: L_ii is promoted from float when the group reaches
+ *     row i and carried in double across the group's columns; V_i^p is the
+ *     promoted float carry; w = sqrt(L_ii^2 + sigma V_i^2), c = w / L_ii,
+ *     s = V_i / L_ii, L_ii <- w; then c and s are rounded to float;
+ *   Apply in float arithmetic, one rounding per operation, in the order
+ *     printed (L_ij <- (L_ij + sigma s V_j) / c, then V_j <- c V_j - s L_ij
+ *     with the new L_ij);
+ * and the new L_ii is rounded to float once the group has passed row i.
+ * Failure: a group that fails at row i records i; later groups then process
+ * only the rows above it (whose values are still defined), so the row
+ * returned is the smallest failing row, that of CholeskyModifyB on all k
+ * columns.  Rows at and below it are left partially modified.
  */
 int orc_modify_mixed32(float *L, int64_t n, int64_t ld, const float *V, int64_t ldv, int64_t k,
-                       const int8_t *sigma, int64_t m_rows, int64_t *info)
+                       const int8_t *sigma, int64_t m_rows, int64_t kgroup, int64_t *info)
 {
     if (info) *info = -1;
     if (!check_args(n, ld, ldv, k, L, V, sigma)) return ORC_ERR_ARG;
     if (m_rows < 0 || m_rows > n) m_rows = n;
     if (n == 0 || k == 0) return ORC_OK;
+    if (kgroup <= 0 || kgroup > k) kgroup = k;
     float *W = (float *)malloc((size_t)n * (size_t)k * sizeof(float));
     if (!W) return ORC_ERR_NOMEM;
     for (int64_t p = 0; p < k; ++p)
         memcpy(W + p * n, V + p * ldv, (size_t)n * sizeof(float));
-    for (int64_t i = 0; i < m_rows; ++i) {
-        for (int64_t p = 0; p < k; ++p) {
-            float *v = W + p * n;
+    int64_t fail = -1;
+    for (int64_t g0 = 0; g0 < k; g0 += kgroup) {
+        const int64_t g1 = g0 + kgroup < k ? g0 + kgroup : k;
+        for (int64_t i = 0; i < m_rows; ++i) {
             double lii = (double)L[i + i * ld];
-            double c, s;
-            if (!compute_step(&c, &s, &lii, (double)v[i], sigma[p])) {
-                if (info) *info = i;
-                free(W);
-                return ORC_ERR_NOT_PD;
+            int ok = 1;
+            for (int64_t p = g0; p < g1 && ok; ++p) {
+                float *v = W + p * n;
+                double c, s;
+                if (!compute_step(&c, &s, &lii, (double)v[i], sigma[p])) {
+                    ok = 0;
+                    break;
+                }
+                float cf = (float)c, sf = (float)s, sg = (float)sigma[p];
+                for (int64_t j = i + 1; j < n; ++j) {
+                    float prod = sg * sf;
+                    prod = prod * v[j];
+                    float num = L[i + j * ld] + prod;
+                    float l = num / cf;
+                    L[i + j * ld] = l;
+                    float a = cf * v[j];
+                    float b = sf * l;
+                    v[j] = a - b;
+                }
+            }
+            if (!ok) {
+                fail = (fail < 0 || i < fail) ? i : fail;
+                m_rows = i;  /* later groups: the rows above the failure only */
+                break;
             }
             L[i + i * ld] = (float)lii;
-            float cf = (float)c, sf = (float)s, sg = (float)sigma[p];
-            for (int64_t j = i + 1; j < n; ++j) {
-                float prod = sg * sf;
-                prod = prod * v[j];
-                float num = L[i + j * ld] + prod;
-                float l = num / cf;
-                L[i + j * ld] = l;
-                float a = cf * v[j];
-                float b = sf * l;
-                v[j] = a - b;
-            }
         }
     }
     free(W);
+    if (fail >= 0) {
+        if (info) *info = fail;
+        return ORC_ERR_NOT_PD;
+    }
     return ORC_OK;
 }
 

@@ -19,6 +19,16 @@ Mutants:
   "compute_first" CholeskyModifyA as printed: the column's Compute happens
                   before the rows above it have rotated V_i
   "no_v_update"   V_j is never rotated (the carry of V between rows dropped)
+
+``modify_mixed32_np`` restates the mixed-precision emulation
+(``orc_modify_mixed32``: float storage and Apply, double Compute, the new
+diagonal carried in double across a group of vectors) with numpy float32
+arithmetic, equal to the C routine bit for bit.  Its mutants:
+  "cs_unrounded"     Apply uses c and s in double (each result still
+                     rounded to float)
+  "diag_per_vector"  the new diagonal is rounded to float after every
+                     vector instead of once per group
+  "apply_in_double"  Apply in double, rounded to float once per step
 """
 from __future__ import annotations
 
@@ -95,4 +105,52 @@ def _modify_a_printed(U, V, sig):
                 new = (U[j, i] + sig[p] * s * vi[p]) / c
                 vi[p] = c * vi[p] - s * new
                 U[j, i] = new
+    return U
+
+
+def modify_mixed32_np(U, V, sigma, group=None, mutant=None):
+    """Mixed-precision emulation on the upper-triangular float32 matrix ``U``
+    (float32 copies in, float32 out); ``group`` vectors per group (None: all)."""
+    f32 = np.float32
+    U = np.array(U, dtype=f32, copy=True)
+    V = np.array(V, dtype=f32, copy=True)
+    if V.ndim == 1:
+        V = V[:, None]
+    n, k = V.shape
+    sig = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (k,)).copy()
+    g = k if group is None or group <= 0 or group > k else int(group)
+    for g0 in range(0, k, g):
+        for i in range(n):
+            lii = np.float64(U[i, i])
+            for p in range(g0, min(k, g0 + g)):
+                v = V[:, p]
+                if not (lii > 0.0 and np.isfinite(lii)):
+                    raise NotPositiveDefinite(i)
+                t = lii * lii + sig[p] * np.float64(v[i]) * np.float64(v[i])
+                if not (t > 0.0 and np.isfinite(t)):
+                    raise NotPositiveDefinite(i)
+                w = np.sqrt(t)
+                c = w / lii
+                s = np.float64(v[i]) / lii
+                lii = w
+                if mutant == "diag_per_vector":
+                    lii = np.float64(f32(lii))
+                row = U[i, i + 1:]
+                vj = v[i + 1:]
+                if mutant == "cs_unrounded":
+                    new = ((row + (sig[p] * s * vj.astype(np.float64)).astype(f32)).astype(np.float64) / c).astype(f32)
+                    vnew = ((c * vj.astype(np.float64)).astype(f32) - (s * new.astype(np.float64)).astype(f32)).astype(f32)
+                elif mutant == "apply_in_double":
+                    r64, v64 = row.astype(np.float64), vj.astype(np.float64)
+                    n64 = (r64 + sig[p] * s * v64) / c
+                    new = n64.astype(f32)
+                    vnew = (c * v64 - s * n64).astype(f32)
+                else:
+                    cf, sf, sg = f32(c), f32(s), f32(sig[p])
+                    prod = (sg * sf) * vj
+                    new = (row + prod) / cf
+                    vnew = cf * vj - sf * new
+                U[i, i + 1:] = new
+                v[i + 1:] = vnew
+            U[i, i] = f32(lii)
     return U

@@ -108,6 +108,10 @@ bool use_pass_path(long long n, long long k, int dtype);
 // at least `bytes`, under the workspaces' lock.
 int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtype,
                         const std::function<int(const Scratch &, PassSpace &)> &fn);
+// Diagnostics: with CHM_TRACE=1 in the environment, a zeroed device buffer
+// of `words` timestamps that chm_trace_dump writes out (null otherwise).
+// Called under the workspaces' lock.
+long long *trace_buffer(size_t words, cudaStream_t stream);
 // Enqueue the passes of one modification (kb <= 16 vectors each).
 int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
                  const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,

@@ -303,6 +303,21 @@ static bool trace_on()
     return v != 0;
 }
 
+long long *trace_buffer(size_t words, cudaStream_t stream)
+{
+    if (!trace_on() || words == 0) return nullptr;
+    if (g_trace_cap < words) {
+        cudaFree(g_trace);
+        g_trace = nullptr;
+        g_trace_cap = 0;
+        if (cudaMalloc(&g_trace, words * sizeof(long long)) != cudaSuccess) return nullptr;
+        g_trace_cap = words;
+    }
+    cudaMemsetAsync(g_trace, 0, words * sizeof(long long), stream);
+    g_trace_words = words;
+    return g_trace;
+}
+
 static Workspace *find_workspace(int dev, cudaStream_t s, bool create)
 {
     for (Workspace *w : g_ws)

@@ -28,19 +28,6 @@ int env_or(const char *name, int dflt)
 }
 }  // namespace
 
-// Lookahead bounds per element type: the chain block keeps d - 1 tiles per
-// stage in shared memory.
-template <typename T>
-struct DMax;
-template <>
-struct DMax<float> {
-    static constexpr int value = 12;
-};
-template <>
-struct DMax<double> {
-    static constexpr int value = 4;
-};
-
 static int pass_kb_max()
 {
     int v = g_pass_kb.load();
@@ -52,9 +39,9 @@ static int pass_d(int dtype)
 {
     int v = g_pass_d.load();
     if (v <= 0) v = env_or("CHM_PASS_D", 0);
-    if (v <= 0) v = dtype == CHM_F64 ? 3 : 8;
-    const int dmax = dtype == CHM_F64 ? DMax<double>::value : DMax<float>::value;
-    return std::max(2, std::min(dmax, v));
+    if (v <= 0) v = dtype == CHM_F64 ? 4 : 6;
+    // each instantiation clamps it further to what its shared memory holds
+    return std::max(2, std::min(dtype == CHM_F64 ? 5 : 12, v));
 }
 
 bool use_pass_path(long long n, long long k, int dtype)
@@ -77,7 +64,7 @@ bool use_pass_path(long long n, long long k, int dtype)
 namespace {
 
 struct PassLayout {
-    size_t P, Zf, Dinv, G, gram, H, coef, escale, dfac, pflag, zflag, ctl, bytes;
+    size_t P, Ptag, Ztag, Dinv, G, gram, H, coef, escale, dfac, ctl, bytes;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -89,12 +76,13 @@ PassLayout pass_layout(long long n, int elt)
     const size_t KB = pass::kMaxKb;
     PassLayout l;
     size_t x = 0;
-    // the flag and control words first: they are zeroed on allocation
-    l.pflag = x; x = al(x + nb * 4);
-    l.zflag = x; x = al(x + nb * 4);
+    // the tagged words and control words first: they are zeroed on
+    // allocation (tag 0 matches no pass, whose epochs start at 1)
+    const size_t words = elt / 4;
+    l.Ptag = x; x = al(x + rows * KB * words * 8);
+    l.Ztag = x; x = al(x + rows * KB * words * 8);
     l.ctl = x; x = al(x + pass::kCtlInts * 4);
     l.P = x; x = al(x + rows * KB * elt);
-    l.Zf = x; x = al(x + rows * KB * elt);
     l.Dinv = x; x = al(x + nb * 1024 * elt);
     l.G = x; x = al(x + nb * 1024 * elt);
     l.gram = x; x = al(x + nb * KB * KB * 8);
@@ -115,7 +103,7 @@ size_t pass_workspace_bytes(long long n, int dtype)
 
 size_t pass_flag_bytes(long long n, int dtype)
 {
-    return pass_layout(n, dtype == CHM_F64 ? 8 : 4).P;
+    return pass_layout(n, dtype == CHM_F64 ? 8 : 4).P;  // the tagged and control words
 }
 
 // ---------------------------------------------------------------- launches
@@ -133,16 +121,16 @@ int sm_of_current(int *nsm)
 template <typename T, int KB>
 size_t trsm_smem()
 {
-    constexpr int DM = DMax<T>::value;
-    const size_t chain = sizeof(pass::ChainSmem<T, KB, DM>);
-    const size_t workers = (size_t)8 * 2 * (pass::kB * pass::kPad + pass::kB * KB) * sizeof(T);
+    const size_t chain = sizeof(pass::ChainSmem<T, KB>);
+    using W = pass::WorkerCfg<T, KB>;
+    const size_t workers = (size_t)W::warps * W::warp_bytes;
     return (std::max(chain, workers) + 127) & ~(size_t)127;
 }
 
 template <typename T, int KB>
 size_t sweep_smem()
 {
-    return (size_t)4 * 3 * sizeof(pass::SweepSlot<T, KB>);
+    return pass::SweepCfg<T, KB>::smem;
 }
 
 // One-time attributes and the sweep's resident blocks per SM, per device
@@ -153,15 +141,15 @@ int pass_setup(int dev, int *sweep_bps)
     static int bps[64] = {0};
     if (dev < 0 || dev >= 64) return CHM_ERR_ARG;
     if (!bps[dev]) {
-        constexpr int DM = DMax<T>::value;
-        if (cudaFuncSetAttribute(pass::trsm_kernel<T, KB, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(pass::trsm_kernel<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)trsm_smem<T, KB>()) != cudaSuccess)
             return CHM_ERR_CUDA;
         if (cudaFuncSetAttribute(pass::sweep_kernel<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sweep_smem<T, KB>()) != cudaSuccess)
             return CHM_ERR_CUDA;
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pass::sweep_kernel<T, KB>, 128, sweep_smem<T, KB>()) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pass::sweep_kernel<T, KB>,
+                                                          pass::SweepCfg<T, KB>::WARPS * 32, sweep_smem<T, KB>()) !=
                 cudaSuccess ||
             b < 1)
             return CHM_ERR_CUDA;
@@ -179,15 +167,15 @@ int launch_pass(pass::Args<T> A, cudaStream_t s)
     int rc = sm_of_current(&nsm);
     if (rc != CHM_OK) return rc;
     if ((rc = pass_setup<T, KB>(dev, &bps)) != CHM_OK) return rc;
-    constexpr int DM = DMax<T>::value;
     const int nb = A.nb;
+    A.d = std::min(A.d, pass::ChainCfg<T, KB>::DMAX);
     if (cudaMemsetAsync(A.ctl, 0, pass::kCtlInts * sizeof(int), s) != cudaSuccess) return CHM_ERR_CUDA;
     pass::prep_kernel<T><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
-    pass::trsm_kernel<T, KB, DM><<<nsm, 256, trsm_smem<T, KB>(), s>>>(A);
+    pass::trsm_kernel<T, KB><<<nsm, pass::kTrsmWarps * 32, trsm_smem<T, KB>(), s>>>(A);
     pass::gram_kernel<T, KB><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::scan_kernel<T, KB><<<(KB * KB + 31) / 32, 1024, 0, s>>>(A);
-    pass::coef_kernel<T, KB><<<nb, 32, 0, s>>>(A);
-    pass::sweep_kernel<T, KB><<<nsm * bps, 128, sweep_smem<T, KB>(), s>>>(A, 4);
+    pass::coef_kernel<T, KB><<<std::min(nb, nsm * 8), 32, pass::Packed<KB>::smem, s>>>(A);
+    pass::sweep_kernel<T, KB><<<nsm * bps, pass::SweepCfg<T, KB>::WARPS * 32, sweep_smem<T, KB>(), s>>>(A);
     return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
 }
 
@@ -218,7 +206,8 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.nb = (int)((n + pass::kB - 1) / pass::kB);
     A.d = pass_d(dtype);
     A.P = reinterpret_cast<T *>(w + lay.P);
-    A.Zf = reinterpret_cast<T *>(w + lay.Zf);
+    A.Ptag = reinterpret_cast<long long *>(w + lay.Ptag);
+    A.Ztag = reinterpret_cast<long long *>(w + lay.Ztag);
     A.Dinv = reinterpret_cast<T *>(w + lay.Dinv);
     A.G = reinterpret_cast<T *>(w + lay.G);
     A.gram = reinterpret_cast<double *>(w + lay.gram);
@@ -226,8 +215,6 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.coef = reinterpret_cast<T *>(w + lay.coef);
     A.escale = reinterpret_cast<T *>(w + lay.escale);
     A.dfac = reinterpret_cast<double *>(w + lay.dfac);
-    A.pflag = reinterpret_cast<int *>(w + lay.pflag);
-    A.zflag = reinterpret_cast<int *>(w + lay.zflag);
     A.ctl = reinterpret_cast<int *>(w + lay.ctl);
     A.status = sc.status;
     A.user_info = d_info;
@@ -242,6 +229,7 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
             if ((sigma ? sigma[q0 + q] : sign) < 0) mask |= 1ull << q;
         A.down_mask = mask;
         A.epoch = ++ps.epoch;
+        A.trace = trace_buffer((size_t)A.nb * 8, stream);  // the last pass's, with CHM_TRACE=1
         const int rc = launch_pass_kb<T>(A, stream);
         if (rc != CHM_OK) return rc;
     }

@@ -63,7 +63,6 @@ struct Args {
     unsigned long long down_mask;   // bit q: vector q is a downdate
     // workspace
     T *P;            // [nb * 32][KB]: F^T P = V, rows past n zero
-    T *Zf;           // [nb][32][KB]: V_b - (far tiles)^T P
     T *Dinv;         // [nb][32][32]: (D_b^T)^{-1}, D_b the diagonal block, row-major
     T *G;            // [nb][32][32]: Dinv_b F_{b-1,b}^T, row-major
     double *gram;    // [nb][KB][KB]: sum over the block's rows of p p^T
@@ -71,12 +70,15 @@ struct Args {
     T *coef;         // [nb * 32][2 KB]: (a_q, b_q) of each row
     T *escale;       // [nb * 32]: 1 / sqrt(D_kb) of each row
     double *dfac;    // [nb * 32]: sqrt(D_kb) of each row
-    int *pflag;      // [nb]: P of the block published (== epoch)
-    int *zflag;      // [nb]: far sum of the column block published (== epoch)
+    long long *Ptag; // [nb * 32][KB][words of T]: P as epoch-tagged words
+    long long *Ztag; // [nb][32][KB][words of T]: Zf as epoch-tagged words
     int *ctl;        // kCtlInts control words
     long long *status;     // sticky {status, row} of the stream
     long long *user_info;  // optional {status, row} of the call
     long long timeout_ns;
+    long long *trace;      // optional [nb][8] %globaltimer stamps of the substitution:
+                           // P posted, Zhat posted, far sum staged, stage loaded,
+                           // P published; a worker's last P seen, its far sum published
 };
 
 template <typename T>
@@ -180,183 +182,485 @@ __global__ void __launch_bounds__(32) prep_kernel(Args<T> A)
 
 // ---------------------------------------------------------------- forward substitution
 
-// out[i][q] = sum_l M[i][l] in[l][q] over the 256 threads of a block
-// (threads per output TPO, consecutive lanes, summed by shuffles); `sub`
-// subtracts the product from `out` instead.  Deterministic order.
-template <typename T, int KB>
-__device__ __forceinline__ void block_mv(const T (*M)[kPad], const T *in, T *out, bool sub)
+// Shared-memory row stride of a staged 32 x 32 tile: 16-byte rows (36 floats,
+// 34 doubles), so that tiles arrive in 16-byte chunks and a lane reading its
+// own row with 16-byte loads hits distinct banks.
+template <typename T>
+struct Stride {
+    static constexpr int value = kB + 16 / (int)sizeof(T);
+};
+// 16-byte vector of T.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+template <typename T>
+__device__ __forceinline__ T vget(const typename Vec16<T>::type &v, int u);
+template <>
+__device__ __forceinline__ float vget<float>(const float4 &v, int u)
 {
-    constexpr int NOUT = kB * KB;
-    constexpr int TPO = NOUT >= 256 ? 1 : 256 / NOUT;
-    constexpr int PER = NOUT >= 256 ? NOUT / 256 : 1;
-    constexpr int LEN = kB / TPO;
-    const int t = threadIdx.x;
-    const int s = t % TPO;
+    return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w;
+}
+template <>
+__device__ __forceinline__ double vget<double>(const double2 &v, int u)
+{
+    return u == 0 ? v.x : v.y;
+}
+
+__device__ __forceinline__ void cp16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void *gmem)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(gmem));
+}
+
+// Warp-cooperative stage of the tile rows r0.. r0 + 31, columns c0 .. c0 + 31
+// of L into dst[column][Stride] (columns >= n are zero).  `vec`: 16-byte
+// copies (every column's segment 16-byte aligned and all 32 rows inside the
+// column, r0 + 32 <= n); otherwise one element per copy, rows >= nrows zero.
+template <typename T>
+__device__ __forceinline__ void stage_tile(T *dst, const T *L, long long ld, long long r0, long long c0,
+                                           long long n, int nrows, bool vec, int lane)
+{
+    constexpr int S = Stride<T>::value;
+    if (vec) {
+        constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
+        constexpr int CPC = kB / E;             // chunks per column
+        for (int c = lane; c < kB * CPC; c += 32) {
+            const int col = c / CPC, ch = c % CPC;
+            T *d = dst + col * S + ch * E;
+            if (c0 + col < n) {
+                cp16(d, L + (r0 + ch * E) + (c0 + col) * ld);
+            } else {
 #pragma unroll
-    for (int o = 0; o < PER; ++o) {
-        const int idx = t / TPO + o * (256 / TPO);
-        const int i = idx % kB, q = idx / kB;
-        T a0 = T(0), a1 = T(0);
-#pragma unroll
-        for (int u = 0; u < LEN; u += 2) {
-            const int l = s * LEN + u;
-            a0 = fma(M[i][l], in[l * KB + q], a0);
-            a1 = fma(M[i][l + 1], in[(l + 1) * KB + q], a1);
+                for (int e = 0; e < E; ++e) d[e] = T(0);
+            }
         }
-        T acc = a0 + a1;
-#pragma unroll
-        for (int off = TPO / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (s == 0) out[i * KB + q] = sub ? out[i * KB + q] - acc : acc;
+    } else {
+        for (int col = 0; col < kB; ++col) {
+            T *d = dst + col * S + lane;
+            if (c0 + col < n && lane < nrows) cp_elem(d, L + (r0 + lane) + (c0 + col) * ld);
+            else *d = T(0);
+        }
+    }
+}
+// The same for a dense row-major 32 x 32 matrix of the workspace (always
+// 16-byte aligned): dst[row][Stride].
+template <typename T>
+__device__ __forceinline__ void stage_dense(T *dst, const T *src, int lane)
+{
+    constexpr int S = Stride<T>::value;
+    constexpr int E = 16 / (int)sizeof(T);
+    constexpr int CPR = kB / E;
+    for (int c = lane; c < kB * CPR; c += 32) {
+        const int row = c / CPR, ch = c % CPR;
+        cp16(dst + row * S + ch * E, src + row * kB + ch * E);
     }
 }
 
-// Shared memory of the chain block.
-template <typename T, int KB, int DMAX>
+// Lane i: out[q] = sum_l M[i][l] x[l][q] (M staged with Stride, x [32][KB]).
+template <typename T, int KB>
+__device__ __forceinline__ void lane_mv(const T *M, const T *x, T (&out)[KB], int i)
+{
+    constexpr int S = Stride<T>::value;
+    constexpr int E = Vec16<T>::n;
+    using V = typename Vec16<T>::type;
+    T a0[KB], a1[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) a0[q] = a1[q] = T(0);
+    const V *row = reinterpret_cast<const V *>(M + i * S);
+#pragma unroll
+    for (int c = 0; c < kB / E; ++c) {
+        const V m = row[c];
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+            const int l = c * E + u;
+            const T mv = vget<T>(m, u);
+            if (KB % E == 0) {
+                // x[l][*] as 16-byte broadcast loads
+                const V *xr = reinterpret_cast<const V *>(x + l * KB);
+#pragma unroll
+                for (int g = 0; g < KB / E; ++g) {
+                    const V xv = xr[g];
+#pragma unroll
+                    for (int w = 0; w < E; ++w) {
+                        const int q = g * E + w;
+                        if (l & 1) a1[q] = fma(mv, vget<T>(xv, w), a1[q]);
+                        else a0[q] = fma(mv, vget<T>(xv, w), a0[q]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < KB; ++q) {
+                    if (l & 1) a1[q] = fma(mv, x[l * KB + q], a1[q]);
+                    else a0[q] = fma(mv, x[l * KB + q], a0[q]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) out[q] = a0[q] + a1[q];
+}
+
+// A value published as epoch-tagged 64-bit words (one per 32 bits of T):
+// each 8-byte store is single-copy atomic, so a reader that sees every word
+// tagged with the current epoch has the value, and no fence or flag is needed.
+template <typename T>
+struct Tag {
+    static constexpr int words = (int)sizeof(T) / 4;
+};
+__device__ __forceinline__ void put_tag(long long *w, float v, long long ep64)
+{
+    __stcg(w, ep64 | (long long)(unsigned)__float_as_uint(v));
+}
+__device__ __forceinline__ void put_tag(long long *w, double v, long long ep64)
+{
+    put_tagged(w, v, ep64);
+}
+__device__ __forceinline__ bool get_tag(const long long *w, long long ep64, float *v)
+{
+    const long long x = ld_relaxed_gpu(w);
+    if ((x & ~0xffffffffll) != ep64) return false;
+    *v = __uint_as_float((unsigned)(x & 0xffffffffll));
+    return true;
+}
+__device__ __forceinline__ bool get_tag(const long long *w, long long ep64, double *v)
+{
+    return get_tagged(w, ep64, v);
+}
+
+// Warp-wide bounded wait on a shared-memory counter (every lane polls; the
+// verdict is lane 0's).  False if the block is stopping or the wait ran out.
+__device__ __forceinline__ bool warp_seq_wait(const SyncArgs &sy, const volatile int *seq, int want,
+                                              volatile int *stop, long long who)
+{
+    int ok = 1;
+    if (*seq < want) {
+        // spin on the counter (the producers are warps of this block, so the
+        // wait is short and a sleep would only add its own granularity)
+        const long long t0 = global_ns();
+        for (unsigned it = 1;; ++it) {
+            if (*seq >= want) break;
+            if ((it & 1023u) == 0u) {
+                if (*stop || aborted(sy)) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > sy.timeout_ns || it > (1u << 28)) {
+                    if ((threadIdx.x & 31) == 0) record_error(sy, kStatusTimeout, who);
+                    *stop = 1;
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    __threadfence_block();
+    return ok != 0;
+}
+__device__ __forceinline__ void warp_seq_post(volatile int *seq, int v)
+{
+    __syncwarp();
+    __threadfence_block();
+    if ((threadIdx.x & 31) == 0) *seq = v;
+}
+
+// Warps of the forward-substitution kernel and the chain block's roles.
+constexpr int kTrsmWarps = 12;
+constexpr int kWCrit = 0, kWZhat = 1, kWNear0 = 2;
+constexpr int kNearWarps = kTrsmWarps - 5;  // warps 2 .. 8
+constexpr int kWZf = kTrsmWarps - 3, kWLoad = kTrsmWarps - 2, kWPub = kTrsmWarps - 1;
+
+// Lookahead bound (near tiles d - 1 per step) and ring depths per
+// instantiation, sized to the 227 KB of shared memory.
+template <typename T, int KB>
+struct ChainCfg {
+    static constexpr int DMAX = sizeof(T) == 4 ? (KB <= 2 ? 10 : KB <= 4 ? 9 : KB <= 8 ? 8 : 6)
+                                               : (KB <= 2 ? 5 : KB <= 8 ? 4 : 3);
+    static constexpr int RP = DMAX + 2;   // P ring
+    static constexpr int RT = DMAX;       // per near offset
+    static constexpr int RZ = 4;          // Zhat ring
+    static constexpr int RF = 4;          // far-sum ring
+    static constexpr int PF = 8;          // steps of L2 prefetch ahead of the stage
+    static constexpr size_t tile = sizeof(T) * kB * Stride<T>::value;
+    static constexpr size_t stage = (size_t)(DMAX + 1) * tile;  // G, Dinv, d - 1 near tiles
+    static constexpr size_t rest = sizeof(T) * kB * KB * ((size_t)RP + (size_t)(DMAX - 1) * RT + RZ + RF + 1) +
+                                   tile + 256;
+    static constexpr int fit = (int)((224u * 1024u - rest) / stage);
+    static constexpr int RS = fit > 4 ? 4 : fit;  // staged steps
+};
+
+template <typename T, int KB>
 struct ChainSmem {
-    T G[3][kB][kPad];              // G_m of step m (stage m % 3)
-    T Di[3][kB][kPad];             // Dinv_{m+1}
-    T near[3][DMAX - 1][kB][kPad]; // tiles (m, m + 2 .. m + d), [column][row]
-    T acc[DMAX + 1][kB * KB];      // near sums of blocks m + 1 .. m + d
-    T P[2][kB * KB];               // P_m, P_{m-1}
-    T zhat[kB * KB];               // Dinv_m (Zf_m + acc_m), for the next step
-    T w[kB * KB];
-    T tmp[kB * KB];
+    using C = ChainCfg<T, KB>;
+    static constexpr int S = Stride<T>::value;
+    T G[C::RS][kB * S];                   // G_m of step m
+    T Di[C::RS][kB * S];                  // Dinv_{m+1}
+    T near[C::DMAX - 1][C::RS][kB * S];   // per offset j = 2 .. d: tiles (m, m + j), [column][row]
+    T Di0[kB * S];                        // Dinv_0
+    T P[C::RP][kB * KB];
+    T Tn[C::DMAX - 1][C::RT][kB * KB];    // F_{b-j,b}^T P_{b-j} per offset j
+    T Z[C::RZ][kB * KB];                  // Zhat_b
+    T F[C::RF][kB * KB];                  // far sums Zf_b
+    T w[kB * KB];                         // Zhat warp's work vector
+    int pseq, zseq, lseq, fseq, pubseq;
+    int nseq[kNearWarps];
     int stop;
 };
 
-template <typename T, int KB, int DMAX>
-__device__ void chain_prefetch(const Args<T> &A, ChainSmem<T, KB, DMAX> &S, int m)
-{
-    // stage of step m: G_m, Dinv_{m+1}, near tiles (m, b), b = m + 2 .. m + d
-    const int st = m % 3;
-    const int t = threadIdx.x, l = t & 31, g8 = t >> 5;
-    const long long n = A.n, ld = A.ld;
-    if (m >= 1 && m < A.nb) {
-        const T *src = A.G + (size_t)m * kB * kB;
-        for (int i = g8; i < kB; i += 8) cp_elem(&S.G[st][i][l], src + i * kB + l);
-    }
-    if (m + 1 < A.nb) {
-        const T *src = A.Dinv + (size_t)(m + 1) * kB * kB;
-        for (int i = g8; i < kB; i += 8) cp_elem(&S.Di[st][i][l], src + i * kB + l);
-    }
-    if (m < A.nb) {
-        const long long r0 = (long long)m * kB;
-        for (int j = 2; j <= A.d; ++j) {
-            const int b = m + j;
-            if (b >= A.nb) break;
-            const long long c0 = (long long)b * kB;
-            for (int i = g8; i < kB; i += 8) {
-                if (c0 + i < n) cp_elem(&S.near[st][j - 2][i][l], A.L + (r0 + l) + (c0 + i) * ld);
-                else S.near[st][j - 2][i][l] = T(0);
-            }
-        }
-    }
-    cp_commit();
-}
-
-// The block that walks the forward substitution F^T P = V block by block:
-//   P_m = Zhat_m - G_m P_{m-1},  Zhat_m = Dinv_m (Zf_m - sum_{r=m-d}^{m-2} F_{r,m}^T P_r),
-// the near sums from its own copies of the tiles, the far sum Zf_m from
-// the worker of column block m (m > d), or V_m.
-template <typename T, int KB, int DMAX>
+// The chain block: every role is one warp, linked by shared-memory
+// sequence counters; nothing on the critical cycle
+//   P_m -> F_{m,m+2}^T P_m -> Zhat_{m+2} -> P_{m+2}
+// waits on global memory: the loader stages G, Dinv and the near tiles a
+// few steps ahead (and prefetches further ones into L2), the far-sum warp
+// polls the workers' tagged sums ahead of use, the publisher writes each P
+// as tagged words.
+template <typename T, int KB>
 __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 {
-    ChainSmem<T, KB, DMAX> &S = *reinterpret_cast<ChainSmem<T, KB, DMAX> *>(smem);
-    const int t = threadIdx.x;
+    using C = ChainCfg<T, KB>;
+    ChainSmem<T, KB> &S = *reinterpret_cast<ChainSmem<T, KB> *>(smem);
+    constexpr int SD = Stride<T>::value;
+    constexpr int TW = Tag<T>::words;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = A.nb, d = A.d;
-    const long long n = A.n;
+    const long long n = A.n, ld = A.ld;
+    const long long ep64 = (long long)A.epoch << 32;
     const SyncArgs sy = sync_of(A);
-    for (int x = t; x < (DMAX + 1) * kB * KB; x += 256) (&S.acc[0][0])[x] = T(0);
-    if (t == 0) S.stop = 0;
-    // Zhat_0 = Dinv_0 V_0
-    {
-        const T *src = A.Dinv;
-        for (int i = t >> 5; i < kB; i += 8) S.Di[2][i][t & 31] = src[i * kB + (t & 31)];
-        for (int x = t; x < kB * KB; x += 256) {
-            const int i = x / KB, q = x % KB;
-            S.w[x] = (i < n && q < A.kb) ? A.V[i + q * A.ldv] : T(0);
-        }
-        __syncthreads();
-        block_mv<T, KB>(S.Di[2], S.w, S.zhat, false);
-        __syncthreads();
+    volatile int *stop = &S.stop;
+    const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
+    if (threadIdx.x == 0) {
+        S.pseq = S.zseq = S.lseq = S.fseq = S.pubseq = 0;
+        for (int t = 0; t < kNearWarps; ++t) S.nseq[t] = 0;
+        S.stop = 0;
     }
-    chain_prefetch<T, KB, DMAX>(A, S, 0);
-    chain_prefetch<T, KB, DMAX>(A, S, 1);
-    for (int m = 0; m < nb; ++m) {
-        const int st = m % 3;
-        chain_prefetch<T, KB, DMAX>(A, S, m + 2);
-        cp_wait<2>();
-        __syncthreads();
-        T *Pm = S.P[m & 1];
-        // critical step: P_m = Zhat_m - G_m P_{m-1}
-        if (m == 0) {
-            for (int x = t; x < kB * KB; x += 256) Pm[x] = S.zhat[x];
-        } else {
-            block_mv<T, KB>(S.G[st], S.P[(m - 1) & 1], S.tmp, false);
-            __syncthreads();
-            for (int x = t; x < kB * KB; x += 256) Pm[x] = S.zhat[x] - S.tmp[x];
-        }
-        __syncthreads();
-        for (int x = t; x < kB * KB; x += 256) __stcg(A.P + (size_t)m * kB * KB + x, Pm[x]);
-        __syncthreads();
-        if (t == 0) {
-            __threadfence();
-            st_release_gpu(A.pflag + m, A.epoch);
-        }
-        // near sums of later blocks with P_m: tiles (m, m + 2 .. m + d)
-        for (int j = 2; j <= d; ++j) {
-            const int b = m + j;
-            if (b >= nb) break;
-            block_mv<T, KB>(S.near[st][j - 2], Pm, S.acc[b % (DMAX + 1)], true);
-        }
-        // Zhat_{m+1} = Dinv_{m+1} (Zf_{m+1} + acc_{m+1})
-        if (m + 1 < nb) {
-            const int b = m + 1;
-            if (b > d) {
-                if (t == 0) {
-                    const bool ok = bounded_wait(
-                        sy, [&] { return ld_relaxed_gpu(A.zflag + b) == A.epoch; },
-                        [] { fence_acq_rel_gpu(); }, b);
-                    S.stop = ok ? 0 : 1;
-                }
-                __syncthreads();
-                if (S.stop) {
-                    cp_wait<0>();
-                    return;
-                }
-                const T *zf = A.Zf + (size_t)b * kB * KB;
-                for (int x = t; x < kB * KB; x += 256) S.w[x] = __ldcg(zf + x) + S.acc[b % (DMAX + 1)][x];
-            } else {
-                const long long r0 = (long long)b * kB;
-                for (int x = t; x < kB * KB; x += 256) {
-                    const int i = x / KB, q = x % KB;
-                    const T v = (r0 + i < n && q < A.kb) ? A.V[r0 + i + q * A.ldv] : T(0);
-                    S.w[x] = v + S.acc[b % (DMAX + 1)][x];
+    __syncthreads();
+    const int nnear = d - 1;  // offsets j = 2 .. d, offset j on near warp (j - 2) % kNearWarps
+#define CW(seqp, want, who)                                                     \
+    do {                                                                        \
+        if (!warp_seq_wait(sy, (seqp), (want), stop, (who))) {                  \
+            cp_wait<0>();                                                       \
+            return;                                                             \
+        }                                                                       \
+    } while (0)
+
+    if (warp == kWLoad) {
+        for (int m = 0; m < nb; ++m) {
+            const int st = m % C::RS;
+            if (m >= C::RS) {
+                const int old = m - C::RS;
+                CW(&S.pseq, old + 1, -10);
+                CW(&S.zseq, old + 2, -12);
+            }
+            if (m >= 1) stage_dense(S.G[st], A.G + (size_t)m * kB * kB, lane);
+            if (m + 1 < nb) stage_dense(S.Di[st], A.Dinv + (size_t)(m + 1) * kB * kB, lane);
+            cp_commit();
+            // later steps' near band into L2 (one line per column segment)
+            const int mf = m + C::PF;
+            if (mf < nb) {
+                const long long rf = (long long)mf * kB;
+                for (int c = lane; c < (d - 1) * kB; c += 32) {
+                    const long long col = (long long)(mf + 2) * kB + c;
+                    if (col < n) prefetch_l2(A.L + rf + col * ld);
                 }
             }
-            __syncthreads();
-            block_mv<T, KB>(S.Di[st], S.w, S.zhat, false);
-            for (int x = t; x < kB * KB; x += 256) S.acc[b % (DMAX + 1)][x] = T(0);
+            // stage m - 1 is complete once at most one group is pending
+            cp_wait<1>();
+            warp_seq_post(&S.lseq, m);
+            if (A.trace && lane == 0 && m >= 1) A.trace[(size_t)(m - 1) * 8 + 3] = global_ns();
         }
-        __syncthreads();
+        cp_wait<0>();
+        warp_seq_post(&S.lseq, nb);
+    } else if (warp == kWCrit) {
+        for (int m = 0; m < nb; ++m) {
+            CW(&S.zseq, m + 1, m);
+            if (m >= 1) CW(&S.lseq, m + 1, m);
+            if (m >= C::RP) CW(&S.pubseq, m - C::RP + 1, m);
+            T out[KB];
+            const T *z = S.Z[m % C::RZ];
+            if (m == 0) {
+#pragma unroll
+                for (int q = 0; q < KB; ++q) out[q] = z[lane * KB + q];
+            } else {
+                lane_mv<T, KB>(S.G[m % C::RS], S.P[(m - 1) % C::RP], out, lane);
+#pragma unroll
+                for (int q = 0; q < KB; ++q) out[q] = z[lane * KB + q] - out[q];
+            }
+            T *pm = S.P[m % C::RP];
+#pragma unroll
+            for (int q = 0; q < KB; ++q) pm[lane * KB + q] = out[q];
+            warp_seq_post(&S.pseq, m + 1);
+            if (A.trace && lane == 0) A.trace[(size_t)m * 8 + 0] = global_ns();
+        }
+    } else if (warp >= kWNear0 && warp < kWNear0 + kNearWarps) {
+        const int t = warp - kWNear0;
+        if (t >= nnear) return;
+        // this warp's offsets' tiles, staged RS - 1 steps ahead (the factor as
+        // it entered the pass: nothing to wait for)
+        auto stage = [&](int m) {
+            if (m < nb) {
+                for (int j = 2 + t; j <= d; j += kNearWarps) {
+                    const int b = m + j;
+                    if (b >= nb) break;
+                    stage_tile(S.near[j - 2][m % C::RS], A.L, ld, (long long)m * kB, (long long)b * kB, n, kB,
+                               vec, lane);
+                }
+            }
+            cp_commit();
+        };
+        for (int m = 0; m < C::RS - 1; ++m) stage(m);
+        for (int m = 0; m < nb; ++m) {
+            stage(m + C::RS - 1);
+            CW(&S.pseq, m + 1, m);
+            cp_wait<C::RS - 1>();
+            __syncwarp();
+            const T *pm = S.P[m % C::RP];
+            for (int j = 2 + t; j <= d; j += kNearWarps) {
+                const int b = m + j;
+                if (b >= nb) break;
+                T out[KB];
+                lane_mv<T, KB>(S.near[j - 2][m % C::RS], pm, out, lane);
+                T *dst = S.Tn[j - 2][b % C::RT];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) dst[lane * KB + q] = out[q];
+            }
+            warp_seq_post(&S.nseq[t], m + 1);
+        }
+    } else if (warp == kWZhat) {
+        // Dinv_0 for Zhat_0
+        stage_dense(S.Di0, A.Dinv, lane);
+        cp_commit();
+        cp_wait<0>();
+        __syncwarp();
+        for (int b = 0; b < nb; ++b) {
+            const long long r0 = (long long)b * kB;
+            // w = Zf_b - sum_{j=2}^{d} F_{b-j,b}^T P_{b-j}
+            T w[KB];
+            if (b > d) {
+                CW(&S.fseq, b + 1, b);
+                const T *f = S.F[b % C::RF];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) w[q] = f[lane * KB + q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < KB; ++q)
+                    w[q] = (r0 + lane < n && q < A.kb) ? A.V[r0 + lane + q * A.ldv] : T(0);
+            }
+            for (int j = 2; j <= d && j <= b; ++j) {
+                const int t = (j - 2) % kNearWarps;
+                CW(&S.nseq[t], b - j + 1, b);
+                const T *tn = S.Tn[j - 2][b % C::RT];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) w[q] -= tn[lane * KB + q];
+            }
+#pragma unroll
+            for (int q = 0; q < KB; ++q) S.w[lane * KB + q] = w[q];
+            __syncwarp();
+            const T *Di = S.Di0;
+            if (b >= 1) {
+                CW(&S.lseq, b, b);  // stage b - 1 holds Dinv_b
+                Di = S.Di[(b - 1) % C::RS];
+            }
+            T out[KB];
+            lane_mv<T, KB>(Di, S.w, out, lane);
+            T *z = S.Z[b % C::RZ];
+#pragma unroll
+            for (int q = 0; q < KB; ++q) z[lane * KB + q] = out[q];
+            warp_seq_post(&S.zseq, b + 1);
+            if (A.trace && lane == 0) A.trace[(size_t)b * 8 + 1] = global_ns();
+        }
+    } else if (warp == kWZf) {
+        for (int b = d + 1; b < nb; ++b) {
+            if (b >= C::RF) CW(&S.zseq, b - C::RF + 1, b);
+            const long long *src = A.Ztag + ((size_t)b * kB + lane) * KB * TW;
+            T v[KB];
+            const long long t0 = global_ns();
+            unsigned ns = 32;
+            for (unsigned it = 0;; ++it) {
+                bool ok = true;
+#pragma unroll
+                for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &v[q]) && ok;
+                if (__all_sync(0xffffffffu, ok)) break;
+                if ((it & 15u) == 15u) {
+                    int bad = 0;
+                    if (lane == 0) {
+                        if (*stop || aborted(sy)) bad = 1;
+                        else if (global_ns() - t0 > sy.timeout_ns || it > (1u << 26)) {
+                            record_error(sy, kStatusTimeout, b);
+                            *stop = 1;
+                            bad = 1;
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, bad, 0)) return;
+                }
+                __nanosleep(ns);
+                if (ns < 128) ns <<= 1;
+            }
+            T *f = S.F[b % C::RF];
+#pragma unroll
+            for (int q = 0; q < KB; ++q) f[lane * KB + q] = v[q];
+            warp_seq_post(&S.fseq, b + 1);
+            if (A.trace && lane == 0) A.trace[(size_t)b * 8 + 2] = global_ns();
+        }
+    } else if (warp == kWPub) {
+        for (int m = 0; m < nb; ++m) {
+            CW(&S.pseq, m + 1, m);
+            const T *pm = S.P[m % C::RP];
+            long long *tg = A.Ptag + ((size_t)m * kB + lane) * KB * TW;
+            T *plain = A.P + ((size_t)m * kB + lane) * KB;
+#pragma unroll
+            for (int q = 0; q < KB; ++q) {
+                const T v = pm[lane * KB + q];
+                put_tag(tg + q * TW, v, ep64);
+                plain[q] = v;
+            }
+            warp_seq_post(&S.pubseq, m + 1);
+            if (A.trace && lane == 0) A.trace[(size_t)m * 8 + 4] = global_ns();
+        }
     }
-    cp_wait<0>();
+#undef CW
 }
 
 // Worker warps: the far part of column block b's sum,
 //   Zf_b = V_b - sum_{r < b - d} F_{r,b}^T P_r,
-// one tile per published P_r, the next tile fetched while this one is used.
+// tiles staged a few ahead (they are the factor as it entered the pass), each
+// P_r polled as tagged words, Zf_b published as tagged words.
+template <typename T, int KB>
+struct WorkerCfg {
+    static constexpr int NS = 3;  // staged tiles per warp
+    static constexpr size_t warp_bytes = sizeof(T) * ((size_t)NS * kB * Stride<T>::value + kB * KB);
+    static constexpr int warps = (int)((200u * 1024u) / warp_bytes) < kTrsmWarps
+                                     ? (int)((200u * 1024u) / warp_bytes) : kTrsmWarps;
+};
+
 template <typename T, int KB>
 __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
 {
+    using W = WorkerCfg<T, KB>;
+    constexpr int SD = Stride<T>::value;
+    constexpr int TW = Tag<T>::words;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kTile = kB * kPad;
-    T *base = reinterpret_cast<T *>(smem) + (size_t)warp * 2 * (kTile + kB * KB);
-    T *tile[2] = {base, base + kTile};
-    T *Pr = base + 2 * kTile;  // [32][KB]
+    if (warp >= W::warps) return;
+    T *base = reinterpret_cast<T *>(smem + (size_t)warp * W::warp_bytes);
+    T *Pr = base + (size_t)W::NS * kB * SD;  // [32][KB]
     const long long n = A.n, ld = A.ld;
     const int nb = A.nb, d = A.d;
+    const long long ep64 = (long long)A.epoch << 32;
     const SyncArgs sy = sync_of(A);
+    const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = ld_relaxed_gpu(A.ctl + kCtlAbort) ? -1 : atomicAdd(A.ctl + kCtlWorkTicket, 1);
@@ -370,69 +674,69 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
 #pragma unroll
         for (int q = 0; q < KB; ++q) z[q] = (col_ok && q < A.kb) ? A.V[c0 + lane + q * A.ldv] : T(0);
         const int nfar = b - d;
-        auto fetch = [&](int r, T *dst) {
-            const long long r0 = (long long)r * kB;
-#pragma unroll 8
-            for (int i = 0; i < kB; ++i) {
-                if (c0 + i < n) cp_elem(dst + i * kPad + lane, A.L + (r0 + lane) + (c0 + i) * ld);
-                else dst[i * kPad + lane] = T(0);
-            }
+        for (int r = 0; r < W::NS - 1 && r < nfar; ++r) {
+            stage_tile(base + (size_t)(r % W::NS) * kB * SD, A.L, ld, (long long)r * kB, c0, n, kB, vec, lane);
             cp_commit();
-        };
-        fetch(0, tile[0]);
+        }
         for (int r = 0; r < nfar; ++r) {
-            if (r + 1 < nfar) fetch(r + 1, tile[(r + 1) & 1]);
-            int ok = 1;
-            if (lane == 0)
-                ok = bounded_wait(sy, [&] { return ld_relaxed_gpu(A.pflag + r) == A.epoch; },
-                                  [] { fence_acq_rel_gpu(); }, b) ? 1 : 0;
-            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
-            const T *src = A.P + (size_t)r * kB * KB;
+            const int rn = r + W::NS - 1;
+            if (rn < nfar)
+                stage_tile(base + (size_t)(rn % W::NS) * kB * SD, A.L, ld, (long long)rn * kB, c0, n, kB, vec, lane);
+            cp_commit();
+            // P_r: lane l polls row l's tagged words
+            const long long *src = A.Ptag + ((size_t)r * kB + lane) * KB * TW;
+            T pv[KB];
+            const long long t0 = global_ns();
+            unsigned ns = 32;
+            for (unsigned it = 0;; ++it) {
+                bool ok = true;
 #pragma unroll
-            for (int x = lane; x < kB * KB; x += 32) Pr[x] = __ldcg(src + x);
-            if (r + 1 < nfar) cp_wait<1>();
-            else cp_wait<0>();
-            __syncwarp();
-            const T *tl = tile[r & 1] + lane * kPad;
-            if (KB == 1) {
-                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-#pragma unroll
-                for (int l = 0; l < kB; l += 4) {
-                    s0 = fma(tl[l], Pr[l], s0);
-                    s1 = fma(tl[l + 1], Pr[l + 1], s1);
-                    s2 = fma(tl[l + 2], Pr[l + 2], s2);
-                    s3 = fma(tl[l + 3], Pr[l + 3], s3);
+                for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &pv[q]) && ok;
+                if (__all_sync(0xffffffffu, ok)) break;
+                if ((it & 15u) == 15u) {
+                    int bad = 0;
+                    if (lane == 0) {
+                        if (aborted(sy)) bad = 1;
+                        else if (global_ns() - t0 > sy.timeout_ns || it > (1u << 26)) {
+                            record_error(sy, kStatusTimeout, b);
+                            bad = 1;
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, bad, 0)) {
+                        cp_wait<0>();
+                        return;
+                    }
                 }
-                z[0] -= (s0 + s1) + (s2 + s3);
-            } else {
-#pragma unroll 4
-                for (int l = 0; l < kB; ++l) {
-                    const T f = tl[l];
-#pragma unroll
-                    for (int q = 0; q < KB; ++q) z[q] = fma(-f, Pr[l * KB + q], z[q]);
-                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
             }
+#pragma unroll
+            for (int q = 0; q < KB; ++q) Pr[lane * KB + q] = pv[q];
+            if (A.trace && lane == 0 && r == nfar - 1) A.trace[(size_t)b * 8 + 6] = global_ns();
+            cp_wait<W::NS - 1>();
+            __syncwarp();
+            T t[KB];
+            lane_mv<T, KB>(base + (size_t)(r % W::NS) * kB * SD, Pr, t, lane);
+#pragma unroll
+            for (int q = 0; q < KB; ++q) z[q] -= t[q];
             __syncwarp();
         }
-        T *zf = A.Zf + (size_t)b * kB * KB + (size_t)lane * KB;
+        cp_wait<0>();
+        long long *zt = A.Ztag + ((size_t)b * kB + lane) * KB * TW;
 #pragma unroll
-        for (int q = 0; q < KB; ++q) __stcg(zf + q, z[q]);
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            st_release_gpu(A.zflag + b, A.epoch);
-        }
+        for (int q = 0; q < KB; ++q) put_tag(zt + q * TW, z[q], ep64);
+        if (A.trace && lane == 0) A.trace[(size_t)b * 8 + 7] = global_ns();
     }
 }
 
-template <typename T, int KB, int DMAX>
-__global__ void __launch_bounds__(256, 1) trsm_kernel(Args<T> A)
+template <typename T, int KB>
+__global__ void __launch_bounds__(kTrsmWarps * 32, 1) trsm_kernel(Args<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_role;
     if (threadIdx.x == 0) s_role = atomicAdd(A.ctl + kCtlRole, 1);
     __syncthreads();
-    if (s_role == 0) trsm_chain<T, KB, DMAX>(A, smem);
+    if (s_role == 0) trsm_chain<T, KB>(A, smem);
     else trsm_workers<T, KB>(A, smem);
 }
 
@@ -476,8 +780,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(Args<T> A)
     const int b0 = s * len, b1 = min(nb, b0 + len);
     const bool valid = e < KB * KB;
     double sum = 0.0;
-    if (valid)
-        for (int b = b0; b < b1; ++b) sum += A.gram[(size_t)b * KB * KB + e];
+    if (valid) {
+#pragma unroll 8
+        for (int b = b0; b < b1; ++b) sum += __ldcg(A.gram + (size_t)b * KB * KB + e);
+    }
     seg[s][threadIdx.x & 31] = sum;
     __syncthreads();
     double pre = 0.0;
@@ -493,19 +799,31 @@ __global__ void __launch_bounds__(1024) scan_kernel(Args<T> A)
     }
 }
 
-// Per row block b (one warp): U with H_b = U Sigma U^T, then the rows in
-// order: lane r's rotated vector y_r = x_r, its rotations (D, a, b) and the
-// transform of the later rows' vectors,
-//   x_q <- (D_{q-1} x_q - y_q sum_{q'<q} sigma_q' y_q' x_q') / sqrt(D_{q-1} D_q),
-// the carry scales t_q <- t_q sqrt(D_q / D_{q-1}).  Lanes are rows; vectors
-// q < kb (padding vectors have p = 0 and change nothing).
+// Per row block b (one warp, lane = row r0 + lane), every row on its own:
+// its prefix Gram H_r = H_b + sum_{i < r in the block} p_i p_i^T (an
+// in-place prefix over the block's rows in shared memory, packed lower
+// triangles), then H_r = L D L^T (L unit lower), z = L^{-1} p_r, and with
+// |D_q| = sigma_q D_q (the factor of H_r = U Sigma U^T is U = L |D|^{1/2},
+// so y_q = z_q / |D_q|^{1/2} and t_q = |D_q|^{1/2}):
+//   Dc_q = 1 + sum_{q' <= q} sigma_q' z_q'^2 / |D_q'|,
+//   a_q = sigma_q z_q,   b_q = z_q / (|D_q| Dc_q),
+//   e = Dc_kb^{-1/2},    the diagonal factor Dc_kb^{1/2}.
+// All in double.  A pivot of the wrong sign or a non-positive Dc is the
+// Compute step's failure (the modified matrix is not positive definite).
+template <int KB>
+struct Packed {
+    static constexpr int entries = KB * (KB + 1) / 2;
+    static constexpr int stride = entries | 1;  // odd: the lanes' rows fall in distinct banks
+    static constexpr size_t smem = sizeof(double) * (kB + 1) * stride;
+};
+__device__ __forceinline__ int pidx(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
+
 template <typename T, int KB>
 __global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
 {
-    __shared__ double U[KB][KB + 1];
-    __shared__ double iu[KB];
-    __shared__ double sh_y[KB], sh_al[KB], sh_be[KB];
-    __shared__ double sh_t[KB];
+    using PK = Packed<KB>;
+    constexpr int NE = PK::entries, HS = PK::stride;
+    extern __shared__ double Hs[];  // [kB + 1][HS]
     const int lane = threadIdx.x;
     const SyncArgs sy = sync_of(A);
     const long long n = A.n;
@@ -513,139 +831,117 @@ __global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
     for (int b = blockIdx.x; b < A.nb; b += gridDim.x) {
         const long long r0 = (long long)b * kB;
         const int rows = (int)min((long long)kB, n - r0);
-        // LDL^T of H_b (lane = row of H), U = L sqrt|D|
-        if (lane < KB)
-            for (int j = 0; j < KB; ++j) U[lane][j] = A.H[(size_t)b * KB * KB + lane * KB + j];
-        __syncwarp();
-        bool badH = false;
-        for (int j = 0; j < kb; ++j) {
-            // column j: D_j on lane j, then L_ij for i > j (U holds L below the
-            // diagonal and D on it while being built)
-            if (lane == j) {
-                double dj = U[j][j];
-                for (int m = 0; m < j; ++m) dj -= U[j][m] * U[j][m] * U[m][m];
-                U[j][j] = dj;
-            }
-            __syncwarp();
-            const double dj = U[j][j];
-            if (lane > j && lane < kb) {
-                double v = U[lane][j];
-                for (int m = 0; m < j; ++m) v -= U[lane][m] * U[j][m] * U[m][m];
-                U[lane][j] = v / dj;
-            }
-            __syncwarp();
-        }
-        if (lane < kb) {
-            const double dd = U[lane][lane];
-            badH = !(dd * sigma_of(A, lane) > 0.0 && fabs(dd) <= DBL_MAX);
-        }
-        __syncwarp();
-        // U = L sqrt|D| (column scaling), iu = 1 / diag(U)
-        if (lane < kb) {
-            const double sd = sqrt(fabs(U[lane][lane]));
-            sh_t[lane] = sd;
-            iu[lane] = 1.0 / sd;
-        }
-        __syncwarp();
-        if (lane < kb)
-            for (int j = 0; j < lane; ++j) U[lane][j] *= sh_t[j];
-        __syncwarp();
-        if (lane < kb) U[lane][lane] = sh_t[lane];
-        __syncwarp();
-        {
-            const unsigned m = __ballot_sync(0xffffffffu, badH);
-            if (m && lane == 0) record_error(sy, kStatusNotPD, r0);
-        }
-        // x = U^{-1} p for this lane's row
-        double x[KB];
+        double p[KB];
         const T *prow = A.P + (size_t)(r0 + lane) * KB;
 #pragma unroll
-        for (int q = 0; q < KB; ++q) x[q] = (q < kb) ? (double)__ldcg(prow + q) : 0.0;
+        for (int q = 0; q < KB; ++q) p[q] = (q < kb) ? (double)__ldcg(prow + q) : 0.0;
+        // row 0: H_b; row lane + 1: this lane's outer product
+        const double *hb = A.H + (size_t)b * KB * KB;
+        for (int e = lane; e < NE; e += 32) {
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            Hs[e] = hb[i * KB + (e - i * (i + 1) / 2)];
+        }
+        double *mine = Hs + (size_t)(lane + 1) * HS;
+#pragma unroll
+        for (int i = 0; i < KB; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) mine[pidx(i, j)] = p[i] * p[j];
+        __syncwarp();
+        for (int e = lane; e < NE; e += 32) {
+            double acc = Hs[e];
+            for (int r = 1; r <= kB; ++r) {
+                acc += Hs[(size_t)r * HS + e];
+                Hs[(size_t)r * HS + e] = acc;
+            }
+        }
+        __syncwarp();
+        // this row's H (the prefix before it): row `lane`
+        double *h = Hs + (size_t)lane * HS;
+        for (int j = 0; j < kb; ++j) {
+            double dj = h[pidx(j, j)];
+            for (int m = 0; m < j; ++m) dj -= h[pidx(j, m)] * h[pidx(j, m)] * h[pidx(m, m)];
+            h[pidx(j, j)] = dj;
+            const double idj = rcp_refined(dj);
+            for (int i = j + 1; i < kb; ++i) {
+                double t = h[pidx(i, j)];
+                for (int m = 0; m < j; ++m) t -= h[pidx(i, m)] * h[pidx(j, m)] * h[pidx(m, m)];
+                h[pidx(i, j)] = t * idj;
+            }
+        }
+        // z = L^{-1} p and the coefficients
+        double z[KB];
+        double Dc = 1.0;
+        bool bad = false;
+        T *cf = A.coef + (size_t)(r0 + lane) * 2 * KB;
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
             if (q < kb) {
-                double s = x[q];
+                double zq = p[q];
 #pragma unroll
-                for (int m = 0; m < q; ++m) s -= U[q][m] * x[m];
-                x[q] = s * iu[q];
-            }
-        }
-        double tq[KB];
-#pragma unroll
-        for (int q = 0; q < KB; ++q) tq[q] = (q < kb) ? sh_t[q] : 1.0;
-        for (int r = 0; r < rows; ++r) {
-            if (lane == r) {
-                double Dp = 1.0;
-                bool bad = false;
-                T *cf = A.coef + (size_t)(r0 + r) * 2 * KB;
-#pragma unroll
-                for (int q = 0; q < KB; ++q) {
-                    if (q < kb) {
-                        const double sg = sigma_of(A, q), y = x[q];
-                        const double Dq = fma(sg * y, y, Dp);
-                        bad = bad || !(Dq > 0.0 && Dq <= DBL_MAX);
-                        const double rs = rsqrt_refined(Dp * Dq);   // 1 / sqrt(D_{q-1} D_q)
-                        sh_y[q] = sg * y;
-                        sh_al[q] = Dp * rs;                       // sqrt(D_{q-1} / D_q)
-                        sh_be[q] = y * rs;
-                        cf[2 * q] = (T)(sg * y * tq[q]);
-                        cf[2 * q + 1] = (T)(y * rcp_refined(Dq * tq[q]));
-                        Dp = Dq;
-                    } else {
-                        sh_y[q] = 0.0;
-                        sh_al[q] = 1.0;
-                        sh_be[q] = 0.0;
-                        cf[2 * q] = T(0);
-                        cf[2 * q + 1] = T(0);
-                    }
+                for (int m = 0; m < q; ++m) zq -= h[pidx(q, m)] * z[m];
+                z[q] = zq;
+                const double sg = sigma_of(A, q);
+                const double ad = sg * h[pidx(q, q)];  // |D_q|
+                bad = bad || !(ad > 0.0 && ad <= DBL_MAX);
+                Dc = fma(sg * zq, zq * rcp_refined(ad), Dc);
+                bad = bad || !(Dc > 0.0 && Dc <= DBL_MAX);
+                if (lane < rows) {
+                    cf[2 * q] = (T)(sg * zq);
+                    cf[2 * q + 1] = (T)(zq * rcp_refined(ad * Dc));
                 }
-                const double rD = rsqrt_refined(Dp);
-                A.escale[r0 + r] = (T)rD;
-                A.dfac[r0 + r] = Dp * rD;
-                if (bad) record_error(sy, kStatusNotPD, r0 + r);
-            }
-            __syncwarp();
-            // every lane: the carry scales; later rows: their vectors
-#pragma unroll
-            for (int q = 0; q < KB; ++q) tq[q] /= sh_al[q] > 0.0 ? sh_al[q] : 1.0;
-            if (lane > r) {
-                double acc = 0.0;
-#pragma unroll
-                for (int q = 0; q < KB; ++q) {
-                    if (q < kb) {
-                        const double xq = x[q];
-                        x[q] = sh_al[q] * xq - sh_be[q] * acc;
-                        acc = fma(sh_y[q], xq, acc);
-                    }
+            } else {
+                z[q] = 0.0;
+                if (lane < rows) {
+                    cf[2 * q] = T(0);
+                    cf[2 * q + 1] = T(0);
                 }
             }
-            __syncwarp();
         }
+        const double rD = rsqrt_refined(Dc);
+        if (lane < rows) {
+            A.escale[r0 + lane] = (T)rD;
+            A.dfac[r0 + lane] = Dc * rD;
+            if (bad) record_error(sy, kStatusNotPD, r0 + lane);
+        }
+        __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------- sweep
 
 // Column block b, rows 0 .. b of the pass's Apply: lane = column, kb carries
-// in registers, tiles and their rows' coefficients staged in a ring of
-// three slots (cp.async) so that two tiles are in flight while one is used.
+// in registers, the column's 32 entries of a tile in registers during the
+// recurrence; tiles and their rows' coefficients staged in a ring of NSLOT
+// slots (cp.async), so that NSLOT - 1 tiles are in flight while one is used.
 template <typename T, int KB>
 struct SweepSlot {
-    T tile[kB][kPad];     // [column][row]
-    T cf[kB][2 * KB];     // (a, b) per row
+    T tile[kB * Stride<T>::value];  // [column][row]
+    T cf[kB * 2 * KB];              // (a, b) per row
     T e[kB];
     double df[kB];
 };
+template <typename T, int KB>
+struct SweepCfg {
+    static constexpr int WARPS = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int fit = (int)((224u * 1024u / WARPS) / sizeof(SweepSlot<T, KB>));
+    static constexpr int NSLOT = fit > 6 ? 6 : (fit < 2 ? 2 : fit);
+    static constexpr size_t smem = (size_t)WARPS * NSLOT * sizeof(SweepSlot<T, KB>);
+};
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(128) sweep_kernel(Args<T> A, int warps_per_block)
+__global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args<T> A)
 {
+    using C = SweepCfg<T, KB>;
+    constexpr int SD = Stride<T>::value;
+    constexpr int E = 16 / (int)sizeof(T);
+    using V = typename Vec16<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * 3;
+    SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * C::NSLOT;
     const long long n = A.n, ld = A.ld;
     const int nb = A.nb;
-    (void)warps_per_block;
+    const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = atomicAdd(A.ctl + kCtlSweepTicket, 1);
@@ -658,54 +954,84 @@ __global__ void __launch_bounds__(128) sweep_kernel(Args<T> A, int warps_per_blo
 #pragma unroll
         for (int q = 0; q < KB; ++q) uh[q] = (active && q < A.kb) ? A.V[c0 + lane + q * A.ldv] : T(0);
         auto fetch = [&](int r) {
-            SweepSlot<T, KB> &s = slot[r % 3];
+            SweepSlot<T, KB> &sl = slot[r % C::NSLOT];
             const long long r0 = (long long)r * kB;
-            const bool diag = r == b;
-#pragma unroll 8
-            for (int i = 0; i < kB; ++i) {
-                // the diagonal tile needs rows <= column only
-                if (c0 + i < n && (!diag || lane <= i)) cp_elem(&s.tile[i][lane], A.L + (r0 + lane) + (c0 + i) * ld);
+            if (r < b) {
+                stage_tile(sl.tile, A.L, ld, r0, c0, n, kB, vec, lane);
+            } else {
+                // the diagonal tile: rows <= column only
+                for (int col = 0; col < kB; ++col)
+                    if (c0 + col < n && lane <= col) cp_elem(&sl.tile[col * SD + lane], A.L + (r0 + lane) + (c0 + col) * ld);
             }
             const T *cf = A.coef + (size_t)r0 * 2 * KB;
-            for (int x = lane; x < kB * 2 * KB; x += 32) cp_elem(&s.cf[0][0] + x, cf + x);
-            cp_elem(&s.e[lane], A.escale + r0 + lane);
-            if (diag) cp_elem(&s.df[lane], A.dfac + r0 + lane);
-            cp_commit();
+            for (int c = lane; c < kB * 2 * KB / E; c += 32) cp16(sl.cf + c * E, cf + c * E);
+            for (int c = lane; c < kB / E; c += 32) cp16(sl.e + c * E, A.escale + r0 + c * E);
+            if (r == b && lane < kB / 2) cp16(sl.df + 2 * lane, A.dfac + r0 + 2 * lane);
         };
-        fetch(0);
-        if (b >= 1) fetch(1);
+        for (int r = 0; r < C::NSLOT - 1; ++r) {
+            if (r <= b) fetch(r);
+            cp_commit();
+        }
         for (int r = 0; r <= b; ++r) {
-            if (r + 2 <= b) fetch(r + 2);
-            if (r + 2 <= b) cp_wait<2>();
-            else if (r + 1 <= b) cp_wait<1>();
-            else cp_wait<0>();
+            if (r + C::NSLOT - 1 <= b) fetch(r + C::NSLOT - 1);
+            cp_commit();
+            cp_wait<C::NSLOT - 1>();
             __syncwarp();
-            SweepSlot<T, KB> &s = slot[r % 3];
+            SweepSlot<T, KB> &sl = slot[r % C::NSLOT];
             const bool diag = r == b;
             const long long r0 = (long long)r * kB;
             const int rows = diag ? lane : (int)min((long long)kB, n - r0);
-            T *col = s.tile[lane];
+            T v[kB];
+            V *colv = reinterpret_cast<V *>(sl.tile + lane * SD);
+#pragma unroll
+            for (int c = 0; c < kB / E; ++c) {
+                const V x = colv[c];
+#pragma unroll
+                for (int u = 0; u < E; ++u) v[c * E + u] = vget<T>(x, u);
+            }
             if (active) {
-#pragma unroll 4
+#pragma unroll
                 for (int i = 0; i < kB; ++i) {
                     if (i < rows) {
-                        T v = col[i];
+                        T x = v[i];
 #pragma unroll
                         for (int q = 0; q < KB; ++q) {
-                            v = fma(s.cf[i][2 * q], uh[q], v);
-                            uh[q] = fma(-s.cf[i][2 * q + 1], v, uh[q]);
+                            x = fma(sl.cf[i * 2 * KB + 2 * q], uh[q], x);
+                            uh[q] = fma(-sl.cf[i * 2 * KB + 2 * q + 1], x, uh[q]);
                         }
-                        col[i] = v * s.e[i];
+                        v[i] = x * sl.e[i];
+                    } else if (diag && i == lane) {
+                        v[i] = (T)((double)v[i] * sl.df[i]);
                     }
                 }
-                if (diag) col[lane] = (T)((double)col[lane] * s.df[lane]);
+            }
+            T *col = sl.tile + lane * SD;
+#pragma unroll
+            for (int c = 0; c < kB / E; ++c) {
+                V x;
+                T *xp = reinterpret_cast<T *>(&x);
+#pragma unroll
+                for (int u = 0; u < E; ++u) xp[u] = v[c * E + u];
+                reinterpret_cast<V *>(col)[c] = x;
             }
             __syncwarp();
+            if (!diag && vec) {
+                constexpr int CPC = kB / E;
+                for (int c = lane; c < kB * CPC; c += 32) {
+                    const int cc = c / CPC, ch = c % CPC;
+                    if (c0 + cc < n)
+                        *reinterpret_cast<V *>(A.L + (r0 + ch * E) + (c0 + cc) * ld) =
+                            *reinterpret_cast<const V *>(sl.tile + cc * SD + ch * E);
+                }
+            } else {
 #pragma unroll 8
-            for (int i = 0; i < kB; ++i)
-                if (c0 + i < n && (!diag || lane <= i)) A.L[(r0 + lane) + (c0 + i) * ld] = s.tile[i][lane];
+                for (int cc = 0; cc < kB; ++cc)
+                    if (c0 + cc < n && (!diag || lane <= cc) && (diag || lane < rows))
+                        A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
+            }
             __syncwarp();
         }
+        cp_wait<0>();
     }
 }
 

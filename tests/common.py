@@ -13,6 +13,32 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 #   |g_ij - o_ij| <= TOL_F64 * max(|o_ij|, max_r |o_rj|)
 TOL_F64 = 1e-11
 
+# Mixed precision (float storage and Apply, double Compute).  The GPU path
+# and the oracle's emulation evaluate the same rotations in float with
+# different operation orders, so they agree to float rounding, not bit for
+# bit.  Bound used, column-scaled: an entry in row i is the end of a chain
+# of at most m = (i + 1) k rotations; each adds at most 4 float roundings
+# (the two products and sums of Apply, and the coefficient's own rounding),
+# relative u = 2^-24 each; treating them as independent (the standard
+# first-order model of rounding, under which such errors grow as sqrt(m) u)
+# each evaluation is within 4 sqrt(m) u of the exact result, and the two
+# within 8 sqrt(m) u of each other.
+U_F32 = 2.0 ** -24
+
+
+def tol_mixed(rows, k):
+    """Column-scaled bound on |GPU - emulation| for a float modification of
+    `rows` rows by k vectors (see above)."""
+    return 8.0 * U_F32 * math.sqrt(max(1, rows) * max(1, k))
+
+
+def accuracy_as_serial(e_gpu, e_serial):
+    """The paper's accuracy claim (Sec. 5: the GPU's error and the serial
+    CPU code's are always very similar), as a test: the GPU path's error
+    against the float64 oracle is at most twice that of the serial algorithm
+    in the same precision split, plus four float ulps."""
+    return e_gpu <= 2.0 * e_serial + 4.0 * U_F32
+
 
 def colscaled_err(got_cm, ref_cm, n=None, chunk=2048):
     """Max over the upper triangle of |got - ref| / max(|ref_ij|, max_r |ref_rj|).

@@ -9,14 +9,17 @@ them.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from oracle.bruteforce import modified_factor_decimal
-from oracle.hyperbolic_np import NotPositiveDefinite, modify_b_np
+from oracle.hyperbolic_np import NotPositiveDefinite, modify_b_np, modify_mixed32_np
 from paper_1011_1173_gb300 import inputs
+from oracle import from_cm, to_cm
 from tests.common import (colscaled_err, cm_from_upper, load_hand_examples, modified_matrix,
                           upper_from_cm)
 
@@ -282,10 +285,16 @@ def test_mixed32_zero_update_and_closed_forms():
     out = Lf.copy()
     st, info = oracle.modify_mixed32(out, np.zeros((2, 20), np.float32), 1)
     assert st == 0 and np.array_equal(out, Lf)
-    # n = 1: each step rounds the new diagonal to float
+    # n = 1: the diagonal is carried in double across the group and rounded
+    # once (sqrt(9 + 16 - 4 + 1) = sqrt(22)); in groups of one vector it is
+    # rounded after each step
     out = np.array([[3.0]], np.float32)
     st, info = oracle.modify_mixed32(out, np.array([[4.0], [2.0], [1.0]], np.float32),
                                      [1, -1, 1])
+    assert st == 0 and out[0, 0] == np.float32(np.sqrt(22.0))
+    out = np.array([[3.0]], np.float32)
+    st, info = oracle.modify_mixed32(out, np.array([[4.0], [2.0], [1.0]], np.float32),
+                                     [1, -1, 1], group=1)
     ref = np.float32(3.0)
     for v, s in ((4.0, 1), (2.0, -1), (1.0, 1)):
         ref = np.float32(np.sqrt(np.float64(ref) ** 2 + s * v * v))
@@ -420,3 +429,100 @@ def test_solve_errors_and_padding():
     Bp[:, :10] = np.random.default_rng(1).standard_normal((2, 10))
     st, _ = oracle.solve(L, Bp, n=10)
     assert st == 0 and np.all(Bp[:, 10:] == 9.0)
+
+
+# ---------------------------------------------------------------- mixed precision: the reading
+
+def load_mixed_examples():
+    import json
+    from fractions import Fraction
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mixed_examples.json")) as f:
+        data = json.load(f)
+
+    def ev(x):
+        num, _, den = x.partition("/")
+        val = Fraction(eval(num, {"__builtins__": {}}))
+        if den:
+            val /= Fraction(eval(den, {"__builtins__": {}}))
+        return np.float32(float(val))
+
+    return [dict(c, L=np.array([[ev(x) for x in r] for r in c["L"]], np.float32),
+                 V=np.array([[ev(x) for x in r] for r in c["V"]], np.float32),
+                 expected=np.array([[ev(x) for x in r] for r in c["expected"]], np.float32))
+            for c in data["cases"]]
+
+
+MIXED_CASES = load_mixed_examples()
+
+
+@pytest.mark.parametrize("case", MIXED_CASES, ids=[c["name"] for c in MIXED_CASES])
+def test_mixed32_hand_derived_bits(case):
+    """The emulation (C and its numpy restatement) reproduces the hand-derived
+    float32 results bit for bit."""
+    out = to_cm(case["L"])
+    st, _ = oracle.modify_mixed32(out, np.ascontiguousarray(case["V"].T), case["sigma"], group=case["group"])
+    assert st == 0
+    assert np.array_equal(from_cm(out), case["expected"])
+    got = modify_mixed32_np(case["L"], case["V"], case["sigma"], group=case["group"])
+    assert np.array_equal(np.triu(got), case["expected"])
+
+
+@pytest.mark.parametrize("mutant", ["cs_unrounded", "diag_per_vector", "apply_in_double"])
+def test_mixed32_pins_reject_planted_mistakes(mutant):
+    """Each planted deviation from the reading changes some hand-derived bits."""
+    changed = False
+    for case in MIXED_CASES:
+        bad = modify_mixed32_np(case["L"], case["V"], case["sigma"], group=case["group"], mutant=mutant)
+        changed = changed or not np.array_equal(np.triu(bad), case["expected"])
+    assert changed, mutant
+
+
+@pytest.mark.parametrize("n,k,group", [(7, 3, None), (40, 5, 2), (33, 4, 1), (65, 6, 4)])
+def test_mixed32_c_equals_numpy_restatement(n, k, group):
+    rng = np.random.default_rng(n * 3 + k)
+    B = rng.standard_normal((n, n))
+    U = np.linalg.cholesky(B.T @ B / n + np.eye(n)).T.astype(np.float32)
+    V = (rng.standard_normal((n, k)) / np.sqrt(n)).astype(np.float32)
+    sig = np.where(rng.random(k) < 0.5, 1, -1).astype(np.int8)
+    sig[0] = 1
+    V[:, sig < 0] *= np.float32(0.3)
+    out = to_cm(U)
+    st, _ = oracle.modify_mixed32(out, np.ascontiguousarray(V.T), sig, group=group)
+    assert st == 0
+    assert np.array_equal(from_cm(out), np.triu(modify_mixed32_np(U, V, sig, group=group)))
+
+
+def test_mixed32_groups_change_only_diagonal_rounding():
+    """Groups of the same vectors differ by float rounding only, and a single
+    vector per group gives the same result for any group size."""
+    rng = np.random.default_rng(3)
+    n, k = 50, 6
+    B = rng.standard_normal((n, n))
+    U = np.linalg.cholesky(B.T @ B / n + np.eye(n)).T.astype(np.float32)
+    V = (rng.standard_normal((n, k)) / np.sqrt(n)).astype(np.float32)
+    outs = []
+    for g in (1, 2, 6):
+        out = to_cm(U)
+        assert oracle.modify_mixed32(out, np.ascontiguousarray(V.T), 1, group=g)[0] == 0
+        outs.append(out)
+    assert colscaled_err(outs[0], outs[2]) < 1e-5
+    one = to_cm(U)
+    two = to_cm(U)
+    oracle.modify_mixed32(one, np.ascontiguousarray(V[:, :1].T), 1, group=1)
+    oracle.modify_mixed32(two, np.ascontiguousarray(V[:, :1].T), 1, group=16)
+    assert np.array_equal(one, two)
+
+
+def test_mixed32_first_failing_row_across_groups():
+    """A later group's failure above an earlier group's is the one reported
+    (the smallest failing row, as CholeskyModifyB over all vectors)."""
+    n = 20
+    V = np.zeros((2, n), np.float32)
+    V[0, 15] = 2.0   # group 1 fails at row 15
+    V[1, 4] = 2.0    # group 2 fails at row 4
+    out = np.eye(n, dtype=np.float32)
+    st, info = oracle.modify_mixed32(out, V, -1, group=1)
+    assert st == oracle.ERR_NOT_PD and info == 4
+    o64 = np.eye(n)
+    st, info = oracle.modify_b(o64, V.astype(np.float64), -1)
+    assert st == oracle.ERR_NOT_PD and info == 4

@@ -16,9 +16,7 @@ import pytest
 import torch
 
 from paper_1011_1173_gb300 import chm, inputs
-from tests.common import TOL_F64, colscaled_err
-
-TOL_MIXED = 1e-4
+from tests.common import TOL_F64, colscaled_err, tol_mixed
 
 
 def _call(fn, L, V, sigma, d_info=None):
@@ -63,7 +61,7 @@ def test_noalloc_matches_allocating_path_twice(n, k, dtype):
     L0 = inputs.spd_factor(n, seed, ld=n + 3).to("cuda", dtype)
     V = inputs.update_block(n, k, seed, scale=0.5 / np.sqrt(n * k)).to("cuda", dtype)
     sig = inputs.sigma_vector(k, seed).tolist()
-    tol = TOL_F64 if dtype == torch.float64 else TOL_MIXED
+    tol = TOL_F64 if dtype == torch.float64 else tol_mixed(n, k)
     ref = L0.clone()
     got = L0.clone()
     info = torch.full((2,), 99, dtype=torch.int64, device="cuda")
