@@ -34,9 +34,15 @@
  *     pointers.
  *   - Precision.  CHM_F64: L and V are double; all arithmetic in double.
  *     CHM_F32_MIXED: L and V are float; the Apply sweep runs in float while
- *     every Compute step (the square root and the c, s ratios) runs in
- *     double on the promoted float values, the new diagonal being rounded to
- *     float after each vector.
+ *     every Compute step runs in double on the promoted float values.  The
+ *     vectors are taken in groups (those of one launch of the wave kernel,
+ *     or one pass of the pass kernels): within a group each diagonal entry
+ *     is carried in double from vector to vector and rounded to float once,
+ *     after the group's last vector; the ratios that enter Apply (c and s,
+ *     or the pass kernels' sweep coefficients) are rounded to float.  The
+ *     result differs from that of the serial Algorithm 1 in the same split
+ *     by float rounding only: its column-scaled error is bounded by
+ *     8 u_f sqrt(n k) with u_f = 2^-24.
  *   - Streams.  Work is enqueued on `stream` (a cudaStream_t; NULL means the
  *     legacy default stream of the current device) and the call returns
  *     without synchronising.  L is modified in place in stream order.
@@ -309,7 +315,10 @@ int chm_solve(const void *L, int64_t n, int64_t ld, void *B, int64_t ldb, int64_
 /*
  * Device memory that chm_update / chm_downdate / chm_modify_ex hold for one
  * factor of order n modified by k vectors (the per-stream workspace; the
- * factor and V themselves are the caller's).  It grows as O(n min(k, 64)):
+ * factor and V themselves are the caller's), for the path the "path"
+ * setting forces, or under the automatic rule the larger of the two paths'
+ * (the wave kernel's grows as O(n min(k, 64)), the pass kernels' as O(n)).
+ * Either way it is O(n min(k, 64)):
  * with L in page-locked host memory this is all the device memory a
  * modification needs (abstract, Sec. 5: O(n) device memory).  Host only.
  *   bytes  receives the size
@@ -370,9 +379,9 @@ int chm_microbench(int which, double *out, int nout);
  *   "path"     0 automatic (default), 1 the wave kernel, 2 the pass kernels
  *   "pass_kb"  update vectors per pass of the pass kernels, 1..16 (0: 16)
  *   "pass_d"   lookahead of the pass kernels' forward-substitution chain in
- *              row blocks, clamped to 2..12 (float) or 2..5 (double) and
+ *              row blocks, clamped to 2..10 (float) or 2..6 (double) and
  *              further by what the chain block's shared memory holds for
- *              the pass's vectors; 0 is the default per type (6 float,
+ *              the pass's vectors; 0 is the default per type (10 float,
  *              4 double)
  * The two paths compute the same factor by the same method (Algorithm 1's
  * rotations, restated exactly) with different work splits:
@@ -385,7 +394,10 @@ int chm_microbench(int which, double *out, int nout);
  *         in double), and one sweep that reads and writes each tile of the
  *         factor once for the whole block of vectors.
  * The automatic rule takes the pass kernels when the factor's upper
- * triangle is at least 32 MB (float) or 256 MB with k <= 2 (double).
+ * triangle is at least 32 MB (float) or 256 MB with k <= 2 (double), and
+ * for every factor of order >= 64 in page-locked host memory (it then
+ * crosses the CPU-GPU link three times per pass of up to 16 vectors; the
+ * wave kernel re-reads it once per vector).
  * chm_config_get also answers "pass_d_f32" and "pass_d_f64" (the values in
  * effect).  Host only.  Returns CHM_OK or CHM_ERR_ARG (unknown key or value
  * out of range).

@@ -102,8 +102,13 @@ struct PassSpace {
 size_t pass_workspace_bytes(long long n, int dtype);
 size_t pass_flag_bytes(long long n, int dtype);
 // True if a single-factor modification of this shape runs on the pass
-// kernels (the library setting "path", else the size rule).
-bool use_pass_path(long long n, long long k, int dtype);
+// kernels (the library setting "path", else the size rule; a factor in
+// page-locked host memory takes the pass kernels, which cross the CPU-GPU
+// link three times per pass instead of once per vector).
+bool use_pass_path(long long n, long long k, int dtype, bool host_factor);
+bool is_host_memory(const void *p);
+// The "path" setting in effect (0 automatic, 1 wave kernel, 2 pass kernels).
+int path_setting();
 // Runs fn on the stream's status word and pass workspace, grown first to
 // at least `bytes`, under the workspaces' lock.
 int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtype,

@@ -206,6 +206,16 @@ static int ctl_init(int *ctl, long long *status)
     return CHM_OK;
 }
 
+bool is_host_memory(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 int check_reachable(const void *p)
 {
     int dev = 0;
@@ -428,7 +438,7 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
     if (rc != CHM_OK) return rc;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
     if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;
-    if (use_pass_path(n, k, dtype)) {
+    if (use_pass_path(n, k, dtype, is_host_memory(L))) {
         return with_pass_workspace(stream, pass_workspace_bytes(n, dtype), n, dtype,
                                    [&](const Scratch &sc, PassSpace &ps) {
                                        return pass_enqueue(L, n, ld, V, ldv, k, sigma, sign, dtype, stream,
@@ -610,10 +620,14 @@ int chm_workspace_bytes(int64_t n, int64_t k, int dtype, size_t *bytes)
 {
     if (!bytes || n < 0 || k < 0 || n > (1ll << 26)) return CHM_ERR_ARG;
     if (dtype != CHM_F64 && dtype != CHM_F32_MIXED) return CHM_ERR_ARG;
-    if (n > 0 && k > 0 && chm::use_pass_path(n, k, dtype))
-        *bytes = chm::kCtlInts * sizeof(int) + 2 * sizeof(long long) + chm::pass_workspace_bytes(n, dtype);
-    else
-        *bytes = chm::single_workspace_bytes(n, k);
+    const size_t wave = chm::single_workspace_bytes(n, k);
+    const size_t pass = (n > 0 && k > 0)
+                            ? chm::kCtlInts * sizeof(int) + 2 * sizeof(long long) + chm::pass_workspace_bytes(n, dtype)
+                            : 0;
+    // a forced path holds its own workspace; the automatic rule may take
+    // either (a factor in host memory takes the pass kernels), so the larger
+    const int path = chm::path_setting();
+    *bytes = path == 1 ? wave : path == 2 ? pass : std::max(wave, pass);
     return CHM_OK;
 }
 

@@ -39,17 +39,24 @@ static int pass_d(int dtype)
 {
     int v = g_pass_d.load();
     if (v <= 0) v = env_or("CHM_PASS_D", 0);
-    if (v <= 0) v = dtype == CHM_F64 ? 4 : 6;
+    if (v <= 0) v = dtype == CHM_F64 ? 4 : 10;
     // each instantiation clamps it further to what its shared memory holds
-    return std::max(2, std::min(dtype == CHM_F64 ? 5 : 12, v));
+    return std::max(2, std::min(dtype == CHM_F64 ? 6 : 10, v));
 }
 
-bool use_pass_path(long long n, long long k, int dtype)
+int path_setting()
 {
     int p = g_path.load();
     if (p == 0) p = env_or("CHM_PATH", 0);
+    return p == 1 || p == 2 ? p : 0;
+}
+
+bool use_pass_path(long long n, long long k, int dtype, bool host_factor)
+{
+    const int p = path_setting();
     if (p == 1) return false;
     if (p == 2) return true;
+    if (host_factor) return n >= 64;
     // automatic: the pass path once the factor is larger than about a
     // third of L2 (where the wave kernel's waves start to re-stream it); in
     // float64 only for few vectors, where the wave kernel's chain, not the
@@ -64,7 +71,7 @@ bool use_pass_path(long long n, long long k, int dtype)
 namespace {
 
 struct PassLayout {
-    size_t P, Ptag, Ztag, Dinv, G, gram, H, coef, escale, dfac, ctl, bytes;
+    size_t P, pflag, Ztag, Dinv, G, gram, H, coef, escale, dfac, ctl, bytes;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -79,12 +86,12 @@ PassLayout pass_layout(long long n, int elt)
     // the tagged words and control words first: they are zeroed on
     // allocation (tag 0 matches no pass, whose epochs start at 1)
     const size_t words = elt / 4;
-    l.Ptag = x; x = al(x + rows * KB * words * 8);
+    l.pflag = x; x = al(x + nb * 4);
     l.Ztag = x; x = al(x + rows * KB * words * 8);
     l.ctl = x; x = al(x + pass::kCtlInts * 4);
     l.P = x; x = al(x + rows * KB * elt);
     l.Dinv = x; x = al(x + nb * 1024 * elt);
-    l.G = x; x = al(x + nb * 1024 * elt);
+    l.G = x; x = al(x + (size_t)pass::kMaxCrit * nb * 1024 * elt);
     l.gram = x; x = al(x + nb * KB * KB * 8);
     l.H = x; x = al(x + nb * KB * KB * 8);
     l.coef = x; x = al(x + rows * 2 * KB * elt);
@@ -169,6 +176,7 @@ int launch_pass(pass::Args<T> A, cudaStream_t s)
     if ((rc = pass_setup<T, KB>(dev, &bps)) != CHM_OK) return rc;
     const int nb = A.nb;
     A.d = std::min(A.d, pass::ChainCfg<T, KB>::DMAX);
+    A.c = std::min(A.d, pass::ChainCfg<T, KB>::CMAX);
     if (cudaMemsetAsync(A.ctl, 0, pass::kCtlInts * sizeof(int), s) != cudaSuccess) return CHM_ERR_CUDA;
     pass::prep_kernel<T><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::trsm_kernel<T, KB><<<nsm, pass::kTrsmWarps * 32, trsm_smem<T, KB>(), s>>>(A);
@@ -206,7 +214,7 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.nb = (int)((n + pass::kB - 1) / pass::kB);
     A.d = pass_d(dtype);
     A.P = reinterpret_cast<T *>(w + lay.P);
-    A.Ptag = reinterpret_cast<long long *>(w + lay.Ptag);
+    A.pflag = reinterpret_cast<int *>(w + lay.pflag);
     A.Ztag = reinterpret_cast<long long *>(w + lay.Ztag);
     A.Dinv = reinterpret_cast<T *>(w + lay.Dinv);
     A.G = reinterpret_cast<T *>(w + lay.G);
@@ -229,7 +237,7 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
             if ((sigma ? sigma[q0 + q] : sign) < 0) mask |= 1ull << q;
         A.down_mask = mask;
         A.epoch = ++ps.epoch;
-        A.trace = trace_buffer((size_t)A.nb * 8, stream);  // the last pass's, with CHM_TRACE=1
+        A.trace = trace_buffer((size_t)A.nb * 16, stream);  // the last pass's, with CHM_TRACE=1
         const int rc = launch_pass_kb<T>(A, stream);
         if (rc != CHM_OK) return rc;
     }
@@ -290,7 +298,7 @@ int chm_config_get(const char *key, int64_t *value)
 int chm_path_for(int64_t n, int64_t k, int dtype, int *path)
 {
     if (!path || n < 0 || k < 0 || (dtype != CHM_F64 && dtype != CHM_F32_MIXED)) return CHM_ERR_ARG;
-    *path = chm::use_pass_path(n, k, dtype) ? 2 : 1;
+    *path = chm::use_pass_path(n, k, dtype, false) ? 2 : 1;
     return CHM_OK;
 }
 

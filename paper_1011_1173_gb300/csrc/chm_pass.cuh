@@ -59,26 +59,28 @@ struct Args {
     int nb;                         // row blocks
     int kb;                         // vectors of this pass (<= KB of the kernels)
     int d;                          // lookahead of the substitution chain (near tiles)
+    int c;                          // offsets the chain's critical warp takes (G^(1..c))
     int epoch;                      // tags this pass's flags
     unsigned long long down_mask;   // bit q: vector q is a downdate
     // workspace
     T *P;            // [nb * 32][KB]: F^T P = V, rows past n zero
     T *Dinv;         // [nb][32][32]: (D_b^T)^{-1}, D_b the diagonal block, row-major
-    T *G;            // [nb][32][32]: Dinv_b F_{b-1,b}^T, row-major
+    T *G;            // [c][nb][32][32]: G^(j)_b = Dinv_b F_{b-j,b}^T, row-major
     double *gram;    // [nb][KB][KB]: sum over the block's rows of p p^T
     double *H;       // [nb][KB][KB]: Sigma + sum over earlier blocks
     T *coef;         // [nb * 32][2 KB]: (a_q, b_q) of each row
     T *escale;       // [nb * 32]: 1 / sqrt(D_kb) of each row
     double *dfac;    // [nb * 32]: sqrt(D_kb) of each row
-    long long *Ptag; // [nb * 32][KB][words of T]: P as epoch-tagged words
+    int *pflag;      // [nb]: P of the block published (== epoch), with release
     long long *Ztag; // [nb][32][KB][words of T]: Zf as epoch-tagged words
     int *ctl;        // kCtlInts control words
     long long *status;     // sticky {status, row} of the stream
     long long *user_info;  // optional {status, row} of the call
     long long timeout_ns;
-    long long *trace;      // optional [nb][8] %globaltimer stamps of the substitution:
-                           // P posted, Zhat posted, far sum staged, stage loaded,
-                           // P published; a worker's last P seen, its far sum published
+    long long *trace;      // optional [nb][16] %globaltimer stamps of the substitution:
+                           // 0 P posted, 1 W posted, 2 far sum staged, 4 P published,
+                           // 5 first near warp done, 6 W warp's inputs in, 7 critical
+                           // warp's inputs in, 8 a worker's last P seen, 9 its far sum out
 };
 
 template <typename T>
@@ -117,7 +119,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // ---------------------------------------------------------------- prep
 
 // Per diagonal block b (one warp): Dinv_b = (D_b^T)^{-1} and
-// G_b = Dinv_b F_{b-1,b}^T from the factor as it enters the pass, and the
+// G^(j)_b = Dinv_b F_{b-j,b}^T, j = 1 .. c, from the factor as it enters the pass, and the
 // check that its diagonal is positive and finite (Algorithm 1's Compute
 // needs L_ii > 0).  Rows and columns past n are the identity.
 template <typename T>
@@ -163,18 +165,20 @@ __global__ void __launch_bounds__(32) prep_kernel(Args<T> A)
             dg[i * kB + lane] = x[i];
         }
         __syncwarp();
-        if (b > 0) {
-            // the tile above the diagonal block: rows of block b - 1 (all < n), columns of block b
+        for (int j = 1; j <= A.c && j <= b; ++j) {
+            // the tile j blocks above the diagonal block: rows of block b - j (all < n), columns of block b
+            const long long rj = c0 - (long long)j * kB;
 #pragma unroll 4
-            for (int l = 0; l < kB; ++l) Ft[l][lane] = (l < rows) ? A.L[(c0 - kB + lane) + (c0 + l) * ld] : T(0);
+            for (int l = 0; l < kB; ++l) Ft[l][lane] = (l < rows) ? A.L[(rj + lane) + (c0 + l) * ld] : T(0);
             __syncwarp();
-            T *gg = A.G + (size_t)b * kB * kB;
+            T *gg = A.G + ((size_t)(j - 1) * A.nb + b) * kB * kB;
 #pragma unroll 4
             for (int i = 0; i < kB; ++i) {
                 T g = T(0);
                 for (int l = 0; l <= i; ++l) g = fma(Di[i][l], Ft[l][lane], g);
                 gg[i * kB + lane] = g;
             }
+            __syncwarp();
         }
         __syncwarp();
     }
@@ -269,16 +273,71 @@ __device__ __forceinline__ void stage_dense(T *dst, const T *src, int lane)
     }
 }
 
-// Lane i: out[q] = sum_l M[i][l] x[l][q] (M staged with Stride, x [32][KB]).
+// A [32][KB] array of per-row vectors in shared memory: row stride KS so
+// that 32 lanes each reading or writing their own row in 16-byte pieces hit
+// distinct banks (an odd number of 16-byte units per row), and rows of
+// fewer than 16 bytes stay contiguous.
 template <typename T, int KB>
-__device__ __forceinline__ void lane_mv(const T *M, const T *x, T (&out)[KB], int i)
+struct Rows {
+    static constexpr int bytes = KB * (int)sizeof(T);
+    static constexpr int E = 16 / (int)sizeof(T);
+    static constexpr int KS = bytes < 16 ? KB : (((bytes / 16) & 1) ? KB : KB + E);
+    static constexpr int size = kB * KS;
+};
+template <typename T, int KB>
+__device__ __forceinline__ void row_store(T *base, int lane, const T (&v)[KB])
+{
+    using R = Rows<T, KB>;
+    T *p = base + lane * R::KS;
+    if (R::bytes % 16 == 0) {
+        using V = typename Vec16<T>::type;
+#pragma unroll
+        for (int g = 0; g < KB / R::E; ++g) {
+            V x;
+            T *xp = reinterpret_cast<T *>(&x);
+#pragma unroll
+            for (int u = 0; u < R::E; ++u) xp[u] = v[g * R::E + u];
+            reinterpret_cast<V *>(p)[g] = x;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < KB; ++q) p[q] = v[q];
+    }
+}
+template <typename T, int KB>
+__device__ __forceinline__ void row_load(const T *base, int lane, T (&v)[KB])
+{
+    using R = Rows<T, KB>;
+    const T *p = base + lane * R::KS;
+    if (R::bytes % 16 == 0) {
+        using V = typename Vec16<T>::type;
+#pragma unroll
+        for (int g = 0; g < KB / R::E; ++g) {
+            const V x = reinterpret_cast<const V *>(p)[g];
+            const T *xp = reinterpret_cast<const T *>(&x);
+#pragma unroll
+            for (int u = 0; u < R::E; ++u) v[g * R::E + u] = xp[u];
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < KB; ++q) v[q] = p[q];
+    }
+}
+
+// Lane i: out[q] (+)= sum_l M[i][l] x[l][q] (M staged with Stride, x a Rows array).
+template <typename T, int KB>
+__device__ __forceinline__ void lane_mv(const T *M, const T *x, T (&out)[KB], int i, bool acc = false)
 {
     constexpr int S = Stride<T>::value;
     constexpr int E = Vec16<T>::n;
+    constexpr int XS = Rows<T, KB>::KS;
     using V = typename Vec16<T>::type;
     T a0[KB], a1[KB];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) a0[q] = a1[q] = T(0);
+    for (int q = 0; q < KB; ++q) {
+        a0[q] = acc ? out[q] : T(0);
+        a1[q] = T(0);
+    }
     const V *row = reinterpret_cast<const V *>(M + i * S);
 #pragma unroll
     for (int c = 0; c < kB / E; ++c) {
@@ -289,7 +348,7 @@ __device__ __forceinline__ void lane_mv(const T *M, const T *x, T (&out)[KB], in
             const T mv = vget<T>(m, u);
             if (KB % E == 0) {
                 // x[l][*] as 16-byte broadcast loads
-                const V *xr = reinterpret_cast<const V *>(x + l * KB);
+                const V *xr = reinterpret_cast<const V *>(x + l * XS);
 #pragma unroll
                 for (int g = 0; g < KB / E; ++g) {
                     const V xv = xr[g];
@@ -303,8 +362,8 @@ __device__ __forceinline__ void lane_mv(const T *M, const T *x, T (&out)[KB], in
             } else {
 #pragma unroll
                 for (int q = 0; q < KB; ++q) {
-                    if (l & 1) a1[q] = fma(mv, x[l * KB + q], a1[q]);
-                    else a0[q] = fma(mv, x[l * KB + q], a0[q]);
+                    if (l & 1) a1[q] = fma(mv, x[l * XS + q], a1[q]);
+                    else a0[q] = fma(mv, x[l * XS + q], a0[q]);
                 }
             }
         }
@@ -378,213 +437,299 @@ __device__ __forceinline__ void warp_seq_post(volatile int *seq, int v)
     if ((threadIdx.x & 31) == 0) *seq = v;
 }
 
+// mbarriers in shared memory (one arrival per lane of each producer warp):
+// a waiting warp is suspended by the hardware instead of polling, so it
+// takes no issue slots or shared-memory bandwidth from the working warps.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(unsigned long long *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+// Arrive once this thread's earlier cp.async copies have landed.
+__device__ __forceinline__ void mb_arrive_cp(unsigned long long *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mb_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Warp-wide bounded wait for the phase of `bar` with this parity to complete.
+__device__ __forceinline__ bool mb_wait(const SyncArgs &sy, unsigned long long *bar, unsigned parity,
+                                        volatile int *stop, long long who)
+{
+    bool ok = mb_try_wait(bar, parity);
+    if (!__all_sync(0xffffffffu, ok)) {
+        const long long t0 = global_ns();
+        for (unsigned it = 1;; ++it) {
+            ok = ok || mb_try_wait(bar, parity);
+            if (__all_sync(0xffffffffu, ok)) break;
+            if ((it & 15u) == 0u) {
+                int bad = 0;
+                if ((threadIdx.x & 31) == 0) {
+                    if (*stop || aborted(sy)) {
+                        bad = 1;
+                    } else if (global_ns() - t0 > sy.timeout_ns || it > (1u << 26)) {
+                        record_error(sy, kStatusTimeout, who);
+                        *stop = 1;
+                        bad = 1;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+            }
+        }
+    }
+    return true;
+}
+
 // Warps of the forward-substitution kernel and the chain block's roles.
 constexpr int kTrsmWarps = 12;
 constexpr int kWCrit = 0, kWZhat = 1, kWNear0 = 2;
 constexpr int kNearWarps = kTrsmWarps - 5;  // warps 2 .. 8
 constexpr int kWZf = kTrsmWarps - 3, kWLoad = kTrsmWarps - 2, kWPub = kTrsmWarps - 1;
+// Offsets the critical warp takes itself, at most (through G^(j) = Dinv F_{b-j,b}^T).
+constexpr int kMaxCrit = 4;
 
-// Lookahead bound (near tiles d - 1 per step) and ring depths per
+// Lookahead bound (d), offsets on the critical warp (c) and ring depths per
 // instantiation, sized to the 227 KB of shared memory.
 template <typename T, int KB>
 struct ChainCfg {
     static constexpr int DMAX = sizeof(T) == 4 ? (KB <= 2 ? 10 : KB <= 4 ? 9 : KB <= 8 ? 8 : 6)
-                                               : (KB <= 2 ? 5 : KB <= 8 ? 4 : 3);
+                                               : (KB <= 2 ? 6 : KB <= 8 ? 4 : 3);
+    static constexpr int CMAX = sizeof(T) == 4 ? (KB <= 2 ? 4 : KB <= 8 ? 2 : 1) : 1;
     static constexpr int RP = DMAX + 2;   // P ring
     static constexpr int RT = DMAX;       // per near offset
-    static constexpr int RZ = 4;          // Zhat ring
+    static constexpr int RZ = 4;          // W ring
     static constexpr int RF = 4;          // far-sum ring
-    static constexpr int PF = 8;          // steps of L2 prefetch ahead of the stage
     static constexpr size_t tile = sizeof(T) * kB * Stride<T>::value;
-    static constexpr size_t stage = (size_t)(DMAX + 1) * tile;  // G, Dinv, d - 1 near tiles
-    static constexpr size_t rest = sizeof(T) * kB * KB * ((size_t)RP + (size_t)(DMAX - 1) * RT + RZ + RF + 1) +
+    static constexpr int NEAR = DMAX - CMAX > 1 ? DMAX - CMAX : 1;  // near offset slots (d - c of them used)
+    static constexpr size_t rest = sizeof(T) * Rows<T, KB>::size *
+                                       ((size_t)RP + (size_t)NEAR * RT + RZ + RF + 1) +
                                    tile + 256;
+    // staged per step: G^(1..c) and Dinv on the loader, one tile per near offset on the near warps
+    static constexpr size_t stage = (size_t)(CMAX + 1 + NEAR) * tile;
     static constexpr int fit = (int)((224u * 1024u - rest) / stage);
-    static constexpr int RS = fit > 4 ? 4 : fit;  // staged steps
+    static constexpr int RS = fit > 4 ? 4 : fit;
 };
 
 template <typename T, int KB>
 struct ChainSmem {
     using C = ChainCfg<T, KB>;
     static constexpr int S = Stride<T>::value;
-    T G[C::RS][kB * S];                   // G_m of step m
+    static constexpr int RW = Rows<T, KB>::size;
+    T G[C::RS][C::CMAX][kB * S];          // G^(j)_m, j = 1 .. c, of step m
     T Di[C::RS][kB * S];                  // Dinv_{m+1}
-    T near[C::DMAX - 1][C::RS][kB * S];   // per offset j = 2 .. d: tiles (m, m + j), [column][row]
+    T near[C::NEAR][C::RS][kB * S];       // per near offset: tiles (m, m + j), [column][row]
     T Di0[kB * S];                        // Dinv_0
-    T P[C::RP][kB * KB];
-    T Tn[C::DMAX - 1][C::RT][kB * KB];    // F_{b-j,b}^T P_{b-j} per offset j
-    T Z[C::RZ][kB * KB];                  // Zhat_b
-    T F[C::RF][kB * KB];                  // far sums Zf_b
-    T w[kB * KB];                         // Zhat warp's work vector
-    int pseq, zseq, lseq, fseq, pubseq;
-    int nseq[kNearWarps];
+    T P[C::RP][RW];
+    T Tn[C::NEAR][C::RT][RW];             // F_{b-j,b}^T P_{b-j} per near offset j
+    T Z[C::RZ][RW];                       // W_b
+    T F[C::RF][RW];                       // far sums Zf_b
+    T w[RW];                              // W warp's work vector
+    // full / empty rings: stage (G, Dinv), W, P, far sums; near warps' steps
+    unsigned long long st_full[C::RS], st_empty[C::RS];
+    unsigned long long w_full[C::RZ], w_empty[C::RZ];
+    unsigned long long p_full[C::RP], p_empty[C::RP];
+    unsigned long long f_full[C::RF], f_empty[C::RF];
+    unsigned long long t_full[kNearWarps][C::RT];
     int stop;
 };
 
-// The chain block: every role is one warp, linked by shared-memory
-// sequence counters; nothing on the critical cycle
-//   P_m -> F_{m,m+2}^T P_m -> Zhat_{m+2} -> P_{m+2}
-// waits on global memory: the loader stages G, Dinv and the near tiles a
-// few steps ahead (and prefetches further ones into L2), the far-sum warp
-// polls the workers' tagged sums ahead of use, the publisher writes each P
-// as tagged words.
+// The chain block: every role is one warp, linked by mbarrier rings (full /
+// empty per resource slot; an item m uses slot m % R with phase parity
+// (m / R) & 1, and no producer can lap a consumer by construction).  With
+// G^(j)_m = Dinv_m F_{m-j,m}^T for the c nearest offsets,
+//   P_m = W_m - sum_{j=1}^{c} G^(j)_m P_{m-j},
+//   W_m = Dinv_m (Zf_m - sum_{j=c+1}^{d} F_{m-j,m}^T P_{m-j}),
+// so the critical warp's step waits on no other warp's work of the last c
+// steps: the near warps (offsets c + 1 .. d) and the W warp have c steps of
+// slack.  The loader stages G^(1..c) and Dinv (its copies arrive on the
+// stage's barrier when they land), each near warp stages its own tiles, the
+// far-sum warp polls the workers' tagged sums ahead of use, the publisher
+// writes each P as tagged words.
 template <typename T, int KB>
 __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 {
     using C = ChainCfg<T, KB>;
     ChainSmem<T, KB> &S = *reinterpret_cast<ChainSmem<T, KB> *>(smem);
-    constexpr int SD = Stride<T>::value;
     constexpr int TW = Tag<T>::words;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nb = A.nb, d = A.d;
+    const int nb = A.nb, d = A.d, cc = A.c;
     const long long n = A.n, ld = A.ld;
     const long long ep64 = (long long)A.epoch << 32;
     const SyncArgs sy = sync_of(A);
     volatile int *stop = &S.stop;
     const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
+    const int nnear = d - cc;  // near offsets j = c + 1 .. d, offset j on near warp (j - c - 1) % kNearWarps
+    const int nnw = nnear < kNearWarps ? nnear : kNearWarps;  // near warps in use
     if (threadIdx.x == 0) {
-        S.pseq = S.zseq = S.lseq = S.fseq = S.pubseq = 0;
-        for (int t = 0; t < kNearWarps; ++t) S.nseq[t] = 0;
+        for (int i = 0; i < C::RS; ++i) {
+            mb_init(&S.st_full[i], 32);
+            mb_init(&S.st_empty[i], 64);  // the critical warp and the W warp
+        }
+        for (int i = 0; i < C::RZ; ++i) {
+            mb_init(&S.w_full[i], 32);
+            mb_init(&S.w_empty[i], 32);
+        }
+        for (int i = 0; i < C::RP; ++i) {
+            mb_init(&S.p_full[i], 32);
+            mb_init(&S.p_empty[i], 32 * (1 + nnw));  // the publisher and the near warps
+        }
+        for (int i = 0; i < C::RF; ++i) {
+            mb_init(&S.f_full[i], 32);
+            mb_init(&S.f_empty[i], 32);
+        }
+        for (int t = 0; t < kNearWarps; ++t)
+            for (int i = 0; i < C::RT; ++i) mb_init(&S.t_full[t][i], 32);
         S.stop = 0;
     }
     __syncthreads();
-    const int nnear = d - 1;  // offsets j = 2 .. d, offset j on near warp (j - 2) % kNearWarps
-#define CW(seqp, want, who)                                                     \
-    do {                                                                        \
-        if (!warp_seq_wait(sy, (seqp), (want), stop, (who))) {                  \
-            cp_wait<0>();                                                       \
-            return;                                                             \
-        }                                                                       \
+#define MW(bar, item, ring, who)                                                               \
+    do {                                                                                       \
+        if (!mb_wait(sy, &(bar)[(item) % (ring)], (unsigned)(((item) / (ring)) & 1), stop, (who))) { \
+            cp_wait<0>();                                                                      \
+            return;                                                                            \
+        }                                                                                      \
     } while (0)
 
     if (warp == kWLoad) {
         for (int m = 0; m < nb; ++m) {
             const int st = m % C::RS;
-            if (m >= C::RS) {
-                const int old = m - C::RS;
-                CW(&S.pseq, old + 1, -10);
-                CW(&S.zseq, old + 2, -12);
-            }
-            if (m >= 1) stage_dense(S.G[st], A.G + (size_t)m * kB * kB, lane);
+            if (m >= C::RS) MW(S.st_empty, m - C::RS, C::RS, -10);
+            if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 3] = global_ns();
+            for (int j = 1; j <= cc && j <= m; ++j)
+                stage_dense(S.G[st][j - 1], A.G + ((size_t)(j - 1) * nb + m) * kB * kB, lane);
             if (m + 1 < nb) stage_dense(S.Di[st], A.Dinv + (size_t)(m + 1) * kB * kB, lane);
-            cp_commit();
-            // later steps' near band into L2 (one line per column segment)
-            const int mf = m + C::PF;
-            if (mf < nb) {
-                const long long rf = (long long)mf * kB;
-                for (int c = lane; c < (d - 1) * kB; c += 32) {
-                    const long long col = (long long)(mf + 2) * kB + c;
-                    if (col < n) prefetch_l2(A.L + rf + col * ld);
-                }
-            }
-            // stage m - 1 is complete once at most one group is pending
-            cp_wait<1>();
-            warp_seq_post(&S.lseq, m);
-            if (A.trace && lane == 0 && m >= 1) A.trace[(size_t)(m - 1) * 8 + 3] = global_ns();
+            mb_arrive_cp(&S.st_full[st]);
         }
         cp_wait<0>();
-        warp_seq_post(&S.lseq, nb);
     } else if (warp == kWCrit) {
         for (int m = 0; m < nb; ++m) {
-            CW(&S.zseq, m + 1, m);
-            if (m >= 1) CW(&S.lseq, m + 1, m);
-            if (m >= C::RP) CW(&S.pubseq, m - C::RP + 1, m);
-            T out[KB];
-            const T *z = S.Z[m % C::RZ];
-            if (m == 0) {
+            MW(S.w_full, m, C::RZ, m);
+            MW(S.st_full, m, C::RS, m);
+            if (m >= C::RP) MW(S.p_empty, m - C::RP, C::RP, m);
+            if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 7] = global_ns();
+            T out[KB], acc[KB];
 #pragma unroll
-                for (int q = 0; q < KB; ++q) out[q] = z[lane * KB + q];
-            } else {
-                lane_mv<T, KB>(S.G[m % C::RS], S.P[(m - 1) % C::RP], out, lane);
+            for (int q = 0; q < KB; ++q) acc[q] = T(0);
+            for (int j = 1; j <= cc && j <= m; ++j)
+                lane_mv<T, KB>(S.G[m % C::RS][j - 1], S.P[(m - j) % C::RP], acc, lane, true);
+            row_load<T, KB>(S.Z[m % C::RZ], lane, out);
 #pragma unroll
-                for (int q = 0; q < KB; ++q) out[q] = z[lane * KB + q] - out[q];
-            }
-            T *pm = S.P[m % C::RP];
-#pragma unroll
-            for (int q = 0; q < KB; ++q) pm[lane * KB + q] = out[q];
-            warp_seq_post(&S.pseq, m + 1);
-            if (A.trace && lane == 0) A.trace[(size_t)m * 8 + 0] = global_ns();
+            for (int q = 0; q < KB; ++q) out[q] -= acc[q];
+            row_store<T, KB>(S.P[m % C::RP], lane, out);
+            __syncwarp();
+            mb_arrive(&S.p_full[m % C::RP]);
+            mb_arrive(&S.w_empty[m % C::RZ]);
+            mb_arrive(&S.st_empty[m % C::RS]);
+            if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 0] = global_ns();
         }
     } else if (warp >= kWNear0 && warp < kWNear0 + kNearWarps) {
         const int t = warp - kWNear0;
-        if (t >= nnear) return;
+        if (t >= nnw) return;
         // this warp's offsets' tiles, staged RS - 1 steps ahead (the factor as
         // it entered the pass: nothing to wait for)
         auto stage = [&](int m) {
             if (m < nb) {
-                for (int j = 2 + t; j <= d; j += kNearWarps) {
+                for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
                     const int b = m + j;
                     if (b >= nb) break;
-                    stage_tile(S.near[j - 2][m % C::RS], A.L, ld, (long long)m * kB, (long long)b * kB, n, kB,
+                    stage_tile(S.near[j - cc - 1][m % C::RS], A.L, ld, (long long)m * kB, (long long)b * kB, n, kB,
                                vec, lane);
                 }
             }
             cp_commit();
         };
+        // and, further ahead, the same tiles into L2 (one line per column segment)
+        auto prefetch = [&](int m) {
+            if (m >= nb) return;
+            for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
+                const long long col = (long long)(m + j) * kB + lane;
+                if (col < n) prefetch_l2(A.L + (long long)m * kB + col * ld);
+            }
+        };
+        constexpr int PF = 16;
+        for (int m = 0; m < PF; ++m) prefetch(m);
         for (int m = 0; m < C::RS - 1; ++m) stage(m);
         for (int m = 0; m < nb; ++m) {
+            prefetch(m + PF);
             stage(m + C::RS - 1);
-            CW(&S.pseq, m + 1, m);
+            MW(S.p_full, m, C::RP, m);
             cp_wait<C::RS - 1>();
             __syncwarp();
             const T *pm = S.P[m % C::RP];
-            for (int j = 2 + t; j <= d; j += kNearWarps) {
+            for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
                 const int b = m + j;
                 if (b >= nb) break;
                 T out[KB];
-                lane_mv<T, KB>(S.near[j - 2][m % C::RS], pm, out, lane);
-                T *dst = S.Tn[j - 2][b % C::RT];
-#pragma unroll
-                for (int q = 0; q < KB; ++q) dst[lane * KB + q] = out[q];
+                lane_mv<T, KB>(S.near[j - cc - 1][m % C::RS], pm, out, lane);
+                row_store<T, KB>(S.Tn[j - cc - 1][b % C::RT], lane, out);
             }
-            warp_seq_post(&S.nseq[t], m + 1);
+            __syncwarp();
+            mb_arrive(&S.p_empty[m % C::RP]);
+            mb_arrive(&S.t_full[t][m % C::RT]);
+            if (A.trace && t == 0 && lane == 0) A.trace[(size_t)m * 16 + 5] = global_ns();
+            if (A.trace && t == nnw - 1 && lane == 0) A.trace[(size_t)m * 16 + 12] = global_ns();
         }
     } else if (warp == kWZhat) {
-        // Dinv_0 for Zhat_0
+        // Dinv_0 for W_0
         stage_dense(S.Di0, A.Dinv, lane);
         cp_commit();
         cp_wait<0>();
         __syncwarp();
         for (int b = 0; b < nb; ++b) {
             const long long r0 = (long long)b * kB;
-            // w = Zf_b - sum_{j=2}^{d} F_{b-j,b}^T P_{b-j}
+            // w = Zf_b - sum_{j=c+1}^{d} F_{b-j,b}^T P_{b-j}
             T w[KB];
             if (b > d) {
-                CW(&S.fseq, b + 1, b);
-                const T *f = S.F[b % C::RF];
-#pragma unroll
-                for (int q = 0; q < KB; ++q) w[q] = f[lane * KB + q];
+                MW(S.f_full, b - d - 1, C::RF, b);
+                if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 10] = global_ns();
+                row_load<T, KB>(S.F[(b - d - 1) % C::RF], lane, w);
+                __syncwarp();
+                mb_arrive(&S.f_empty[(b - d - 1) % C::RF]);
             } else {
 #pragma unroll
                 for (int q = 0; q < KB; ++q)
                     w[q] = (r0 + lane < n && q < A.kb) ? A.V[r0 + lane + q * A.ldv] : T(0);
             }
-            for (int j = 2; j <= d && j <= b; ++j) {
-                const int t = (j - 2) % kNearWarps;
-                CW(&S.nseq[t], b - j + 1, b);
-                const T *tn = S.Tn[j - 2][b % C::RT];
+            for (int j = cc + 1; j <= d && j <= b; ++j) {
+                const int t = (j - cc - 1) % kNearWarps;
+                MW(S.t_full[t], b - j, C::RT, b);
+                T tn[KB];
+                row_load<T, KB>(S.Tn[j - cc - 1][b % C::RT], lane, tn);
 #pragma unroll
-                for (int q = 0; q < KB; ++q) w[q] -= tn[lane * KB + q];
+                for (int q = 0; q < KB; ++q) w[q] -= tn[q];
             }
-#pragma unroll
-            for (int q = 0; q < KB; ++q) S.w[lane * KB + q] = w[q];
+            if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 11] = global_ns();
+            row_store<T, KB>(S.w, lane, w);
             __syncwarp();
             const T *Di = S.Di0;
             if (b >= 1) {
-                CW(&S.lseq, b, b);  // stage b - 1 holds Dinv_b
+                MW(S.st_full, b - 1, C::RS, b);  // stage b - 1 holds Dinv_b
                 Di = S.Di[(b - 1) % C::RS];
             }
+            if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 6] = global_ns();
             T out[KB];
             lane_mv<T, KB>(Di, S.w, out, lane);
-            T *z = S.Z[b % C::RZ];
-#pragma unroll
-            for (int q = 0; q < KB; ++q) z[lane * KB + q] = out[q];
-            warp_seq_post(&S.zseq, b + 1);
-            if (A.trace && lane == 0) A.trace[(size_t)b * 8 + 1] = global_ns();
+            // W_{b - RZ}'s slot is free once the critical warp has used it
+            if (b >= C::RZ) MW(S.w_empty, b - C::RZ, C::RZ, b);
+            row_store<T, KB>(S.Z[b % C::RZ], lane, out);
+            __syncwarp();
+            mb_arrive(&S.w_full[b % C::RZ]);
+            if (b >= 1) mb_arrive(&S.st_empty[(b - 1) % C::RS]);
+            if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 1] = global_ns();
         }
     } else if (warp == kWZf) {
         for (int b = d + 1; b < nb; ++b) {
-            if (b >= C::RF) CW(&S.zseq, b - C::RF + 1, b);
+            const int k = b - d - 1;
+            if (k >= C::RF) MW(S.f_empty, k - C::RF, C::RF, b);
             const long long *src = A.Ztag + ((size_t)b * kB + lane) * KB * TW;
             T v[KB];
             const long long t0 = global_ns();
@@ -609,29 +754,32 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
                 __nanosleep(ns);
                 if (ns < 128) ns <<= 1;
             }
-            T *f = S.F[b % C::RF];
-#pragma unroll
-            for (int q = 0; q < KB; ++q) f[lane * KB + q] = v[q];
-            warp_seq_post(&S.fseq, b + 1);
-            if (A.trace && lane == 0) A.trace[(size_t)b * 8 + 2] = global_ns();
+            row_store<T, KB>(S.F[k % C::RF], lane, v);
+            __syncwarp();
+            mb_arrive(&S.f_full[k % C::RF]);
+            if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 2] = global_ns();
         }
     } else if (warp == kWPub) {
         for (int m = 0; m < nb; ++m) {
-            CW(&S.pseq, m + 1, m);
-            const T *pm = S.P[m % C::RP];
-            long long *tg = A.Ptag + ((size_t)m * kB + lane) * KB * TW;
+            MW(S.p_full, m, C::RP, m);
+            T v[KB];
+            row_load<T, KB>(S.P[m % C::RP], lane, v);
+            __syncwarp();
+            mb_arrive(&S.p_empty[m % C::RP]);
             T *plain = A.P + ((size_t)m * kB + lane) * KB;
 #pragma unroll
-            for (int q = 0; q < KB; ++q) {
-                const T v = pm[lane * KB + q];
-                put_tag(tg + q * TW, v, ep64);
-                plain[q] = v;
+            for (int q = 0; q < KB; ++q) __stcg(plain + q, v[q]);
+            // one flag per block (the workers poll these words only), released
+            // after the block's values
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                st_release_gpu(A.pflag + m, A.epoch);
             }
-            warp_seq_post(&S.pubseq, m + 1);
-            if (A.trace && lane == 0) A.trace[(size_t)m * 8 + 4] = global_ns();
+            if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 4] = global_ns();
         }
     }
-#undef CW
+#undef MW
 }
 
 // Worker warps: the far part of column block b's sum,
@@ -641,7 +789,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 template <typename T, int KB>
 struct WorkerCfg {
     static constexpr int NS = 3;  // staged tiles per warp
-    static constexpr size_t warp_bytes = sizeof(T) * ((size_t)NS * kB * Stride<T>::value + kB * KB);
+    static constexpr size_t warp_bytes = sizeof(T) * ((size_t)NS * kB * Stride<T>::value + Rows<T, KB>::size);
     static constexpr int warps = (int)((200u * 1024u) / warp_bytes) < kTrsmWarps
                                      ? (int)((200u * 1024u) / warp_bytes) : kTrsmWarps;
 };
@@ -655,7 +803,7 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= W::warps) return;
     T *base = reinterpret_cast<T *>(smem + (size_t)warp * W::warp_bytes);
-    T *Pr = base + (size_t)W::NS * kB * SD;  // [32][KB]
+    T *Pr = base + (size_t)W::NS * kB * SD;  // Rows<T, KB>
     const long long n = A.n, ld = A.ld;
     const int nb = A.nb, d = A.d;
     const long long ep64 = (long long)A.epoch << 32;
@@ -678,41 +826,40 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
             stage_tile(base + (size_t)(r % W::NS) * kB * SD, A.L, ld, (long long)r * kB, c0, n, kB, vec, lane);
             cp_commit();
         }
+        int avail = 0;  // blocks r .. avail - 1 are known to be published
         for (int r = 0; r < nfar; ++r) {
             const int rn = r + W::NS - 1;
             if (rn < nfar)
                 stage_tile(base + (size_t)(rn % W::NS) * kB * SD, A.L, ld, (long long)rn * kB, c0, n, kB, vec, lane);
             cp_commit();
-            // P_r: lane l polls row l's tagged words
-            const long long *src = A.Ptag + ((size_t)r * kB + lane) * KB * TW;
-            T pv[KB];
-            const long long t0 = global_ns();
-            unsigned ns = 32;
-            for (unsigned it = 0;; ++it) {
-                bool ok = true;
-#pragma unroll
-                for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &pv[q]) && ok;
-                if (__all_sync(0xffffffffu, ok)) break;
-                if ((it & 15u) == 15u) {
-                    int bad = 0;
-                    if (lane == 0) {
-                        if (aborted(sy)) bad = 1;
-                        else if (global_ns() - t0 > sy.timeout_ns || it > (1u << 26)) {
-                            record_error(sy, kStatusTimeout, b);
-                            bad = 1;
-                        }
-                    }
-                    if (__shfl_sync(0xffffffffu, bad, 0)) {
+            if (r >= avail) {
+                // one probe of the next 32 blocks' flags (lane l: block r + l);
+                // the published prefix needs no further look
+                const int f = (r + lane < nfar) ? ld_relaxed_gpu(A.pflag + r + lane) : A.epoch;
+                const unsigned not_ready = __ballot_sync(0xffffffffu, f != A.epoch);
+                int got = not_ready ? __ffs(not_ready) - 1 : 32;
+                if (got == 0) {
+                    // the next one is not out yet: lane 0 waits on its flag alone
+                    int ok = 1;
+                    if (lane == 0)
+                        ok = bounded_wait(sy, [&] { return ld_relaxed_gpu(A.pflag + r) == A.epoch; }, [] {}, b) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, ok, 0)) {
                         cp_wait<0>();
                         return;
                     }
+                    got = 1;
                 }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                fence_acq_rel_gpu();
+                avail = r + got;
             }
+            __syncwarp();
+            // P_r: every lane reads its row through L1 (shared with this SM's other warps)
+            T pv[KB];
+            const T *src = A.P + ((size_t)r * kB + lane) * KB;
 #pragma unroll
-            for (int q = 0; q < KB; ++q) Pr[lane * KB + q] = pv[q];
-            if (A.trace && lane == 0 && r == nfar - 1) A.trace[(size_t)b * 8 + 6] = global_ns();
+            for (int q = 0; q < KB; ++q) pv[q] = src[q];
+            row_store<T, KB>(Pr, lane, pv);
+            if (A.trace && lane == 0 && r == nfar - 1) A.trace[(size_t)b * 16 + 8] = global_ns();
             cp_wait<W::NS - 1>();
             __syncwarp();
             T t[KB];
@@ -725,7 +872,7 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
         long long *zt = A.Ztag + ((size_t)b * kB + lane) * KB * TW;
 #pragma unroll
         for (int q = 0; q < KB; ++q) put_tag(zt + q * TW, z[q], ep64);
-        if (A.trace && lane == 0) A.trace[(size_t)b * 8 + 7] = global_ns();
+        if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 9] = global_ns();
     }
 }
 
@@ -929,12 +1076,54 @@ struct SweepCfg {
     static constexpr size_t smem = (size_t)WARPS * NSLOT * sizeof(SweepSlot<T, KB>);
 };
 
+// One tile's rotations for column `lane`: rows 0 .. 31 (all present), kb
+// carries in registers, the row scales applied at the end.  The rows'
+// coefficients come in 16-byte broadcast loads ahead of the dependent FMA
+// chain (the only serial part: two FMAs per row and vector).
+template <typename T, int KB>
+__device__ __forceinline__ void rotate_full(T (&v)[kB], T (&uh)[KB], const T *cf, const T *e)
+{
+    using V = typename Vec16<T>::type;
+    constexpr int E = Vec16<T>::n;
+    constexpr int RW = 2 * KB;  // coefficients per row
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+        T c[RW];
+        if ((RW * (int)sizeof(T)) % 16 == 0) {
+#pragma unroll
+            for (int g = 0; g < RW / E; ++g) {
+                const V x = reinterpret_cast<const V *>(cf + i * RW)[g];
+#pragma unroll
+                for (int u = 0; u < E; ++u) c[g * E + u] = vget<T>(x, u);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < RW; ++u) c[u] = cf[i * RW + u];
+        }
+        T x = v[i];
+#pragma unroll
+        for (int q = 0; q < KB; ++q) {
+            x = fma(c[2 * q], uh[q], x);
+            uh[q] = fma(-c[2 * q + 1], x, uh[q]);
+        }
+        v[i] = x;
+    }
+#pragma unroll
+    for (int g = 0; g < kB / E; ++g) {
+        const V x = reinterpret_cast<const V *>(e)[g];
+#pragma unroll
+        for (int u = 0; u < E; ++u) v[g * E + u] *= vget<T>(x, u);
+    }
+}
+
 template <typename T, int KB>
 __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args<T> A)
 {
     using C = SweepCfg<T, KB>;
     constexpr int SD = Stride<T>::value;
     constexpr int E = 16 / (int)sizeof(T);
+    constexpr int CPC = kB / E;         // 16-byte chunks per column segment
+    constexpr int CPL = kB * CPC / 32;  // chunks per lane per tile
     using V = typename Vec16<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -942,6 +1131,9 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
     const long long n = A.n, ld = A.ld;
     const int nb = A.nb;
     const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
+    // this lane's chunk of every staged column segment: chunk ch of columns
+    // col0 + t * (32 / CPC), t = 0 .. CPL - 1
+    const int ch = lane % CPC, col0 = lane / CPC, cstep = 32 / CPC;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = atomicAdd(A.ctl + kCtlSweepTicket, 1);
@@ -953,11 +1145,28 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
         T uh[KB];
 #pragma unroll
         for (int q = 0; q < KB; ++q) uh[q] = (active && q < A.kb) ? A.V[c0 + lane + q * A.ldv] : T(0);
+        // per-lane addresses of the staged chunks (vector path)
+        const T *gbase = A.L + (long long)ch * E + (c0 + col0) * ld;
+        unsigned colmask = 0;
+#pragma unroll
+        for (int t = 0; t < CPL; ++t)
+            if (c0 + col0 + t * cstep < n) colmask |= 1u << t;
         auto fetch = [&](int r) {
             SweepSlot<T, KB> &sl = slot[r % C::NSLOT];
             const long long r0 = (long long)r * kB;
-            if (r < b) {
-                stage_tile(sl.tile, A.L, ld, r0, c0, n, kB, vec, lane);
+            if (r < b && vec) {
+                const T *g = gbase + r0;
+                T *d = sl.tile + col0 * SD + ch * E;
+#pragma unroll
+                for (int t = 0; t < CPL; ++t) {
+                    if (colmask >> t & 1u) cp16(d + t * cstep * SD, g + (long long)t * cstep * ld);
+                    else {
+#pragma unroll
+                        for (int u = 0; u < E; ++u) d[t * cstep * SD + u] = T(0);
+                    }
+                }
+            } else if (r < b) {
+                stage_tile(sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
             } else {
                 // the diagonal tile: rows <= column only
                 for (int col = 0; col < kB; ++col)
@@ -965,7 +1174,7 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
             }
             const T *cf = A.coef + (size_t)r0 * 2 * KB;
             for (int c = lane; c < kB * 2 * KB / E; c += 32) cp16(sl.cf + c * E, cf + c * E);
-            for (int c = lane; c < kB / E; c += 32) cp16(sl.e + c * E, A.escale + r0 + c * E);
+            if (lane < kB / E) cp16(sl.e + lane * E, A.escale + r0 + lane * E);
             if (r == b && lane < kB / 2) cp16(sl.df + 2 * lane, A.dfac + r0 + 2 * lane);
         };
         for (int r = 0; r < C::NSLOT - 1; ++r) {
@@ -980,7 +1189,6 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
             SweepSlot<T, KB> &sl = slot[r % C::NSLOT];
             const bool diag = r == b;
             const long long r0 = (long long)r * kB;
-            const int rows = diag ? lane : (int)min((long long)kB, n - r0);
             T v[kB];
             V *colv = reinterpret_cast<V *>(sl.tile + lane * SD);
 #pragma unroll
@@ -989,10 +1197,13 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
 #pragma unroll
                 for (int u = 0; u < E; ++u) v[c * E + u] = vget<T>(x, u);
             }
-            if (active) {
+            if (!diag) {
+                if (active) rotate_full<T, KB>(v, uh, sl.cf, sl.e);
+            } else if (active) {
+                // rows above the diagonal of column `lane`, then the diagonal
 #pragma unroll
                 for (int i = 0; i < kB; ++i) {
-                    if (i < rows) {
+                    if (i < lane) {
                         T x = v[i];
 #pragma unroll
                         for (int q = 0; q < KB; ++q) {
@@ -1000,7 +1211,7 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
                             uh[q] = fma(-sl.cf[i * 2 * KB + 2 * q + 1], x, uh[q]);
                         }
                         v[i] = x * sl.e[i];
-                    } else if (diag && i == lane) {
+                    } else if (i == lane) {
                         v[i] = (T)((double)v[i] * sl.df[i]);
                     }
                 }
@@ -1016,18 +1227,16 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
             }
             __syncwarp();
             if (!diag && vec) {
-                constexpr int CPC = kB / E;
-                for (int c = lane; c < kB * CPC; c += 32) {
-                    const int cc = c / CPC, ch = c % CPC;
-                    if (c0 + cc < n)
-                        *reinterpret_cast<V *>(A.L + (r0 + ch * E) + (c0 + cc) * ld) =
-                            *reinterpret_cast<const V *>(sl.tile + cc * SD + ch * E);
-                }
+                T *g = const_cast<T *>(gbase) + r0;
+                const T *d = sl.tile + col0 * SD + ch * E;
+#pragma unroll
+                for (int t = 0; t < CPL; ++t)
+                    if (colmask >> t & 1u)
+                        *reinterpret_cast<V *>(g + (long long)t * cstep * ld) = *reinterpret_cast<const V *>(d + t * cstep * SD);
             } else {
 #pragma unroll 8
                 for (int cc = 0; cc < kB; ++cc)
-                    if (c0 + cc < n && (!diag || lane <= cc) && (diag || lane < rows))
-                        A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
+                    if (c0 + cc < n && (!diag || lane <= cc)) A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
             }
             __syncwarp();
         }

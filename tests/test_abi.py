@@ -159,10 +159,10 @@ def test_path_settings_and_automatic_rule():
     assert chm.config_get("pass_kb") == 5
     chm.config_set("pass_kb", 0)
     assert chm.config_get("pass_kb") == 16
-    chm.config_set("pass_d", 100 // 10)
-    assert chm.config_get("pass_d_f32") == 10 and chm.config_get("pass_d_f64") == 5
+    chm.config_set("pass_d", 9)
+    assert chm.config_get("pass_d_f32") == 9 and chm.config_get("pass_d_f64") == 6
     chm.config_set("pass_d", 0)
-    assert chm.config_get("pass_d_f32") == 6 and chm.config_get("pass_d_f64") == 4
+    assert chm.config_get("pass_d_f32") == 10 and chm.config_get("pass_d_f64") == 4
     for key, val in (("path", 3), ("pass_kb", 17), ("pass_kb", -1), ("nope", 1)):
         assert chm.chm_config_set(key, val) == chm.CHM_ERR_ARG
 
