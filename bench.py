@@ -158,11 +158,12 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="time the batch plan's default configuration")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-factors", type=int, default=2000)
-    ap.add_argument("--serve-warmup", type=int, default=0,
+    ap.add_argument("--serve-warmup", type=int, default=1000,
                     help="served requests before the measured ones (left out of rates and latencies)")
-    ap.add_argument("--serve-loads", default="0.9",
+    ap.add_argument("--serve-loads", default="0.9,1.5",
                     help="offered loads as fractions of the plain path's saturation rate, comma separated")
     ap.add_argument("--no-batch-mixed", action="store_true")
+    ap.add_argument("--no-serve-f64", action="store_true", help="skip the float64 serving run")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the n = 32768 single-factor cases (k = 1, 16; float64 and float32 storage)")
     return ap.parse_args()
@@ -338,13 +339,16 @@ def bench_solve(dev, L, reps=5):
     return {"workload": "solve with the bench factor after the timed steps, n=%d float64" % n, "runs": runs}
 
 
-def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n=32768, reps=4):
+def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n=32768, reps=4, tune=True):
     """The large single-factor configuration (n = 32768, an update by U then
     the cancellation-stressed downdate by 0.9 U, the factor built on the
     device from its seed) through the same C ABI call as the main line, on
     the path the library picks; per case the median time of one
     modification (CUDA events), GB/s, the fraction of measured HBM and of the
-    binding roofline.  L is restored from a device copy before each pair."""
+    binding roofline.  L is restored from a device copy before each pair.
+    With ``tune`` each case is then autotuned (chm_tune) and timed again
+    with the tuned configuration ("tuned": the choice, its tuning-run
+    times, and the same measurement as the case's)."""
     import torch
 
     from paper_1011_1173_gb300 import chm, inputs
@@ -389,16 +393,42 @@ def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n
         alu_peak = fp32_tflops if dt == "f32" else fp64_tflops
         t_alu = alg_flops(n, k) / (alu_peak * 1e12)
         bound = "hbm" if t_hbm >= t_alu else "alu"
-        out.append({
+        rec = {
             "n": n, "k": k, "dtype": dt, "path": "pass" if path == chm.PATH_PASS else "wave",
             "ms_per_modification": ms, "GBps": gbs, "hbm_frac": gbs / peak_hbm,
             "TFLOPs": flops, "alu_frac": flops / alu_peak,
             "bound": bound, "binding_frac": max(t_hbm, t_alu) / (ms / 1e3),
-            "launches_per_modification": launches_per_modification(path, k)})
+            "launches_per_modification": launches_per_modification(path, k)}
+        if tune:
+            # the autotuner's choice for this shape (chm_tune), then the same
+            # timing with the tuned configuration from the cache
+            t = chm.tune(n, k, chm.CHM_F32_MIXED if dt == "f32" else chm.CHM_F64)
+            L.copy_(L0)
+            tts = []
+            for r in range(reps + 1):
+                L.copy_(L0)
+                for V, sg in ((U, 1), (U9, -1)):
+                    flush.zero_()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    chm.check(chm.modify(L, V, sg, stream=stream), "large tuned")
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    if r > 0:
+                        tts.append(a.elapsed_time(b))
+            chm.check(chm.status_sync(stream)[0], "large tuned status")
+            tms = statistics.median(tts)
+            t["ms_per_modification"] = tms
+            t["GBps"] = alg_bytes(n, k, elt) / (tms / 1e3) / 1e9
+            t["hbm_frac"] = t["GBps"] / peak_hbm
+            rec["tuned"] = t
+        out.append(rec)
         del L, L0, U, U9
         torch.cuda.empty_cache()
     del base, flush
     torch.cuda.empty_cache()
+    chm.chm_tune_clear()  # later sections time the library's defaults
     return {"workload": "n=%d, update by U then downdate by 0.9 U (U ~ N(0, 1/n)), factor of B^T B / n + I "
                         "built on the device" % n,
             "hbm_peak_GBps": peak_hbm, "hbm_peak_source": hbm_src,
@@ -442,20 +472,28 @@ def bench_host_resident(dev, L0, V, reps=3):
             "device_workspace_bytes": chm.workspace_bytes(n, k)}
 
 
-def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.9,), warm=0):
+def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.9,), warm=0, dtype="f32"):
     """Served requests (chm_server_*) against plain launches serialised on one
     stream, at each offered load (a fraction of the plain path's measured
     saturation rate); the same request sequence is replayed at every load.
     The first ``warm`` requests of each run are served but left out of the
-    reported rates and latencies."""
+    reported rates and latencies.  In float64 the dense factors of all
+    ``nfactors`` orders would exceed the budget, so the leading factors of
+    the same sampled sequence that fit in 80 % of it are resident (the
+    server keeps the rest for its launches' scratch)."""
     import numpy as np
     import torch
 
     from paper_1011_1173_gb300 import chm, inputs
     rng = np.random.default_rng(inputs.config_seed(4))
     ns = np.exp(rng.uniform(np.log(256), np.log(8192), nfactors)).astype(int)
-    dt = torch.float32
-    srv = chm.Server(budget, chm.CHM_F32_MIXED, max_inflight=2)
+    f64 = dtype == "f64"
+    dt = torch.float64 if f64 else torch.float32
+    elt = 8 if f64 else 4
+    fits = np.cumsum(ns.astype(np.float64) ** 2 * elt) <= 0.8 * budget  # the rest: the server's launch scratch
+    nfactors = int(np.count_nonzero(fits)) if f64 else nfactors
+    ns = ns[:nfactors]
+    srv = chm.Server(budget, chm.CHM_F64 if f64 else chm.CHM_F32_MIXED, max_inflight=2)
     perm = rng.permutation(nfactors)
     for i in range(nfactors):
         L = inputs.random_factor(int(ns[i]), 20000 + i, device=dev, dtype=dt)
@@ -480,7 +518,7 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
     def plain_copies():  # plain comparator's copies of the factors touched
         return {f: inputs.random_factor(int(ns[f]), 20000 + f, device=dev, dtype=dt) for f in used}
 
-    bytes_req = [alg_bytes(int(ns[f]), V.shape[0], 4) for f, V, _ in reqs]
+    bytes_req = [alg_bytes(int(ns[f]), V.shape[0], elt) for f, V, _ in reqs]
     tot = float(sum(bytes_req[warm:]))
     # plain saturation rate: back-to-back launches on one stream
     stream = torch.cuda.current_stream()
@@ -547,10 +585,12 @@ def bench_serve(dev, nfactors=2000, nreq=2000, budget=120 * (1 << 30), loads=(0.
     srv.close()
     del reqs, hist
     torch.cuda.empty_cache()
-    out = {"workload": "%d resident factors, n log-uniform [256, 8192], float32 storage + float64 Compute, "
+    out = {"workload": "%d resident factors, n log-uniform [256, 8192], %s, "
                        "%d requests after %d warm-up requests, k ~ U{1..32}, factor Zipf(1.1), 70%% updates / "
                        "30%% downdates, Poisson arrivals at %s x the plain path's saturation rate"
-                       % (nfactors, nreq, warm, "/".join("%g" % x for x in loads)),
+                       % (nfactors, "float64" if f64 else "float32 storage + float64 Compute", nreq, warm,
+                          "/".join("%g" % x for x in loads)),
+           "dtype": dtype, "resident_bytes": float(np.sum(ns.astype(np.float64) ** 2 * elt)),
            "plain_saturation_rps": sat}
     if len(results) == 1:
         out.update(results[0])
@@ -812,7 +852,7 @@ def main():
                      "traffic": NCU_TRAFFIC.get((kernel, kernel_source_hash(), n, k)),
                      "kernel_source_hash": kernel_source_hash()})
 
-    batch = batch_mixed = serve = solve = host = large = None
+    batch = batch_mixed = serve = serve_f64 = solve = host = large = None
     if rank == 0 and not args.no_large:
         large = bench_large(dev)
     if rank == 0 and not args.no_solve and not mixed:
@@ -827,6 +867,9 @@ def main():
         loads = [float(x) for x in args.serve_loads.split(",") if x.strip()]
         serve = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests, loads=loads,
                             warm=args.serve_warmup)
+        if not args.no_serve_f64:
+            serve_f64 = bench_serve(dev, nfactors=args.serve_factors, nreq=args.serve_requests, loads=loads,
+                                    warm=args.serve_warmup, dtype="f64")
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -843,7 +886,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
                 "large": large,
-                "batched": batch, "batched_mixed": batch_mixed, "served": serve, "solve": solve, "host_resident": host,
+                "batched": batch, "batched_mixed": batch_mixed, "served": serve, "served_f64": serve_f64,
+                "solve": solve, "host_resident": host,
                 "gpu_launches": 2 * args.steps * launches_per_modification(path, k),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -57,6 +57,16 @@
  *     for the launch's other waits, -5 for a problem of a batch or server
  *     launch that stopped because another problem's wait ran out).  After
  *     either, L is unspecified.
+ *   - Bounds-checked build.  The same sources compiled with -DCHM_CHECK
+ *     (libchm_check.so, built beside libchm.so) check every global index
+ *     the kernels form: each element of L against the upper triangle of its
+ *     leading n x n block with leading dimension ld, each element of V and
+ *     of a solve's B against their leading n rows and k (nrhs) columns, and
+ *     every workspace region against its allocation.  A failed check skips
+ *     the access, records CHM_ERR_BOUNDS (info = the element's offset from
+ *     the array's base, or the region's byte offset from its allocation)
+ *     and ends the launch's waits; nothing traps.  chm_config_get("checked")
+ *     says which build is loaded (1 checked, 0 not).
  *   - Memory.  The library keeps a workspace per (device, stream): per
  *     vector of a launch (at most 64 per launch) rotation panels, ratio
  *     tiles and flags of about 19 KB per 32 rows, and the status word
@@ -93,7 +103,8 @@ typedef enum {
     CHM_ERR_CUDA = -4,
     CHM_ERR_NOMEM = -5,
     CHM_ERR_BUDGET = -6,
-    CHM_ERR_STATE = -7
+    CHM_ERR_STATE = -7,
+    CHM_ERR_BOUNDS = -8  /* bounds-checked build only: a kernel index outside its array */
 } chm_status;
 
 /*
@@ -399,18 +410,67 @@ int chm_microbench(int which, double *out, int nout);
  * crosses the CPU-GPU link three times per pass of up to 16 vectors; the
  * wave kernel re-reads it once per vector).
  * chm_config_get also answers "pass_d_f32" and "pass_d_f64" (the values in
- * effect).  Host only.  Returns CHM_OK or CHM_ERR_ARG (unknown key or value
- * out of range).
+ * effect) and "checked" (1 in the bounds-checked build).  The bounds-checked
+ * build also takes "check_cut" (>= 0, default 0): its checks treat each
+ * factor as that many columns narrower than declared, so that they report
+ * accesses to real, valid memory (a test of the checks themselves; the
+ * access is skipped).  Host only.  Returns CHM_OK or CHM_ERR_ARG (unknown
+ * key or value out of range).
  */
 int chm_config_set(const char *key, int64_t value);
 int chm_config_get(const char *key, int64_t *value);
 
 /*
  * The path (1 wave kernel, 2 pass kernels) a single-factor modification of
- * order n by k vectors takes under the current settings.  Host only.
- * Returns CHM_OK or CHM_ERR_ARG.
+ * order n by k vectors takes under the current settings and tuning cache.
+ * Host only.  Returns CHM_OK or CHM_ERR_ARG.
  */
 int chm_path_for(int64_t n, int64_t k, int dtype, int *path);
+
+/*
+ * Autotuning of the single-factor entry points.  The paper fixes its
+ * kernels' parameters for its GPU (Sec. 4.1: blocks per kernel, threads per
+ * block, elements per thread); here they are measured.  chm_tune times, on
+ * the current device, a modification of order n by k vectors in dtype
+ * under candidate configurations: the wave kernel, and the pass kernels
+ * over vectors per pass (min(k, 16) and the two powers of two below it),
+ * the substitution's lookahead d ({4, 6, 8, 10} float, {2, 3, 4, 6}
+ * double) and the sweep's segment length (the default, 32, 128 row blocks).
+ * Each candidate runs an update and downdate by the same V four times on a
+ * scratch factor it generates (diagonal 1 + U[0,1), strictly upper entries
+ * of variance 1/n; V of variance 1/(4nk)); the median of the last three is
+ * its time.  The fastest configuration is stored in the library's tuning
+ * cache under (dtype, floor(log2 n), ceil(log2 k)); from then on every
+ * single-factor modification of a device factor whose shape falls in that
+ * bucket takes it, except for the parameters a library setting ("path",
+ * "pass_kb", "pass_d", "pass_seg") forces.  The result is the same factor
+ * up to rounding whichever configuration runs.
+ *   result  HOST array of 6 (may be NULL): path, vectors per pass,
+ *           lookahead, segment length (0: by the order), the tuned time of
+ *           one modification in ns, and the time of the built-in default
+ *           configuration in ns.
+ * Synchronous; allocates n*n + n*k elements and a workspace on its own
+ * stream and frees them before returning.  Returns CHM_OK, CHM_ERR_ARG
+ * (n < 1, k < 1, n > 2^20, k > 4096, bad dtype), CHM_ERR_NOMEM or
+ * CHM_ERR_CUDA (a launch failed, or a candidate's modification reported an
+ * error; the cache is then unchanged).
+ */
+int chm_tune(int64_t n, int64_t k, int dtype, int64_t *result);
+/* Empties the tuning cache.  Host only; returns CHM_OK. */
+int chm_tune_clear(void);
+/*
+ * Writes the tuning cache to a text file: the line "chm-tune 1", then one
+ * line per entry, "dtype nbucket kbucket path kb d seg ns".  Host only;
+ * returns CHM_OK or CHM_ERR_ARG (NULL path, file not writable).
+ */
+int chm_tune_save(const char *path);
+/*
+ * Merges a file written by chm_tune_save into the tuning cache (its entries
+ * replace those with the same key).  A file that is not in that format, or
+ * holds an out-of-range value, changes nothing and returns CHM_ERR_ARG.
+ * Host only.
+ */
+int chm_tune_load(const char *path);
 
 /*
  * Self-test of the reciprocal and reciprocal square root the kernels use in

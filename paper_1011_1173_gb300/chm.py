@@ -11,6 +11,7 @@ p of V (see ``inputs.py``).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 
@@ -29,8 +30,11 @@ CHM_ERR_CUDA = -4
 CHM_ERR_NOMEM = -5
 CHM_ERR_BUDGET = -6
 CHM_ERR_STATE = -7
+CHM_ERR_BOUNDS = -8
 
 _lib = None
+_lib_checked = None
+_use_checked = False
 
 
 class ChmError(RuntimeError):
@@ -44,14 +48,38 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = False):
-    """Load libchm.so (optionally building it first).  Raises if unavailable."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.LIB
+    """Load libchm.so (optionally building it first).  Raises if unavailable.
+    Inside ``with checked_library():`` this is the bounds-checked build."""
+    global _lib, _lib_checked
+    if _use_checked:
+        if _lib_checked is None:
+            _lib_checked = _open(_build.LIB_CHECK, build_if_missing)
+        return _lib_checked
+    if _lib is None:
+        _lib = _open(_build.LIB, build_if_missing)
+    return _lib
+
+
+@contextlib.contextmanager
+def checked_library(build_if_missing: bool = True):
+    """Route every call of this module made inside the block to
+    libchm_check.so, the library built with -DCHM_CHECK (every global index
+    of the kernels checked; an index outside the arguments' arrays reports
+    CHM_ERR_BOUNDS instead of being accessed)."""
+    global _use_checked
+    prev = _use_checked
+    _use_checked = True
+    try:
+        load(build_if_missing)
+        yield _lib_checked
+    finally:
+        _use_checked = prev
+
+
+def _open(path, build_if_missing):
     if not os.path.exists(path):
         if not build_if_missing:
-            raise RuntimeError("libchm.so is not built (run paper_1011_1173_gb300.build.build())")
+            raise RuntimeError("%s is not built (run paper_1011_1173_gb300.build.build())" % os.path.basename(path))
         _build.build()
     lib = ctypes.CDLL(path)
     i64, vp, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
@@ -85,12 +113,15 @@ def load(build_if_missing: bool = False):
         "chm_path_for": ([i64, i64, i32, vp], i32),
         "chm_workspace_bytes": ([i64, i64, i32, vp], i32),
         "chm_solve": ([vp, i64, i64, vp, i64, i64, i32, vp], i32),
+        "chm_tune": ([i64, i64, i32, vp], i32),
+        "chm_tune_clear": ([], i32),
+        "chm_tune_save": ([ctypes.c_char_p], i32),
+        "chm_tune_load": ([ctypes.c_char_p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
-    _lib = lib
     return lib
 
 
@@ -229,6 +260,32 @@ def path_for(n, k, dtype=CHM_F64) -> int:
 
 def chm_selftest_reciprocals(x, count, out):
     return load().chm_selftest_reciprocals(x, count, out)
+
+
+def chm_tune(n, k, dtype, result):
+    return load().chm_tune(n, k, dtype, result)
+
+
+def chm_tune_clear():
+    return load().chm_tune_clear()
+
+
+def chm_tune_save(path):
+    return load().chm_tune_save(path.encode() if isinstance(path, str) else path)
+
+
+def chm_tune_load(path):
+    return load().chm_tune_load(path.encode() if isinstance(path, str) else path)
+
+
+def tune(n, k, dtype=CHM_F64) -> dict:
+    """Autotune single-factor modifications of this shape (chm_tune); the
+    choice enters the library's tuning cache.  Returns the chosen
+    configuration and the tuned and default times per modification (ms)."""
+    r = (ctypes.c_int64 * 6)()
+    check(chm_tune(int(n), int(k), int(dtype), ctypes.cast(r, ctypes.c_void_p)), "chm_tune")
+    return {"path": "pass" if r[0] == PATH_PASS else "wave", "vectors_per_pass": int(r[1]), "lookahead": int(r[2]),
+            "segment_blocks": int(r[3]), "ms": r[4] / 1e6, "default_ms": r[5] / 1e6}
 
 
 def chm_solve(L, n, ld, B, ldb, nrhs, dtype, stream):

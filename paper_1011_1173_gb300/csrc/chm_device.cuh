@@ -11,6 +11,7 @@ namespace chm {
 // Device status codes (mirror chm_status in chm.h).
 constexpr long long kStatusNotPD = -2;
 constexpr long long kStatusTimeout = -3;
+constexpr long long kStatusBounds = -8;
 
 // What a waiting or failing thread needs: the launch's abort flag and
 // status words, and the epoch that tags this launch's flags.
@@ -20,6 +21,7 @@ struct SyncArgs {
     long long *user_info;  // optional {status, info} of the problem
     int epoch;             // distinguishes this launch's flags from older ones
     long long timeout_ns;  // bound on any single wait
+    long long chk_cut;     // bounds-checked build: columns taken off a factor's declared extent
 };
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p)
@@ -101,8 +103,63 @@ __device__ __forceinline__ void record_error(const SyncArgs &s, long long code, 
 {
     record_one(s.status, code, info);
     if (s.user_info) record_one(s.user_info, code, info);
-    if (code == kStatusTimeout) atomicExch(s.abort_flag, 1);
+    if (code == kStatusTimeout || code == kStatusBounds) atomicExch(s.abort_flag, 1);
 }
+
+// Bounds checks.  A library built with -DCHM_CHECK passes every global
+// access of the factor L, the update vectors V and the right-hand sides B
+// through these predicates, and every workspace region a kernel derives
+// through chk_region.  An index outside what the call's arguments declare
+// (L: the upper triangle of the leading n x n block with leading dimension
+// ld; V, B: the leading n rows of their k or nrhs columns) records
+// CHM_ERR_BOUNDS with info = the element's offset from the array's base (for
+// a region, the region's byte offset from its allocation), raises the abort
+// flag so that every wait of the launch ends, and makes the caller skip the
+// access: nothing traps and nothing outside the arrays is touched.
+// chk_cut > 0 (a test setting) takes that many columns off the factor's
+// declared extent, so that accesses to real, valid memory are reported.
+// Without -DCHM_CHECK the predicates are the constant true.
+#ifdef CHM_CHECK
+static __device__ __noinline__ bool chk_fail(const SyncArgs &s, long long where)
+{
+    record_error(s, kStatusBounds, where < 0 ? 0x7fffffffffffffffll : where);
+    return false;
+}
+// element `off` of an upper-triangular factor of order n, leading dimension ld
+__device__ __forceinline__ bool chk_tri(const SyncArgs &s, long long off, long long n, long long ld)
+{
+    if (off >= 0 && ld > 0) {
+        const long long j = off / ld, i = off - j * ld;
+        if (i <= j && j < n - s.chk_cut) return true;
+    }
+    return chk_fail(s, off);
+}
+// element `off` of a column-major rows x cols array, leading dimension ld
+__device__ __forceinline__ bool chk_rect(const SyncArgs &s, long long off, long long rows, long long cols,
+                                         long long ld)
+{
+    if (off >= 0 && ld > 0) {
+        const long long j = off / ld, i = off - j * ld;
+        if (i < rows && j < cols) return true;
+    }
+    return chk_fail(s, off);
+}
+// bytes [p, p + bytes) inside the allocation [lo, lo + size)
+__device__ __forceinline__ bool chk_region(const SyncArgs &s, const void *p, size_t bytes, const void *lo,
+                                           size_t size)
+{
+    const char *a = static_cast<const char *>(p), *b = static_cast<const char *>(lo);
+    if (a >= b && (size_t)(a - b) <= size && bytes <= size - (size_t)(a - b)) return true;
+    return chk_fail(s, (long long)(a - b));
+}
+#define CHK_TRI(s, off, n, ld) ::chm::chk_tri((s), (off), (n), (ld))
+#define CHK_RECT(s, off, rows, cols, ld) ::chm::chk_rect((s), (off), (rows), (cols), (ld))
+#define CHK_REGION(s, p, bytes, lo, size) ::chm::chk_region((s), (p), (bytes), (lo), (size))
+#else
+#define CHK_TRI(s, off, n, ld) true
+#define CHK_RECT(s, off, rows, cols, ld) true
+#define CHK_REGION(s, p, bytes, lo, size) true
+#endif
 
 // One thread waits until ready() holds.  ready() polls with relaxed loads
 // (cheap, no ordering) under exponential backoff; once it holds, acquire()

@@ -98,8 +98,33 @@ struct PassSpace {
     char *buf = nullptr;
     size_t bytes = 0;
     int epoch = 0;
+    long long flag_n = -1;  // the order and element type whose flag layout the buffer holds
+    int flag_dtype = -1;
+    // the sweep task table the buffer holds: where it is (its offset depends
+    // on the element type and the order), the (nb, d, seg) it was built for
+    // (nb < 0: none; reset whenever the buffer is allocated) and its length
+    const void *task_at = nullptr;
+    int task_nb = -1, task_d = -1, task_seg = -1, task_count = 0;
 };
-size_t pass_workspace_bytes(long long n, int dtype);
+// What a single-factor modification runs: the path and the pass kernels' parameters.
+struct PassChoice {
+    int path;  // 1 the wave kernel, 2 the pass kernels
+    int kb;    // vectors per pass, 1 .. 16
+    int d;     // lookahead of the substitution chain (each instantiation clamps it further)
+    int seg;   // row blocks per sweep segment (0: by the order)
+};
+// The choice for a modification of this shape: explicit settings, else the
+// tuner's candidate while it times one, else the tuning cache (device
+// factors), else the built-in rule and defaults.
+PassChoice choose_path(long long n, long long k, int dtype, bool host_factor);
+// The tuning cache (chm_tune.cu): the entry for (dtype, floor(log2 n), ceil(log2 k)).
+bool tune_lookup(int dtype, long long n, long long k, PassChoice *out);
+// The configuration the tuner is timing on this thread (null outside chm_tune).
+const PassChoice *tune_override();
+size_t pass_workspace_bytes(long long n, int dtype, int seg);
+// Frees the workspace the library keeps for (device, stream), if any; the
+// caller has synchronised the stream.
+void release_workspace(int dev, cudaStream_t s);
 size_t pass_flag_bytes(long long n, int dtype);
 // True if a single-factor modification of this shape runs on the pass
 // kernels (the library setting "path", else the size rule; a factor in
@@ -109,6 +134,8 @@ bool use_pass_path(long long n, long long k, int dtype, bool host_factor);
 bool is_host_memory(const void *p);
 // The "path" setting in effect (0 automatic, 1 wave kernel, 2 pass kernels).
 int path_setting();
+// Bounds-checked builds: columns taken off each factor's declared extent by the checks (a test setting; 0 otherwise).
+long long check_cut();
 // Runs fn on the stream's status word and pass workspace, grown first to
 // at least `bytes`, under the workspaces' lock.
 int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtype,
@@ -120,6 +147,6 @@ long long *trace_buffer(size_t words, cudaStream_t stream);
 // Enqueue the passes of one modification (kb <= 16 vectors each).
 int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
                  const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
-                 const Scratch &sc, PassSpace &ps);
+                 const PassChoice &ch, const Scratch &sc, PassSpace &ps);
 
 }  // namespace chm

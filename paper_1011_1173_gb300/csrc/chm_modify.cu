@@ -163,6 +163,13 @@ static int launch_t(const Prob *single, const Prob *d_probs, const int *d_pair_p
     P.trace = trace;
     P.timeout_ns = timeout_ns();
     P.skip_publish = cfg.skip_publish;
+    P.ws_data = sc.data;
+    P.ws_data_bytes = sc.data_bytes;
+    P.ws_iflags = sc.iflags;
+    P.ws_iflags_n = sc.iflags_cap;
+    P.ws_progress = sc.progress;
+    P.ws_progress_n = sc.progress_cap;
+    P.chk_cut = check_cut();
     wave_kernel<T><<<grid, 128, kBlockSmemBytes, stream>>>(P);
     return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
 }
@@ -328,6 +335,22 @@ long long *trace_buffer(size_t words, cudaStream_t stream)
     return g_trace;
 }
 
+// Frees the workspace of (dev, s), if any (the caller has synchronised s).
+void release_workspace(int dev, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (size_t i = 0; i < g_ws.size(); ++i) {
+        Workspace *w = g_ws[i];
+        if (w->device == dev && w->stream == s) {
+            scratch_free(&w->sc);
+            cudaFree(w->ps.buf);
+            delete w;
+            g_ws.erase(g_ws.begin() + (long)i);
+            return;
+        }
+    }
+}
+
 static Workspace *find_workspace(int dev, cudaStream_t s, bool create)
 {
     for (Workspace *w : g_ws)
@@ -438,11 +461,12 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
     if (rc != CHM_OK) return rc;
     if (n == 0 || k == 0) return info_init(d_info, 1, stream);
     if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK) return rc;
-    if (use_pass_path(n, k, dtype, is_host_memory(L))) {
-        return with_pass_workspace(stream, pass_workspace_bytes(n, dtype), n, dtype,
+    const PassChoice ch = choose_path(n, k, dtype, is_host_memory(L));
+    if (ch.path == 2) {
+        return with_pass_workspace(stream, pass_workspace_bytes(n, dtype, ch.seg), n, dtype,
                                    [&](const Scratch &sc, PassSpace &ps) {
                                        return pass_enqueue(L, n, ld, V, ldv, k, sigma, sign, dtype, stream,
-                                                           d_info, sc, ps);
+                                                           d_info, ch, sc, ps);
                                    });
     }
     const int kw_max = (int)std::min<long long>(k, kMaxWaves);
@@ -475,6 +499,20 @@ int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtyp
         if (cudaMemset(w->ps.buf, 0, pass_flag_bytes(n, dtype)) != cudaSuccess) return CHM_ERR_CUDA;
         w->ps.bytes = bytes;
         w->ps.epoch = 0;
+        w->ps.flag_n = n;
+        w->ps.flag_dtype = dtype;
+        w->ps.task_nb = -1;  // holds no sweep task table yet
+    }
+    // The flags' places move with the order and the element type: a call
+    // whose layout differs from the last one's zeroes its flag region first
+    // (in stream order), so that no word left there by another layout (a
+    // data value, a control count) can pass for one of this pass's flags.
+    // Within one layout the region only ever holds flags and tagged words of
+    // earlier passes, whose epochs match no later pass.
+    if (w->ps.flag_n != n || w->ps.flag_dtype != dtype) {
+        if (cudaMemsetAsync(w->ps.buf, 0, pass_flag_bytes(n, dtype), stream) != cudaSuccess) return CHM_ERR_CUDA;
+        w->ps.flag_n = n;
+        w->ps.flag_dtype = dtype;
     }
     return fn(w->sc, w->ps);
 }
@@ -621,9 +659,10 @@ int chm_workspace_bytes(int64_t n, int64_t k, int dtype, size_t *bytes)
     if (!bytes || n < 0 || k < 0 || n > (1ll << 26)) return CHM_ERR_ARG;
     if (dtype != CHM_F64 && dtype != CHM_F32_MIXED) return CHM_ERR_ARG;
     const size_t wave = chm::single_workspace_bytes(n, k);
-    const size_t pass = (n > 0 && k > 0)
-                            ? chm::kCtlInts * sizeof(int) + 2 * sizeof(long long) + chm::pass_workspace_bytes(n, dtype)
-                            : 0;
+    const chm::PassChoice ch = chm::choose_path(n, k, dtype, false);
+    const size_t pass = (n > 0 && k > 0) ? chm::kCtlInts * sizeof(int) + 2 * sizeof(long long) +
+                                               chm::pass_workspace_bytes(n, dtype, ch.seg)
+                                         : 0;
     // a forced path holds its own workspace; the automatic rule may take
     // either (a factor in host memory takes the pass kernels), so the larger
     const int path = chm::path_setting();
@@ -666,6 +705,7 @@ const char *chm_status_string(int status)
     case CHM_ERR_NOMEM: return "CHM_ERR_NOMEM: device allocation failed";
     case CHM_ERR_BUDGET: return "CHM_ERR_BUDGET: memory budget exceeded";
     case CHM_ERR_STATE: return "CHM_ERR_STATE: invalid object state";
+    case CHM_ERR_BOUNDS: return "CHM_ERR_BOUNDS: a kernel index outside its array (bounds-checked build)";
     default: return "unknown status";
     }
 }

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <vector>
 #include <cstdlib>
 #include <cstring>
 
@@ -20,6 +21,8 @@ namespace {
 std::atomic<int> g_path{0};      // 0 automatic, 1 wave kernel, 2 pass kernels
 std::atomic<int> g_pass_kb{0};   // vectors per pass (0: the largest, 16)
 std::atomic<int> g_pass_d{0};    // lookahead of the substitution chain (0: per type)
+std::atomic<int> g_pass_seg{0};  // row blocks per sweep segment (0: by the order)
+std::atomic<long long> g_check_cut{0};  // bounds-checked build: columns taken off a factor's extent
 
 int env_or(const char *name, int dflt)
 {
@@ -28,20 +31,41 @@ int env_or(const char *name, int dflt)
 }
 }  // namespace
 
-static int pass_kb_max()
+long long check_cut() { return g_check_cut.load(); }
+
+// The explicit settings (library setting, else environment; 0: not set).
+static int kb_setting()
 {
-    int v = g_pass_kb.load();
-    if (v <= 0) v = env_or("CHM_PASS_KB", pass::kMaxKb);
-    return std::max(1, std::min(pass::kMaxKb, v));
+    const int v = g_pass_kb.load();
+    return v > 0 ? v : std::max(0, env_or("CHM_PASS_KB", 0));
+}
+static int d_setting()
+{
+    const int v = g_pass_d.load();
+    return v > 0 ? v : std::max(0, env_or("CHM_PASS_D", 0));
+}
+static int seg_setting()
+{
+    const int v = g_pass_seg.load();
+    return v > 0 ? v : std::max(0, env_or("CHM_PASS_SEG", 0));
 }
 
-static int pass_d(int dtype)
+static int clamp_kb(int v) { return std::max(1, std::min(pass::kMaxKb, v)); }
+// each instantiation clamps the lookahead further to what its shared memory holds
+static int clamp_d(int v, int dtype) { return std::max(2, std::min(dtype == CHM_F64 ? 6 : 10, v)); }
+
+static int pass_kb_max() { return clamp_kb(kb_setting() > 0 ? kb_setting() : pass::kMaxKb); }
+
+static int pass_d(int dtype) { return clamp_d(d_setting() > 0 ? d_setting() : (dtype == CHM_F64 ? 4 : 10), dtype); }
+
+// Row blocks per segment of the sweep's column tasks: a column block's
+// tiles are split at multiples of this, each segment starting from the
+// carry rebuilt from the substitution's partial residual, so that no task
+// is longer than about this many tiles.  By default at most 16 boundaries,
+// so that the residual snapshots stay O(n k).
+static int pass_seg(int nb, int seg)
 {
-    int v = g_pass_d.load();
-    if (v <= 0) v = env_or("CHM_PASS_D", 0);
-    if (v <= 0) v = dtype == CHM_F64 ? 4 : 10;
-    // each instantiation clamps it further to what its shared memory holds
-    return std::max(2, std::min(dtype == CHM_F64 ? 6 : 10, v));
+    return std::max(1, seg > 0 ? seg : std::max(64, (nb + 15) / 16));
 }
 
 int path_setting()
@@ -51,19 +75,41 @@ int path_setting()
     return p == 1 || p == 2 ? p : 0;
 }
 
-bool use_pass_path(long long n, long long k, int dtype, bool host_factor)
+// The built-in rule: the pass path once the factor is larger than about a
+// third of L2 (where the wave kernel's waves start to re-stream it); in
+// float64 only for few vectors, where the wave kernel's chain, not the FP64
+// rate, bounds it; and for a factor in page-locked host memory.
+static bool rule_pass(long long n, long long k, int dtype, bool host_factor)
 {
-    const int p = path_setting();
-    if (p == 1) return false;
-    if (p == 2) return true;
     if (host_factor) return n >= 64;
-    // automatic: the pass path once the factor is larger than about a
-    // third of L2 (where the wave kernel's waves start to re-stream it); in
-    // float64 only for few vectors, where the wave kernel's chain, not the
-    // FP64 rate, bounds it
     const double bytes = (double)(dtype == CHM_F64 ? 8 : 4) * n * n / 2;
     if (dtype == CHM_F64) return bytes >= 256e6 && k <= 2;
     return bytes >= 32e6;
+}
+
+PassChoice choose_path(long long n, long long k, int dtype, bool host_factor)
+{
+    // precedence: explicit settings, then the tuner's candidate while it
+    // times one, then the tuning cache (device factors), then the defaults
+    PassChoice base{rule_pass(n, k, dtype, host_factor) ? 2 : 1, pass::kMaxKb, dtype == CHM_F64 ? 4 : 10, 0};
+    PassChoice tuned;
+    if (const PassChoice *o = tune_override()) base = *o;
+    else if (!host_factor && tune_lookup(dtype, n, k, &tuned)) base = tuned;
+    PassChoice c = base;
+    const int p = path_setting();
+    if (p != 0) c.path = p;
+    if (kb_setting() > 0) c.kb = kb_setting();
+    if (d_setting() > 0) c.d = d_setting();
+    if (seg_setting() > 0) c.seg = seg_setting();
+    c.kb = clamp_kb(c.kb);
+    c.d = clamp_d(c.d, dtype);
+    c.seg = std::max(0, c.seg);
+    return c;
+}
+
+bool use_pass_path(long long n, long long k, int dtype, bool host_factor)
+{
+    return choose_path(n, k, dtype, host_factor).path == 2;
 }
 
 // ---------------------------------------------------------------- workspace
@@ -71,12 +117,14 @@ bool use_pass_path(long long n, long long k, int dtype, bool host_factor)
 namespace {
 
 struct PassLayout {
-    size_t P, pflag, Ztag, Dinv, G, gram, H, coef, escale, dfac, ctl, bytes;
+    size_t P, pflag, Ztag, Dinv, G, gram, H, coef, escale, dfac, snap, rst, tasks, ctl, bytes;
+    int seg, nbound;  // row blocks per sweep segment; segment boundaries (the snapshots' count)
+    size_t ntask_max;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-PassLayout pass_layout(long long n, int elt)
+PassLayout pass_layout(long long n, int elt, int seg)
 {
     const size_t nb = (size_t)((n + pass::kB - 1) / pass::kB);
     const size_t rows = nb * pass::kB;
@@ -97,20 +145,27 @@ PassLayout pass_layout(long long n, int elt)
     l.coef = x; x = al(x + rows * 2 * KB * elt);
     l.escale = x; x = al(x + rows * elt);
     l.dfac = x; x = al(x + rows * 8);
+    // sweep segments: boundaries at row blocks seg, 2 seg, ... below the last block
+    l.seg = pass_seg((int)nb, seg);
+    l.nbound = nb > 1 ? (int)((nb - 1) / (size_t)l.seg) : 0;
+    l.snap = x; x = al(x + (size_t)l.nbound * rows * KB * elt);
+    l.rst = x; x = al(x + (size_t)l.nbound * KB * (KB + 1) / 2 * 8);
+    l.ntask_max = nb * (size_t)(1 + l.nbound);
+    l.tasks = x; x = al(x + l.ntask_max * 8);
     l.bytes = x;
     return l;
 }
 
 }  // namespace
 
-size_t pass_workspace_bytes(long long n, int dtype)
+size_t pass_workspace_bytes(long long n, int dtype, int seg)
 {
-    return pass_layout(n, dtype == CHM_F64 ? 8 : 4).bytes;
+    return pass_layout(n, dtype == CHM_F64 ? 8 : 4, seg).bytes;
 }
 
 size_t pass_flag_bytes(long long n, int dtype)
 {
-    return pass_layout(n, dtype == CHM_F64 ? 8 : 4).P;  // the tagged and control words
+    return pass_layout(n, dtype == CHM_F64 ? 8 : 4, 0).P;  // the tagged and control words (lead the buffer)
 }
 
 // ---------------------------------------------------------------- launches
@@ -166,8 +221,50 @@ int pass_setup(int dev, int *sweep_bps)
     return CHM_OK;
 }
 
+// The sweep's tasks, (column block, segment), longest first, in the
+// workspace.  Column block b has 1 + floor((b - d - 1) / seg) segments (a
+// boundary needs the residual snapshot the substitution's workers take,
+// which covers row blocks below b - d); the last one ends at the diagonal
+// tile.  The table is written when its place in the buffer (which moves
+// with the element type and the order) or (nb, d, seg) differs from the one
+// the workspace holds: the copy is ordered before this pass's kernels on
+// the stream, and every earlier pass has read its table by then.
+int sweep_tasks(PassSpace &ps, int nb, int d, int seg, int2 *dst, int *ntasks, cudaStream_t s)
+{
+    if (!(ps.task_at == dst && ps.task_nb == nb && ps.task_d == d && ps.task_seg == seg)) {
+        struct Item {
+            int len, b, s;
+        };
+        std::vector<Item> items;
+        for (int b = 0; b < nb; ++b) {
+            const int ns = 1 + std::max(0, (b - d - 1) / seg);
+            for (int q = 0; q < ns; ++q) {
+                const int last_rb = q == ns - 1 ? b : (q + 1) * seg - 1;
+                items.push_back(Item{last_rb - q * seg + 1, b, q});
+            }
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+            return x.len != y.len ? x.len > y.len : x.b > y.b;
+        });
+        std::vector<int2> tab(items.size());
+        for (size_t i = 0; i < items.size(); ++i) tab[i] = make_int2(items[i].b, items[i].s);
+        // pageable source: the call returns once the data is staged, so the
+        // vector may go out of scope afterwards
+        ps.task_nb = -1;
+        if (cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return CHM_ERR_CUDA;
+        ps.task_at = dst;
+        ps.task_nb = nb;
+        ps.task_d = d;
+        ps.task_seg = seg;
+        ps.task_count = (int)tab.size();
+    }
+    *ntasks = ps.task_count;
+    return CHM_OK;
+}
+
 template <typename T, int KB>
-int launch_pass(pass::Args<T> A, cudaStream_t s)
+int launch_pass(pass::Args<T> A, PassSpace &ps, cudaStream_t s)
 {
     int dev = 0, nsm = 0, bps = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHM_ERR_CUDA;
@@ -177,6 +274,7 @@ int launch_pass(pass::Args<T> A, cudaStream_t s)
     const int nb = A.nb;
     A.d = std::min(A.d, pass::ChainCfg<T, KB>::DMAX);
     A.c = std::min(A.d, pass::ChainCfg<T, KB>::CMAX);
+    if ((rc = sweep_tasks(ps, A.nb, A.d, A.seg, const_cast<int2 *>(A.tasks), &A.ntasks, s)) != CHM_OK) return rc;
     if (cudaMemsetAsync(A.ctl, 0, pass::kCtlInts * sizeof(int), s) != cudaSuccess) return CHM_ERR_CUDA;
     pass::prep_kernel<T><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::trsm_kernel<T, KB><<<nsm, pass::kTrsmWarps * 32, trsm_smem<T, KB>(), s>>>(A);
@@ -188,22 +286,22 @@ int launch_pass(pass::Args<T> A, cudaStream_t s)
 }
 
 template <typename T>
-int launch_pass_kb(const pass::Args<T> &A, cudaStream_t s)
+int launch_pass_kb(const pass::Args<T> &A, PassSpace &ps, cudaStream_t s)
 {
     const int kb = A.kb;
-    if (kb <= 1) return launch_pass<T, 1>(A, s);
-    if (kb <= 2) return launch_pass<T, 2>(A, s);
-    if (kb <= 4) return launch_pass<T, 4>(A, s);
-    if (kb <= 8) return launch_pass<T, 8>(A, s);
-    return launch_pass<T, 16>(A, s);
+    if (kb <= 1) return launch_pass<T, 1>(A, ps, s);
+    if (kb <= 2) return launch_pass<T, 2>(A, ps, s);
+    if (kb <= 4) return launch_pass<T, 4>(A, ps, s);
+    if (kb <= 8) return launch_pass<T, 8>(A, ps, s);
+    return launch_pass<T, 16>(A, ps, s);
 }
 
 template <typename T>
 int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
                    const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
-                   const Scratch &sc, PassSpace &ps)
+                   const PassChoice &ch, const Scratch &sc, PassSpace &ps)
 {
-    const PassLayout lay = pass_layout(n, sizeof(T));
+    const PassLayout lay = pass_layout(n, sizeof(T), ch.seg);
     char *w = ps.buf;
     pass::Args<T> A;
     memset(&A, 0, sizeof(A));
@@ -212,7 +310,7 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.ld = ld;
     A.ldv = ldv;
     A.nb = (int)((n + pass::kB - 1) / pass::kB);
-    A.d = pass_d(dtype);
+    A.d = ch.d;
     A.P = reinterpret_cast<T *>(w + lay.P);
     A.pflag = reinterpret_cast<int *>(w + lay.pflag);
     A.Ztag = reinterpret_cast<long long *>(w + lay.Ztag);
@@ -224,10 +322,17 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.escale = reinterpret_cast<T *>(w + lay.escale);
     A.dfac = reinterpret_cast<double *>(w + lay.dfac);
     A.ctl = reinterpret_cast<int *>(w + lay.ctl);
+    A.snap = reinterpret_cast<T *>(w + lay.snap);
+    A.rst = reinterpret_cast<double *>(w + lay.rst);
+    A.tasks = reinterpret_cast<const int2 *>(w + lay.tasks);
+    A.seg = lay.seg;
+    A.ws = w;
+    A.ws_bytes = ps.bytes;
+    A.chk_cut = check_cut();
     A.status = sc.status;
     A.user_info = d_info;
     A.timeout_ns = timeout_ns();
-    const int kbmax = pass_kb_max();
+    const int kbmax = ch.kb;
     for (long long q0 = 0; q0 < k; q0 += kbmax) {
         const int kb = (int)std::min<long long>(kbmax, k - q0);
         A.V = V + q0 * ldv;
@@ -238,7 +343,7 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
         A.down_mask = mask;
         A.epoch = ++ps.epoch;
         A.trace = trace_buffer((size_t)A.nb * 16, stream);  // the last pass's, with CHM_TRACE=1
-        const int rc = launch_pass_kb<T>(A, stream);
+        const int rc = launch_pass_kb<T>(A, ps, stream);
         if (rc != CHM_OK) return rc;
     }
     return CHM_OK;
@@ -248,15 +353,15 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
 
 int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
                  const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
-                 const Scratch &sc, PassSpace &ps)
+                 const PassChoice &ch, const Scratch &sc, PassSpace &ps)
 {
     int rc = info_init(d_info, 1, stream);
     if (rc != CHM_OK) return rc;
     if (dtype == CHM_F64)
         return enqueue_passes<double>(static_cast<double *>(L), n, ld, static_cast<const double *>(V), ldv, k,
-                                      sigma, sign, dtype, stream, d_info, sc, ps);
+                                      sigma, sign, dtype, stream, d_info, ch, sc, ps);
     return enqueue_passes<float>(static_cast<float *>(L), n, ld, static_cast<const float *>(V), ldv, k, sigma,
-                                 sign, dtype, stream, d_info, sc, ps);
+                                 sign, dtype, stream, d_info, ch, sc, ps);
 }
 
 }  // namespace chm
@@ -281,6 +386,18 @@ int chm_config_set(const char *key, int64_t value)
         chm::g_pass_d.store((int)value);
         return CHM_OK;
     }
+    if (!strcmp(key, "pass_seg")) {
+        if (value < 0 || value > (1 << 24)) return CHM_ERR_ARG;
+        chm::g_pass_seg.store((int)value);
+        return CHM_OK;
+    }
+#ifdef CHM_CHECK
+    if (!strcmp(key, "check_cut")) {
+        if (value < 0) return CHM_ERR_ARG;
+        chm::g_check_cut.store((long long)value);
+        return CHM_OK;
+    }
+#endif
     return CHM_ERR_ARG;
 }
 
@@ -291,6 +408,13 @@ int chm_config_get(const char *key, int64_t *value)
     else if (!strcmp(key, "pass_kb")) *value = chm::pass_kb_max();
     else if (!strcmp(key, "pass_d_f32")) *value = chm::pass_d(CHM_F32_MIXED);
     else if (!strcmp(key, "pass_d_f64")) *value = chm::pass_d(CHM_F64);
+    else if (!strcmp(key, "pass_seg")) *value = chm::seg_setting();
+#ifdef CHM_CHECK
+    else if (!strcmp(key, "checked")) *value = 1;
+    else if (!strcmp(key, "check_cut")) *value = chm::check_cut();
+#else
+    else if (!strcmp(key, "checked")) *value = 0;
+#endif
     else return CHM_ERR_ARG;
     return CHM_OK;
 }

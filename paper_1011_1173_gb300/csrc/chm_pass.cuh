@@ -43,6 +43,8 @@ namespace pass {
 constexpr int kB = 32;     // rows of a row block == columns of a column block
 constexpr int kPad = 33;   // shared-memory row stride of a 32 x 32 matrix
 constexpr int kMaxKb = 16; // vectors per pass
+// Offsets the substitution's critical warp takes itself, at most (through G^(j) = Dinv F_{b-j,b}^T).
+constexpr int kMaxCrit = 4;
 
 // Control words of a pass (zeroed before each pass).
 constexpr int kCtlWorkTicket = 0;   // next worker task of the forward substitution
@@ -71,6 +73,12 @@ struct Args {
     T *coef;         // [nb * 32][2 KB]: (a_q, b_q) of each row
     T *escale;       // [nb * 32]: 1 / sqrt(D_kb) of each row
     double *dfac;    // [nb * 32]: sqrt(D_kb) of each row
+    T *snap;         // [nbound][nb * 32][KB]: each column's partial residual of the substitution,
+                     // V_j - sum over rows below s seg 32 of F_ij p_i, at boundary s = 1 .. nbound
+    double *rst;     // [nbound][KB (KB + 1) / 2]: packed LDL^T of the prefix Gram at each boundary
+    const int2 *tasks;  // [ntasks]: the sweep's (column block, segment) tasks, longest first
+    int ntasks;
+    int seg;         // row blocks per sweep segment
     int *pflag;      // [nb]: P of the block published (== epoch), with release
     long long *Ztag; // [nb][32][KB][words of T]: Zf as epoch-tagged words
     int *ctl;        // kCtlInts control words
@@ -81,6 +89,9 @@ struct Args {
                            // 0 P posted, 1 W posted, 2 far sum staged, 4 P published,
                            // 5 first near warp done, 6 W warp's inputs in, 7 critical
                            // warp's inputs in, 8 a worker's last P seen, 9 its far sum out
+    const char *ws;        // the workspace allocation the regions above are carved from
+    size_t ws_bytes;
+    long long chk_cut;     // bounds-checked build: columns taken off the factor's declared extent
 };
 
 template <typename T>
@@ -92,7 +103,40 @@ __device__ __forceinline__ SyncArgs sync_of(const Args<T> &A)
     s.user_info = A.user_info;
     s.epoch = A.epoch;
     s.timeout_ns = A.timeout_ns;
+    s.chk_cut = A.chk_cut;
     return s;
+}
+
+// Bounds-checked builds: every workspace region a kernel with KB vectors
+// per pass indexes lies inside the workspace allocation, and the pass's
+// shape fits the regions (the kernel returns at once otherwise).
+template <typename T, int KB>
+__device__ __forceinline__ bool ws_ok(const Args<T> &A, const SyncArgs &sy)
+{
+#ifdef CHM_CHECK
+    const size_t nb = (size_t)A.nb, rows = nb * kB, e = sizeof(T);
+    const size_t tagw = e / 4;  // 64-bit words of one tagged value
+    return CHK_RECT(sy, (long long)A.kb, KB + 1, 1, 1 << 30) && CHK_RECT(sy, (long long)A.c, kMaxCrit + 1, 1, 1 << 30) &&
+           CHK_RECT(sy, A.n, (long long)rows + 1, 1, 1ll << 62) &&
+           CHK_REGION(sy, A.P, rows * KB * e, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.pflag, nb * sizeof(int), A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.Ztag, rows * KB * tagw * 8, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.Dinv, nb * kB * kB * e, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.G, (size_t)A.c * nb * kB * kB * e, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.gram, nb * KB * KB * 8, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.H, nb * KB * KB * 8, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.coef, rows * 2 * KB * e, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.escale, rows * e, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.dfac, rows * 8, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.snap, (nb > 1 ? (nb - 1) / (size_t)A.seg : 0) * rows * KB * e, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.rst, (nb > 1 ? (nb - 1) / (size_t)A.seg : 0) * KB * (KB + 1) / 2 * 8, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.tasks, (size_t)A.ntasks * sizeof(int2), A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.ctl, kCtlInts * sizeof(int), A.ws, A.ws_bytes);
+#else
+    (void)A;
+    (void)sy;
+    return true;
+#endif
 }
 
 template <typename T>
@@ -132,13 +176,14 @@ __global__ void __launch_bounds__(32) prep_kernel(Args<T> A)
     const int lane = threadIdx.x;
     const SyncArgs sy = sync_of(A);
     const long long n = A.n, ld = A.ld;
+    if (!ws_ok<T, kMaxKb>(A, sy)) return;  // touches no region that depends on the pass's vectors
     for (int b = blockIdx.x; b < A.nb; b += gridDim.x) {
         const long long c0 = (long long)b * kB;
         const int rows = (int)min((long long)kB, n - c0);
 #pragma unroll 4
         for (int j = 0; j < kB; ++j) {
             T v = T(0);
-            if (j < rows && lane <= j) v = A.L[c0 + lane + (c0 + j) * ld];
+            if (j < rows && lane <= j && CHK_TRI(sy, c0 + lane + (c0 + j) * ld, n, ld)) v = A.L[c0 + lane + (c0 + j) * ld];
             else if (lane == j) v = T(1);
             D[lane][j] = v;
         }
@@ -169,7 +214,8 @@ __global__ void __launch_bounds__(32) prep_kernel(Args<T> A)
             // the tile j blocks above the diagonal block: rows of block b - j (all < n), columns of block b
             const long long rj = c0 - (long long)j * kB;
 #pragma unroll 4
-            for (int l = 0; l < kB; ++l) Ft[l][lane] = (l < rows) ? A.L[(rj + lane) + (c0 + l) * ld] : T(0);
+            for (int l = 0; l < kB; ++l)
+                Ft[l][lane] = (l < rows && CHK_TRI(sy, (rj + lane) + (c0 + l) * ld, n, ld)) ? A.L[(rj + lane) + (c0 + l) * ld] : T(0);
             __syncwarp();
             T *gg = A.G + ((size_t)(j - 1) * A.nb + b) * kB * kB;
 #pragma unroll 4
@@ -234,8 +280,8 @@ __device__ __forceinline__ void prefetch_l2(const void *gmem)
 // copies (every column's segment 16-byte aligned and all 32 rows inside the
 // column, r0 + 32 <= n); otherwise one element per copy, rows >= nrows zero.
 template <typename T>
-__device__ __forceinline__ void stage_tile(T *dst, const T *L, long long ld, long long r0, long long c0,
-                                           long long n, int nrows, bool vec, int lane)
+__device__ __forceinline__ void stage_tile(const SyncArgs &sy, T *dst, const T *L, long long ld, long long r0,
+                                           long long c0, long long n, int nrows, bool vec, int lane)
 {
     constexpr int S = Stride<T>::value;
     if (vec) {
@@ -244,8 +290,9 @@ __device__ __forceinline__ void stage_tile(T *dst, const T *L, long long ld, lon
         for (int c = lane; c < kB * CPC; c += 32) {
             const int col = c / CPC, ch = c % CPC;
             T *d = dst + col * S + ch * E;
-            if (c0 + col < n) {
-                cp16(d, L + (r0 + ch * E) + (c0 + col) * ld);
+            const long long o = (r0 + ch * E) + (c0 + col) * ld;
+            if (c0 + col < n && CHK_TRI(sy, o, n, ld) && CHK_TRI(sy, o + E - 1, n, ld)) {
+                cp16(d, L + o);
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) d[e] = T(0);
@@ -254,7 +301,8 @@ __device__ __forceinline__ void stage_tile(T *dst, const T *L, long long ld, lon
     } else {
         for (int col = 0; col < kB; ++col) {
             T *d = dst + col * S + lane;
-            if (c0 + col < n && lane < nrows) cp_elem(d, L + (r0 + lane) + (c0 + col) * ld);
+            const long long o = (r0 + lane) + (c0 + col) * ld;
+            if (c0 + col < n && lane < nrows && CHK_TRI(sy, o, n, ld)) cp_elem(d, L + o);
             else *d = T(0);
         }
     }
@@ -494,8 +542,6 @@ constexpr int kTrsmWarps = 12;
 constexpr int kWCrit = 0, kWZhat = 1, kWNear0 = 2;
 constexpr int kNearWarps = kTrsmWarps - 5;  // warps 2 .. 8
 constexpr int kWZf = kTrsmWarps - 3, kWLoad = kTrsmWarps - 2, kWPub = kTrsmWarps - 1;
-// Offsets the critical warp takes itself, at most (through G^(j) = Dinv F_{b-j,b}^T).
-constexpr int kMaxCrit = 4;
 
 // Lookahead bound (d), offsets on the critical warp (c) and ring depths per
 // instantiation, sized to the 227 KB of shared memory.
@@ -641,7 +687,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
                 for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
                     const int b = m + j;
                     if (b >= nb) break;
-                    stage_tile(S.near[j - cc - 1][m % C::RS], A.L, ld, (long long)m * kB, (long long)b * kB, n, kB,
+                    stage_tile(sy, S.near[j - cc - 1][m % C::RS], A.L, ld, (long long)m * kB, (long long)b * kB, n, kB,
                                vec, lane);
                 }
             }
@@ -652,7 +698,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             if (m >= nb) return;
             for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
                 const long long col = (long long)(m + j) * kB + lane;
-                if (col < n) prefetch_l2(A.L + (long long)m * kB + col * ld);
+                if (col < n && CHK_TRI(sy, (long long)m * kB + col * ld, n, ld)) prefetch_l2(A.L + (long long)m * kB + col * ld);
             }
         };
         constexpr int PF = 16;
@@ -697,7 +743,8 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             } else {
 #pragma unroll
                 for (int q = 0; q < KB; ++q)
-                    w[q] = (r0 + lane < n && q < A.kb) ? A.V[r0 + lane + q * A.ldv] : T(0);
+                    w[q] = (r0 + lane < n && q < A.kb && CHK_RECT(sy, r0 + lane + q * A.ldv, n, A.kb, A.ldv))
+                               ? A.V[r0 + lane + q * A.ldv] : T(0);
             }
             for (int j = cc + 1; j <= d && j <= b; ++j) {
                 const int t = (j - cc - 1) % kNearWarps;
@@ -820,17 +867,24 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
         const bool col_ok = c0 + lane < n;
         T z[KB];
 #pragma unroll
-        for (int q = 0; q < KB; ++q) z[q] = (col_ok && q < A.kb) ? A.V[c0 + lane + q * A.ldv] : T(0);
+        for (int q = 0; q < KB; ++q)
+            z[q] = (col_ok && q < A.kb && CHK_RECT(sy, c0 + lane + q * A.ldv, n, A.kb, A.ldv)) ? A.V[c0 + lane + q * A.ldv] : T(0);
         const int nfar = b - d;
         for (int r = 0; r < W::NS - 1 && r < nfar; ++r) {
-            stage_tile(base + (size_t)(r % W::NS) * kB * SD, A.L, ld, (long long)r * kB, c0, n, kB, vec, lane);
+            stage_tile(sy, base + (size_t)(r % W::NS) * kB * SD, A.L, ld, (long long)r * kB, c0, n, kB, vec, lane);
             cp_commit();
         }
         int avail = 0;  // blocks r .. avail - 1 are known to be published
         for (int r = 0; r < nfar; ++r) {
+            if (r > 0 && r % A.seg == 0) {
+                // a sweep segment boundary: the residual before row block r
+                T *sn = A.snap + (((size_t)(r / A.seg - 1) * nb + b) * kB + lane) * KB;
+#pragma unroll
+                for (int q = 0; q < KB; ++q) sn[q] = z[q];
+            }
             const int rn = r + W::NS - 1;
             if (rn < nfar)
-                stage_tile(base + (size_t)(rn % W::NS) * kB * SD, A.L, ld, (long long)rn * kB, c0, n, kB, vec, lane);
+                stage_tile(sy, base + (size_t)(rn % W::NS) * kB * SD, A.L, ld, (long long)rn * kB, c0, n, kB, vec, lane);
             cp_commit();
             if (r >= avail) {
                 // one probe of the next 32 blocks' flags (lane l: block r + l);
@@ -881,6 +935,7 @@ __global__ void __launch_bounds__(kTrsmWarps * 32, 1) trsm_kernel(Args<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_role;
+    if (!ws_ok<T, KB>(A, sync_of(A))) return;
     if (threadIdx.x == 0) s_role = atomicAdd(A.ctl + kCtlRole, 1);
     __syncthreads();
     if (s_role == 0) trsm_chain<T, KB>(A, smem);
@@ -895,6 +950,7 @@ __global__ void __launch_bounds__(32) gram_kernel(Args<T> A)
 {
     __shared__ double p[kB][KB];
     const int lane = threadIdx.x;
+    if (!ws_ok<T, KB>(A, sync_of(A))) return;
     for (int b = blockIdx.x; b < A.nb; b += gridDim.x) {
         const T *src = A.P + (size_t)b * kB * KB;
         for (int x = lane; x < kB * KB; x += 32) (&p[0][0])[x] = (double)src[x];
@@ -923,6 +979,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(Args<T> A)
     const int e = blockIdx.x * 32 + (threadIdx.x & 31);  // entry
     const int s = threadIdx.x >> 5;                      // segment
     const int nb = A.nb;
+    if (!ws_ok<T, KB>(A, sync_of(A))) return;
     const int len = (nb + 31) / 32;
     const int b0 = s * len, b1 = min(nb, b0 + len);
     const bool valid = e < KB * KB;
@@ -975,6 +1032,7 @@ __global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
     const SyncArgs sy = sync_of(A);
     const long long n = A.n;
     const int kb = A.kb;
+    if (!ws_ok<T, KB>(A, sy)) return;
     for (int b = blockIdx.x; b < A.nb; b += gridDim.x) {
         const long long r0 = (long long)b * kB;
         const int rows = (int)min((long long)kB, n - r0);
@@ -1015,6 +1073,11 @@ __global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
                 for (int m = 0; m < j; ++m) t -= h[pidx(i, m)] * h[pidx(j, m)] * h[pidx(m, m)];
                 h[pidx(i, j)] = t * idj;
             }
+        }
+        // at a sweep segment boundary, the prefix Gram's LDL^T before the block
+        if (lane == 0 && b > 0 && b % A.seg == 0) {
+            double *dst = A.rst + (size_t)(b / A.seg - 1) * (KB * (KB + 1) / 2);
+            for (int e = 0; e < NE; ++e) dst[e] = h[e];
         }
         // z = L^{-1} p and the coefficients
         double z[KB];
@@ -1130,6 +1193,8 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
     SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * C::NSLOT;
     const long long n = A.n, ld = A.ld;
     const int nb = A.nb;
+    const SyncArgs sy = sync_of(A);
+    if (!ws_ok<T, KB>(A, sy)) return;
     const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
     // this lane's chunk of every staged column segment: chunk ch of columns
     // col0 + t * (32 / CPC), t = 0 .. CPL - 1
@@ -1138,15 +1203,51 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
         int tk = 0;
         if (lane == 0) tk = atomicAdd(A.ctl + kCtlSweepTicket, 1);
         tk = __shfl_sync(0xffffffffu, tk, 0);
-        if (tk >= nb) return;
-        const int b = nb - 1 - tk;  // largest first
+        if (tk >= A.ntasks) return;
+        // segment sg of column block b: row blocks rb .. re (the last
+        // segment ends at the diagonal tile)
+        const int2 task = __ldg(A.tasks + tk);
+        const int b = task.x, sg = task.y;
+        const int nseg = 1 + max(0, (b - A.d - 1) / A.seg);
+        if (b < 0 || b >= nb || sg < 0 || sg >= nseg) {
+            // not a task of this pass (an internal invariant, checked in every build)
+            if (lane == 0) record_error(sy, kStatusBounds, (long long)b);
+            return;
+        }
+        const int rb = sg * A.seg, re = sg == nseg - 1 ? b : rb + A.seg - 1;
         const long long c0 = (long long)b * kB;
         const bool active = c0 + lane < n;
         T uh[KB];
+        if (sg == 0) {
 #pragma unroll
-        for (int q = 0; q < KB; ++q) uh[q] = (active && q < A.kb) ? A.V[c0 + lane + q * A.ldv] : T(0);
+            for (int q = 0; q < KB; ++q)
+                uh[q] = (active && q < A.kb && CHK_RECT(sy, c0 + lane + q * A.ldv, n, A.kb, A.ldv)) ? A.V[c0 + lane + q * A.ldv]
+                                                                                                   : T(0);
+        } else {
+            // the carry entering row block rb, rebuilt from the substitution's
+            // residual w there: u_hat = |D|^{-1} L^{-1} w with H = L D L^T the
+            // prefix Gram before the block (the scaled rotations' carry is
+            // this linear image of the residual at every row)
+            const T *w = A.snap + (((size_t)(sg - 1) * nb + b) * kB + lane) * KB;
+            const double *h = A.rst + (size_t)(sg - 1) * (KB * (KB + 1) / 2);
+            double z[KB];
+#pragma unroll
+            for (int q = 0; q < KB; ++q) {
+                if (q < A.kb) {
+                    double zq = active ? (double)w[q] : 0.0;
+#pragma unroll
+                    for (int m = 0; m < q; ++m) zq -= __ldg(h + pidx(q, m)) * z[m];
+                    z[q] = zq;
+                    uh[q] = (T)(zq / (sigma_of(A, q) * __ldg(h + pidx(q, q))));
+                } else {
+                    z[q] = 0.0;
+                    uh[q] = T(0);
+                }
+            }
+        }
         // per-lane addresses of the staged chunks (vector path)
-        const T *gbase = A.L + (long long)ch * E + (c0 + col0) * ld;
+        const long long gofs = (long long)ch * E + (c0 + col0) * ld;
+        const T *gbase = A.L + gofs;
         unsigned colmask = 0;
 #pragma unroll
         for (int t = 0; t < CPL; ++t)
@@ -1159,30 +1260,33 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
                 T *d = sl.tile + col0 * SD + ch * E;
 #pragma unroll
                 for (int t = 0; t < CPL; ++t) {
-                    if (colmask >> t & 1u) cp16(d + t * cstep * SD, g + (long long)t * cstep * ld);
+                    if ((colmask >> t & 1u) && CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld, n, ld) &&
+                        CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld + E - 1, n, ld))
+                        cp16(d + t * cstep * SD, g + (long long)t * cstep * ld);
                     else {
 #pragma unroll
                         for (int u = 0; u < E; ++u) d[t * cstep * SD + u] = T(0);
                     }
                 }
             } else if (r < b) {
-                stage_tile(sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
+                stage_tile(sy, sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
             } else {
                 // the diagonal tile: rows <= column only
                 for (int col = 0; col < kB; ++col)
-                    if (c0 + col < n && lane <= col) cp_elem(&sl.tile[col * SD + lane], A.L + (r0 + lane) + (c0 + col) * ld);
+                    if (c0 + col < n && lane <= col && CHK_TRI(sy, (r0 + lane) + (c0 + col) * ld, n, ld))
+                        cp_elem(&sl.tile[col * SD + lane], A.L + (r0 + lane) + (c0 + col) * ld);
             }
             const T *cf = A.coef + (size_t)r0 * 2 * KB;
             for (int c = lane; c < kB * 2 * KB / E; c += 32) cp16(sl.cf + c * E, cf + c * E);
             if (lane < kB / E) cp16(sl.e + lane * E, A.escale + r0 + lane * E);
             if (r == b && lane < kB / 2) cp16(sl.df + 2 * lane, A.dfac + r0 + 2 * lane);
         };
-        for (int r = 0; r < C::NSLOT - 1; ++r) {
-            if (r <= b) fetch(r);
+        for (int r = rb; r < rb + C::NSLOT - 1; ++r) {
+            if (r <= re) fetch(r);
             cp_commit();
         }
-        for (int r = 0; r <= b; ++r) {
-            if (r + C::NSLOT - 1 <= b) fetch(r + C::NSLOT - 1);
+        for (int r = rb; r <= re; ++r) {
+            if (r + C::NSLOT - 1 <= re) fetch(r + C::NSLOT - 1);
             cp_commit();
             cp_wait<C::NSLOT - 1>();
             __syncwarp();
@@ -1231,12 +1335,14 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
                 const T *d = sl.tile + col0 * SD + ch * E;
 #pragma unroll
                 for (int t = 0; t < CPL; ++t)
-                    if (colmask >> t & 1u)
+                    if ((colmask >> t & 1u) && CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld, n, ld) &&
+                        CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld + E - 1, n, ld))
                         *reinterpret_cast<V *>(g + (long long)t * cstep * ld) = *reinterpret_cast<const V *>(d + t * cstep * SD);
             } else {
 #pragma unroll 8
                 for (int cc = 0; cc < kB; ++cc)
-                    if (c0 + cc < n && (!diag || lane <= cc)) A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
+                    if (c0 + cc < n && (!diag || lane <= cc) && CHK_TRI(sy, (r0 + lane) + (c0 + cc) * ld, n, ld))
+                        A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
             }
             __syncwarp();
         }

@@ -51,6 +51,14 @@ struct SolveArgs {
     int *ctl;
     long long *status;
     long long timeout_ns;
+    // the workspace allocations inv, yflag and ytag / xtag are carved from (bounds-checked builds)
+    const char *ws_data;
+    size_t ws_data_bytes;
+    const int *ws_iflags;
+    size_t ws_iflags_n;
+    const long long *ws_progress;
+    size_t ws_progress_n;
+    long long chk_cut;
 };
 
 template <int R>
@@ -134,16 +142,20 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
         const int i = e & (kW - 1), j = e / kW;
         double v = 0.0;
         if (j < nc) {
-            if (i <= j) v = (double)__ldg(a.L + c0 + i + (c0 + j) * ld);
+            if (i <= j && CHK_TRI(sy, c0 + i + (c0 + j) * ld, a.n, ld)) v = (double)__ldg(a.L + c0 + i + (c0 + j) * ld);
         } else if (i == j) {
             v = 1.0;
         }
         S.D[i][j] = v;
-        if (b >= 1) S.T[i][j] = (j < nc) ? (double)__ldg(a.L + c0 - kW + i + (c0 + j) * ld) : 0.0;
+        if (b >= 1)
+            S.T[i][j] = (j < nc && CHK_TRI(sy, c0 - kW + i + (c0 + j) * ld, a.n, ld))
+                            ? (double)__ldg(a.L + c0 - kW + i + (c0 + j) * ld) : 0.0;
     }
     double rhs[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) rhs[r] = (active && r < a.nr) ? (double)a.B[c0 + lane + r * a.ldb] : 0.0;
+    for (int r = 0; r < R; ++r)
+        rhs[r] = (active && r < a.nr && CHK_RECT(sy, c0 + lane + r * a.ldb, a.n, a.nr, a.ldb))
+                     ? (double)a.B[c0 + lane + r * a.ldb] : 0.0;
     __syncthreads();
 
     if (warp == 0) {
@@ -192,12 +204,14 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0;
-    const T *col = a.L + (c0 + (active ? lane : 0)) * ld;
+    const long long colo = (c0 + (active ? lane : 0)) * ld;
+    const T *col = a.L + colo;
     for (int p = warp; p <= b - 3; p += kSolveWarps) {
         const T *src = col + (long long)p * kW;
         double t[kW];
 #pragma unroll
-        for (int j = 0; j < kW; ++j) t[j] = active ? (double)__ldg(src + j) : 0.0;
+        for (int j = 0; j < kW; ++j)
+            t[j] = (active && CHK_TRI(sy, colo + (long long)p * kW + j, a.n, ld)) ? (double)__ldg(src + j) : 0.0;
         double yv[R];
         wait_block<R>(sy, a.ytag, ep64, p, who, yv);
 #pragma unroll
@@ -289,7 +303,8 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
     for (int e = threadIdx.x; e < kW * kW; e += kSolveThreads) {
         const int i = e / kW, j = e & (kW - 1);
         S.U[i][j] = __ldcg(inv + e);
-        S.T[j][i] = (has_next && j < nc && i < nc1) ? (double)__ldg(a.L + c0 + j + (q1 + i) * ld) : 0.0;
+        S.T[j][i] = (has_next && j < nc && i < nc1 && CHK_TRI(sy, c0 + j + (q1 + i) * ld, n, ld))
+                        ? (double)__ldg(a.L + c0 + j + (q1 + i) * ld) : 0.0;
     }
     double yv[R];
     wait_block<R>(sy, a.ytag, ep64, b, who, yv);
@@ -315,13 +330,15 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0;
-    const T *row = a.L + c0 + (active ? lane : 0);
+    const long long rowo = c0 + (active ? lane : 0);
+    const T *row = a.L + rowo;
     for (int q = a.nb - 1 - warp; q >= b + 3; q -= kSolveWarps) {
         const long long q0 = (long long)q * kW;
         const int ncq = (int)min((long long)kW, n - q0);
         double t[kW];
 #pragma unroll
-        for (int c = 0; c < kW; ++c) t[c] = (active && c < ncq) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
+        for (int c = 0; c < kW; ++c)
+            t[c] = (active && c < ncq && CHK_TRI(sy, rowo + (q0 + c) * ld, n, ld)) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
         double xv[R];
         wait_block<R>(sy, a.xtag, ep64, q, who, xv);
 #pragma unroll
@@ -337,7 +354,7 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
 #pragma unroll
         for (int cc = 0; cc < kRowsPerWarp; ++cc) {
             const int c = warp * kRowsPerWarp + cc;
-            t[cc] = (active && c < ncq) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
+            t[cc] = (active && c < ncq && CHK_TRI(sy, rowo + (q0 + c) * ld, n, ld)) ? (double)__ldg(row + (q0 + c) * ld) : 0.0;
         }
         double xv[R];
         wait_block<R>(sy, a.xtag, ep64, b + 2, who, xv);
@@ -392,7 +409,7 @@ __device__ void backward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lo
         for (int r = 0; r < R; ++r) {
             const double x = z[r] - part_sum(S, 0, r, lane);
             put_tagged(a.xtag + tag_at<R>(b, lane, r), x, ep64);
-            if (active && r < a.nr) a.B[c0 + lane + r * a.ldb] = (T)x;
+            if (active && r < a.nr && CHK_RECT(sy, c0 + lane + r * a.ldb, a.n, a.nr, a.ldb)) a.B[c0 + lane + r * a.ldb] = (T)x;
         }
     }
 }
@@ -408,10 +425,18 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs<T> a)
     sy.user_info = nullptr;
     sy.epoch = ld_relaxed_gpu(a.ctl + kCtlEpoch);
     sy.timeout_ns = a.timeout_ns;
+    sy.chk_cut = a.chk_cut;
     const long long ep64 = (long long)sy.epoch << 32;
+    // bounds-checked builds: the workspace regions inside their allocations
+    const bool ws_in = CHK_REGION(sy, a.inv, (size_t)a.nb * kW * kW * sizeof(double), a.ws_data, a.ws_data_bytes) &&
+                       CHK_REGION(sy, a.yflag, (size_t)a.nb * sizeof(int), a.ws_iflags, a.ws_iflags_n * sizeof(int)) &&
+                       CHK_REGION(sy, a.ytag, (size_t)a.nb * kW * R * 2 * sizeof(long long), a.ws_progress,
+                                  a.ws_progress_n * sizeof(long long)) &&
+                       CHK_REGION(sy, a.xtag, (size_t)a.nb * kW * R * 2 * sizeof(long long), a.ws_progress,
+                                  a.ws_progress_n * sizeof(long long));
 
     for (;;) {
-        if (threadIdx.x == 0) s_task = aborted(sy) ? -1 : atomicAdd(a.ctl + kCtlPairNext, 1);
+        if (threadIdx.x == 0) s_task = (!ws_in || aborted(sy)) ? -1 : atomicAdd(a.ctl + kCtlPairNext, 1);
         __syncthreads();
         const int t = s_task;
         if (t < 0 || t >= 2 * a.nb) break;
@@ -471,6 +496,13 @@ int launch_solve(const void *L, long long n, long long ld, void *B, long long ld
     a.ctl = sc.ctl;
     a.status = sc.status;
     a.timeout_ns = timeout_ns();
+    a.ws_data = sc.data;
+    a.ws_data_bytes = sc.data_bytes;
+    a.ws_iflags = sc.iflags;
+    a.ws_iflags_n = sc.iflags_cap;
+    a.ws_progress = sc.progress;
+    a.ws_progress_n = sc.progress_cap;
+    a.chk_cut = check_cut();
     const int grid = (int)std::min<long long>(2ll * nb, (long long)sm_count(dev) * occ[dev]);
     solve_kernel<T, R><<<grid, kSolveThreads, 0, stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;

@@ -65,6 +65,14 @@ struct Launch {
     long long *trace;       // optional timestamps, [2][npairs][nbmax][kTracePoints]
     long long timeout_ns;
     int skip_publish;       // test hook: wave blocks never release this block's panel (-1: none)
+    // the workspace allocations the problems' regions are carved from (bounds-checked builds)
+    const char *ws_data;
+    size_t ws_data_bytes;
+    const int *ws_iflags;
+    size_t ws_iflags_n;
+    const long long *ws_progress;
+    size_t ws_progress_n;
+    long long chk_cut;      // bounds-checked build: columns taken off each factor's declared extent
 };
 
 // Everything one task needs about its pair.
@@ -91,6 +99,7 @@ struct Wave {
     long long *final_done;      // final pass: tagged count of finished column tasks
     long long *trace_sweep, *trace_wave;  // this pair's rows, or null
     int skip_publish;                     // test hook (see Launch)
+    bool ok;                              // false: a region failed its bounds check; skip the task
     SyncArgs sync;
 };
 
@@ -145,6 +154,21 @@ __device__ Wave<T> make_wave(const Launch<T> &P, int j)
     w.sync.user_info = pr.info;
     w.sync.epoch = ld_relaxed_gpu(P.ctl + kCtlEpoch);
     w.sync.timeout_ns = P.timeout_ns;
+    w.sync.chk_cut = P.chk_cut;
+    w.ok = true;
+#ifdef CHM_CHECK
+    // the problem's regions inside the workspace allocations, and this pair's
+    // slice (or, for the final pass, the row data after the k slices) inside
+    // the problem's data region
+    w.ok = CHK_REGION(w.sync, pr.data, prob_data_bytes(nb, pr.k), P.ws_data, P.ws_data_bytes) &&
+           CHK_REGION(w.sync, pr.iflags, prob_iflags(nb, pr.k) * sizeof(int), P.ws_iflags,
+                      P.ws_iflags_n * sizeof(int)) &&
+           CHK_REGION(w.sync, pr.progress, prob_progress(nb, pr.k) * sizeof(long long), P.ws_progress,
+                      P.ws_progress_n * sizeof(long long)) &&
+           CHK_REGION(w.sync, d, q < pr.k ? rc.bytes : (size_t)nb * kW * sizeof(ChainRow), pr.data,
+                      prob_data_bytes(nb, pr.k)) &&
+           CHK_RECT(w.sync, (long long)q, (long long)pr.k + 1, 1, 1 << 30);
+#endif
     return w;
 }
 
@@ -321,7 +345,8 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
     long long *prog_me = w.progress + b;
     CHM_TRACE(0);
 
-    T uh = active ? w.V[c0 + lane] : T(0);
+    if (!CHK_RECT(sy, (long long)b, (long long)w.nb, 1, 1 << 30)) return;
+    T uh = (active && CHK_RECT(sy, c0 + lane, n, 1, n)) ? w.V[c0 + lane] : T(0);
 
     if (w.q == 0) {
         // Original-factor data of block b for wave 0: the diagonal and its
@@ -330,7 +355,8 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
         T x[kW];
 #pragma unroll
         for (int c = 0; c < kW; ++c)
-            x[c] = (lane <= c && c < ncols) ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
+            x[c] = (lane <= c && c < ncols && CHK_TRI(sy, c0 + lane + (c0 + c) * ld, n, ld))
+                       ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
         double dl = 1.0;
 #pragma unroll
         for (int c = 0; c < kW; ++c)
@@ -346,7 +372,9 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
         if (b >= 1) {
             const long long r0 = c0 - kW;
 #pragma unroll
-            for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(w.L + r0 + lane + (c0 + c) * ld) : T(0);
+            for (int c = 0; c < kW; ++c)
+                x[c] = (c < ncols && CHK_TRI(sy, r0 + lane + (c0 + c) * ld, n, ld))
+                           ? __ldcg(w.L + r0 + lane + (c0 + c) * ld) : T(0);
             double *rt = w.rtile + (size_t)(b - 1) * kW * kW;  // tile (b-1, b)
 #pragma unroll
             for (int c = 0; c < kW; ++c) __stcg(rt + (size_t)lane * kW + c, -(double)x[c]);
@@ -366,9 +394,10 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
             // the tile as the previous wave left it, fetched while the panel is pending
             if (prog_prev) CHM_WARP_WAIT(wait_ge(sy, prog_prev, ep64 + p + 1, who));
             T x[kW];
-            const T *src = w.L + (long long)p * kW + lane;
+            const long long o = (long long)p * kW + lane;
 #pragma unroll
-            for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
+            for (int c = 0; c < kW; ++c)
+                x[c] = (c < ncols && CHK_TRI(sy, o + (c0 + c) * ld, n, ld)) ? __ldcg(w.L + o + (c0 + c) * ld) : T(0);
 #pragma unroll
             for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
         }
@@ -416,10 +445,10 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
         }
         __syncwarp();
         {
-            T *dst = w.L + (long long)p * kW + lane;
+            const long long o = (long long)p * kW + lane;
 #pragma unroll
             for (int c = 0; c < kW; ++c)
-                if (c < ncols) __stcg(dst + (c0 + c) * ld, tile[c][lane]);
+                if (c < ncols && CHK_TRI(sy, o + (c0 + c) * ld, n, ld)) __stcg(w.L + o + (c0 + c) * ld, tile[c][lane]);
         }
         __syncwarp();
         staged = false;
@@ -428,9 +457,10 @@ __device__ void sweep_task(const Wave<T> &w, int b, unsigned char *sm)
                                         : 1;
             if (ready) {
                 T x[kW];
-                const T *src = w.L + (long long)(p + 1) * kW + lane;
+                const long long o = (long long)(p + 1) * kW + lane;
 #pragma unroll
-                for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
+                for (int c = 0; c < kW; ++c)
+                    x[c] = (c < ncols && CHK_TRI(sy, o + (c0 + c) * ld, n, ld)) ? __ldcg(w.L + o + (c0 + c) * ld) : T(0);
 #pragma unroll
                 for (int c = 0; c < kW; ++c) tile[c][lane] = x[c];
                 staged = true;
@@ -462,16 +492,20 @@ __device__ void unscale_task(const Wave<T> &w, int b)
     const int ncols = (int)min((long long)kW, n - c0);
     const long long ep64 = (long long)sy.epoch << 32;
     const long long who = b;
+    if (!CHK_RECT(sy, (long long)b, (long long)w.nb, 1, 1 << 30)) return;
     for (int p = 0; p < b; ++p) {
         CHM_WARP_WAIT(wait_ge(sy, w.progress_prev + b, ep64 + p + 1, who));
         const T e = (T)__ldcg(&w.chain_in[(size_t)p * kW + lane].e1);
-        T *src = w.L + (long long)p * kW + lane;
+        const long long o = (long long)p * kW + lane;
         T x[kW];
+        bool in[kW];
 #pragma unroll
-        for (int c = 0; c < kW; ++c) x[c] = (c < ncols) ? __ldcg(src + (c0 + c) * ld) : T(0);
+        for (int c = 0; c < kW; ++c) in[c] = c < ncols && CHK_TRI(sy, o + (c0 + c) * ld, n, ld);
+#pragma unroll
+        for (int c = 0; c < kW; ++c) x[c] = in[c] ? __ldcg(w.L + o + (c0 + c) * ld) : T(0);
 #pragma unroll
         for (int c = 0; c < kW; ++c)
-            if (c < ncols) __stcg(src + (c0 + c) * ld, x[c] * e);
+            if (in[c]) __stcg(w.L + o + (c0 + c) * ld, x[c] * e);
     }
     // count this task done (the pair's wave block waits for all of them);
     // the count word is tagged with the epoch, so it restarts every launch
@@ -501,10 +535,11 @@ __device__ void unscale_diag(const Wave<T> &w, int warp)
         CHM_WARP_WAIT(wait_eq(sy, w.dflag_prev + b, epoch, who));
         if (lane < ncols) {
             const T e = (T)__ldcg(&w.chain_in[(size_t)b * kW + lane].e1);
-            T *src = w.L + c0 + lane;
+            const long long o = c0 + lane;
 #pragma unroll
             for (int c = 0; c < kW; ++c)
-                if (lane < c && c < ncols) __stcg(src + (c0 + c) * ld, __ldcg(src + (c0 + c) * ld) * e);
+                if (lane < c && c < ncols && CHK_TRI(sy, o + (c0 + c) * ld, n, ld))
+                    __stcg(w.L + o + (c0 + c) * ld, __ldcg(w.L + o + (c0 + c) * ld) * e);
         }
     }
     // the pair is done only when its column tasks are: idle sweep warps stop
@@ -556,7 +591,8 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
             const int ncols = (int)min((long long)kW, n - c0);
 #pragma unroll
             for (int c = 0; c < kW; ++c)
-                if (lane <= c && c < ncols) __stcg(w.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
+                if (lane <= c && c < ncols && CHK_TRI(sy, c0 + lane + (c0 + c) * ld, n, ld))
+                    __stcg(w.L + c0 + lane + (c0 + c) * ld, S.DT[c][lane]);
             __syncwarp();
             if (lane == 0) st_release_gpu(w.dflag + b, epoch);
             CHM_WTRACE(b, 13);
@@ -591,7 +627,7 @@ __device__ void wave_io(const Wave<T> &w, WaveSmem<T> &S)
                 if (b >= 2) {
                     S.zpart[s][lane] = zc;
                 } else {
-                    S.zpart[s][lane] = (c0 + lane < n) ? (double)w.V[c0 + lane] : 0.0;
+                    S.zpart[s][lane] = (c0 + lane < n && CHK_RECT(sy, c0 + lane, n, 1, n)) ? (double)w.V[c0 + lane] : 0.0;
                 }
                 cp_async_commit();
                 cp_async_wait();
@@ -785,7 +821,7 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
         // u_hat entering the block (from the sweep of its last off-diagonal tile)
         T uh = T(0);
         if (b == 0) {
-            uh = active ? w.V[c0 + lane] : T(0);
+            uh = (active && CHK_RECT(sy, c0 + lane, n, 1, n)) ? w.V[c0 + lane] : T(0);
         } else {
             double u = 0.0;
             if (!warp_wait_tagged(sy, w.ctag + ((size_t)b * kW + lane) * 2, ep64, who, &u)) return;
@@ -798,7 +834,8 @@ __device__ void wave_diag(const Wave<T> &w, WaveSmem<T> &S)
         T x[kW];
 #pragma unroll
         for (int c = 0; c < kW; ++c)
-            x[c] = (lane <= c && c < ncols) ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
+            x[c] = (lane <= c && c < ncols && CHK_TRI(sy, c0 + lane + (c0 + c) * ld, n, ld))
+                       ? __ldcg(w.L + c0 + lane + (c0 + c) * ld) : T(0);
         // the tile buffer is free once warp D has finished the previous block
         CHM_SEQ_WAIT(&S.fseq, b);
 #pragma unroll
@@ -928,6 +965,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
     sy.user_info = nullptr;
     sy.epoch = 0;
     sy.timeout_ns = P.timeout_ns;
+    sy.chk_cut = P.chk_cut;
 
     if (threadIdx.x == 0) {
         atomicAdd(ctl + kCtlStarted, 1);
@@ -998,7 +1036,9 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             const int j = s_pair;
             if (j < 0) break;
             const Wave<T> w = make_wave(P, j);
-            if (w.unscale) unscale_diag<T>(w, warp);
+            if (!w.ok) {
+                // a region failed its bounds check (recorded, the launch is aborting)
+            } else if (w.unscale) unscale_diag<T>(w, warp);
             else if (warp == 0) wave_chain<T>(w, S);
             else if (warp == 1) wave_coef<T>(w, S);
             else if (warp == 2) wave_diag<T>(w, S);
@@ -1019,6 +1059,7 @@ __global__ void __launch_bounds__(128, 3) wave_kernel(Launch<T> P)
             const int j = take_task(P, group, ep64, &b);
             if (j >= 0) {
                 const Wave<T> w = make_wave(P, j);
+                if (!w.ok) break;
                 if (w.unscale) unscale_task<T>(w, b);
                 else sweep_task<T>(w, b, sm);
                 idle_since = -1;

@@ -181,3 +181,63 @@ def test_solve_argument_errors_without_gpu():
     # nothing to do: no CUDA call
     assert chm.chm_solve(None, 0, 1, None, 1, 3, chm.CHM_F64, None) == chm.CHM_OK
     assert chm.chm_solve(8, 5, 5, None, 5, 0, chm.CHM_F64, None) == chm.CHM_OK
+
+
+def test_checked_build_exports_the_same_symbols_and_reports_itself():
+    """The bounds-checked variant (-DCHM_CHECK) is built beside the library,
+    exports every declared symbol, and answers the "checked" and
+    "check_cut" settings that only it accepts."""
+    chm_build.build()
+    plain = ctypes.CDLL(chm_build.LIB)
+    missing = [n for n in declared_functions() if not hasattr(ctypes.CDLL(chm_build.LIB_CHECK), n)]
+    assert not missing, missing
+    v = ctypes.c_int64(-1)
+    plain.chm_config_get.argtypes = [ctypes.c_char_p, ctypes.c_void_p]
+    plain.chm_config_set.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+    assert plain.chm_config_get(b"checked", ctypes.byref(v)) == 0 and v.value == 0
+    assert plain.chm_config_set(b"check_cut", 1) == chm.CHM_ERR_ARG
+    with chm.checked_library(build_if_missing=False):
+        assert chm.config_get("checked") == 1
+        assert chm.chm_config_set(b"check_cut", -1) == chm.CHM_ERR_ARG
+        assert chm.chm_config_set(b"check_cut", 2) == chm.CHM_OK
+        assert chm.config_get("check_cut") == 2
+        assert chm.chm_config_set(b"check_cut", 0) == chm.CHM_OK
+        assert "BOUNDS" in chm.chm_status_string(chm.CHM_ERR_BOUNDS)
+    assert chm.config_get("checked") == 0
+
+
+def test_tuning_cache_file_round_trip_and_lookup(tmp_path):
+    """chm_tune_load / chm_tune_save / chm_tune_clear without a GPU: a loaded
+    entry decides the path of its (dtype, floor(log2 n), ceil(log2 k))
+    bucket, an explicit "path" setting still wins, a malformed file changes
+    nothing, and a saved cache reads back to the same entries."""
+    assert chm.chm_tune_clear() == chm.CHM_OK
+    # float32 n in [2048, 4096), k in (4, 8]: the built-in rule takes the wave kernel (8 MB < 32 MB)
+    assert chm.path_for(3000, 6, chm.CHM_F32_MIXED) == chm.PATH_WAVE
+    f = tmp_path / "tune.txt"
+    f.write_text("chm-tune 1\n%d 11 3 2 4 6 32 123456\n" % chm.CHM_F32_MIXED)
+    assert chm.chm_tune_load(str(f)) == chm.CHM_OK
+    assert chm.path_for(3000, 6, chm.CHM_F32_MIXED) == chm.PATH_PASS
+    assert chm.path_for(2048, 5, chm.CHM_F32_MIXED) == chm.PATH_PASS
+    assert chm.path_for(2047, 6, chm.CHM_F32_MIXED) == chm.PATH_WAVE   # the n bucket below
+    assert chm.path_for(3000, 9, chm.CHM_F32_MIXED) == chm.PATH_WAVE   # next k bucket
+    assert chm.path_for(3000, 6, chm.CHM_F64) == chm.PATH_WAVE         # other dtype
+    chm.config_set("path", chm.PATH_WAVE)
+    try:
+        assert chm.path_for(3000, 6, chm.CHM_F32_MIXED) == chm.PATH_WAVE
+    finally:
+        chm.config_set("path", chm.PATH_AUTO)
+    out = tmp_path / "saved.txt"
+    assert chm.chm_tune_save(str(out)) == chm.CHM_OK
+    assert out.read_text() == "chm-tune 1\n%d 11 3 2 4 6 32 123456\n" % chm.CHM_F32_MIXED
+    for bad in ("chm-tune 2\n", "chm-tune 1\n1 11 3 2 4 6 32\n", "chm-tune 1\n1 11 3 3 4 6 32 1\n",
+                "chm-tune 1\n1 11 3 2 17 6 32 1\n", "chm-tune 1\n7 11 3 2 4 6 32 1\n"):
+        f.write_text(bad)
+        assert chm.chm_tune_load(str(f)) == chm.CHM_ERR_ARG, bad
+    assert chm.path_for(3000, 6, chm.CHM_F32_MIXED) == chm.PATH_PASS   # unchanged
+    assert chm.chm_tune_load(str(tmp_path / "missing.txt")) == chm.CHM_ERR_ARG
+    assert chm.chm_tune(0, 1, chm.CHM_F64, None) == chm.CHM_ERR_ARG
+    assert chm.chm_tune(10, 0, chm.CHM_F64, None) == chm.CHM_ERR_ARG
+    assert chm.chm_tune(10, 1, 5, None) == chm.CHM_ERR_ARG
+    assert chm.chm_tune_clear() == chm.CHM_OK
+    assert chm.path_for(3000, 6, chm.CHM_F32_MIXED) == chm.PATH_WAVE

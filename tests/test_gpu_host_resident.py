@@ -5,8 +5,11 @@ from host memory (abstract, Sec. 4 and Sec. 5), so the factor's size is
 bounded by host memory.  Here the kernel reads and writes L in place in
 page-locked host memory across the CPU-GPU link; the device holds only the
 O(n k) workspace.  The arithmetic is the same as for a device-resident
-factor, so results must be bit-identical to it, and within the float64
-tolerance of the oracle.  Pageable host memory is rejected on the host.
+factor on the same path (the wave kernel or the pass kernels), so results
+must be bit-identical to it, and within the float64 tolerance of the
+oracle.  Under the automatic rule a host factor of order >= 64 takes the
+pass kernels (three crossings of the link per pass of up to 16 vectors).
+Pageable host memory is rejected on the host.
 """
 from __future__ import annotations
 
@@ -29,6 +32,8 @@ def _device():
         pytest.skip("no CUDA device")
     chm.load(build_if_missing=True)
     torch.cuda.set_device(0)
+    yield
+    chm.config_set("path", chm.PATH_AUTO)
 
 
 def pinned(t):
@@ -50,23 +55,39 @@ def test_host_resident_matches_device_resident(n, k, pad, dtype):
     seed = 9100 + n + k
     L, V = problem(n, k, pad, dtype, seed)
     sig = inputs.sigma_vector(k, seed).tolist()
-    dev_L = L.cuda()
-    assert chm.modify(dev_L, V.cuda(), sig) == chm.CHM_OK
-    assert chm.status_sync()[0] == chm.CHM_OK
-    host_L, host_V = pinned(L), pinned(V)
-    assert chm.modify(host_L, host_V, sig) == chm.CHM_OK
-    assert chm.status_sync()[0] == chm.CHM_OK
-    assert torch.equal(host_L, dev_L.cpu()), (n, k)
-    assert torch.equal(host_V, V)  # V is read only
+    ref = None
     if dtype == torch.float64:
         ref = L.numpy().copy()
         assert oracle.modify_b(ref, V.numpy(), sig)[0] == 0
-        assert colscaled_err(host_L.numpy(), ref) <= TOL_F64
+    by_path = {}
+    for path in (chm.PATH_WAVE, chm.PATH_PASS):
+        chm.config_set("path", path)
+        dev_L = L.cuda()
+        assert chm.modify(dev_L, V.cuda(), sig) == chm.CHM_OK
+        assert chm.status_sync()[0] == chm.CHM_OK
+        host_L, host_V = pinned(L), pinned(V)
+        assert chm.modify(host_L, host_V, sig) == chm.CHM_OK
+        assert chm.status_sync()[0] == chm.CHM_OK
+        assert torch.equal(host_L, dev_L.cpu()), (n, k, path)
+        assert torch.equal(host_V, V)  # V is read only
+        if ref is not None:
+            assert colscaled_err(host_L.numpy(), ref) <= TOL_F64
+        by_path[path] = host_L
+    # the automatic rule: a host factor of order >= 64 on the pass kernels
+    chm.config_set("path", chm.PATH_AUTO)
+    host_L = pinned(L)
+    assert chm.modify(host_L, pinned(V), sig) == chm.CHM_OK
+    assert chm.status_sync()[0] == chm.CHM_OK
+    assert torch.equal(host_L, by_path[chm.PATH_PASS if n >= 64 else chm.PATH_WAVE]), (n, k)
 
 
 def test_mixed_residency_and_noalloc():
+    """One operand on the host and the other on the device, and the
+    no-allocation entry point (the wave kernel) with a host factor; every
+    call on the wave kernel so that the results are bit-identical."""
     n, k = 700, 9
     L, V = problem(n, k, 0, torch.float64, 77)
+    chm.config_set("path", chm.PATH_WAVE)
     ref = L.cuda()
     assert chm.modify(ref, V.cuda(), 1) == chm.CHM_OK
     # L on the host, V on the device, and the reverse
@@ -85,6 +106,7 @@ def test_mixed_residency_and_noalloc():
     torch.cuda.synchronize()
     assert info.tolist() == [0, -1]
     assert torch.equal(c, ref.cpu())
+    chm.config_set("path", chm.PATH_AUTO)
 
 
 def test_batch_with_host_resident_factors():

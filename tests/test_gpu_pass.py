@@ -14,7 +14,7 @@ import torch
 
 import oracle
 from paper_1011_1173_gb300 import chm, inputs
-from tests.common import TOL_F64, colscaled_err
+from tests.common import TOL_F64, accuracy_as_serial, colscaled_err, tol_mixed
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +30,7 @@ def _device():
     chm.config_set("path", chm.PATH_AUTO)
     chm.config_set("pass_kb", 0)
     chm.config_set("pass_d", 0)
+    chm.config_set("pass_seg", 0)
 
 
 def run(L, V, sig, dtype=torch.float64):
@@ -62,6 +63,44 @@ def test_vectors_per_pass_and_lookahead(kb, d):
             assert st == ost == 0
             assert colscaled_err(g, o) <= TOL_F64, (n, k, kb, d)
     finally:
+        chm.config_set("pass_kb", 0)
+        chm.config_set("pass_d", 0)
+
+
+@pytest.mark.parametrize("seg", [1, 2, 5])
+@pytest.mark.parametrize("kb,d", [(1, 2), (3, 4), (16, 3)])
+def test_sweep_segments_restart_from_residuals(seg, kb, d):
+    """Short sweep segments (every seg row blocks a column's carry is rebuilt
+    from the substitution's partial residual and the prefix Gram's LDL^T
+    there), so that most tiles of these shapes lie in restarted segments:
+    float64 against the oracle, float storage against the emulation."""
+    chm.config_set("pass_seg", seg)
+    chm.config_set("pass_kb", kb)
+    chm.config_set("pass_d", d)
+    try:
+        for n, k, pad in [(200, 16, 0), (611, 19, 3), (1025, 2, 1)]:
+            seed = 31 + n + k + seg
+            L = inputs.spd_factor(n, seed, ld=n + pad).numpy()
+            V = inputs.update_block(n, k, seed, scale=0.5 / np.sqrt(n * k)).numpy()
+            sig = inputs.sigma_vector(k, seed).numpy()
+            st, info, g = run(L, V, sig)
+            ost, _, o = ref(L, V, sig)
+            assert st == ost == 0
+            err = colscaled_err(g, o)
+            assert err <= TOL_F64, (n, k, seg, kb, d, err)
+            L32, V32 = L.astype(np.float32), V.astype(np.float32)
+            st, info, g32 = run(L32, V32, sig, dtype=torch.float32)
+            o32 = np.array(L32, copy=True)
+            assert oracle.modify_mixed32(o32, np.ascontiguousarray(V32), sig, n=n, group=kb)[0] == 0
+            o64 = np.array(L32, dtype=np.float64, copy=True)
+            assert oracle.modify_b(o64, np.ascontiguousarray(V32, dtype=np.float64), sig, n=n)[0] == 0
+            dm, e_gpu, e_emu = colscaled_err(g32, o32, n=n), colscaled_err(g32, o64, n=n), colscaled_err(o32, o64, n=n)
+            print("seg=%d kb=%d d=%d n=%d k=%d: f64 %.2e; mixed |gpu-emu| %.2e (bound %.2e), gpu %.2e emu %.2e"
+                  % (seg, kb, d, n, k, err, dm, tol_mixed(n, k), e_gpu, e_emu))
+            assert st == 0 and dm <= tol_mixed(n, k)
+            assert accuracy_as_serial(e_gpu, e_emu)
+    finally:
+        chm.config_set("pass_seg", 0)
         chm.config_set("pass_kb", 0)
         chm.config_set("pass_d", 0)
 
