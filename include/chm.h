@@ -406,9 +406,9 @@ int chm_microbench(int which, double *out, int nout);
  *         factor once for the whole block of vectors.
  * The automatic rule takes the pass kernels when the factor's upper
  * triangle is at least 32 MB (float) or 256 MB with k <= 2 (double), and
- * for every factor of order >= 64 in page-locked host memory (it then
- * crosses the CPU-GPU link three times per pass of up to 16 vectors; the
- * wave kernel re-reads it once per vector).
+ * for a factor of order >= 64 in page-locked host memory modified by two or
+ * more vectors (it then crosses the CPU-GPU link three times per pass of up
+ * to 16 vectors; the wave kernel twice per vector).
  * chm_config_get also answers "pass_d_f32" and "pass_d_f64" (the values in
  * effect) and "checked" (1 in the bounds-checked build).  The bounds-checked
  * build also takes "check_cut" (>= 0, default 0): its checks treat each

@@ -162,12 +162,14 @@ __device__ __forceinline__ bool chk_region(const SyncArgs &s, const void *p, siz
 #endif
 
 // One thread waits until ready() holds.  ready() polls with relaxed loads
-// (cheap, no ordering) under exponential backoff; once it holds, acquire()
+// (cheap, no ordering) under exponential backoff up to max_ns between polls
+// (the sleep is a hint the hardware may shorten); once it holds, acquire()
 // performs the single acquiring load that orders this thread's later reads
 // after the writer's release.  Returns false if the launch is being aborted
 // or the wait ran out of time (then recorded as CHM_ERR_TIMEOUT, info = who).
 template <typename F, typename A>
-__device__ __forceinline__ bool bounded_wait(const SyncArgs &s, F ready, A acquire, long long who)
+__device__ __forceinline__ bool bounded_wait(const SyncArgs &s, F ready, A acquire, long long who,
+                                             unsigned max_ns = 256)
 {
     if (ready()) {
         acquire();
@@ -177,7 +179,7 @@ __device__ __forceinline__ bool bounded_wait(const SyncArgs &s, F ready, A acqui
     unsigned ns = 16;
     for (unsigned it = 1;; ++it) {
         __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (ns < max_ns) ns <<= 1;
         if (ready()) {
             acquire();
             return true;

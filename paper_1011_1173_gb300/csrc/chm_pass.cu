@@ -78,10 +78,12 @@ int path_setting()
 // The built-in rule: the pass path once the factor is larger than about a
 // third of L2 (where the wave kernel's waves start to re-stream it); in
 // float64 only for few vectors, where the wave kernel's chain, not the FP64
-// rate, bounds it; and for a factor in page-locked host memory.
+// rate, bounds it; and for a factor in page-locked host memory with two or
+// more vectors (the pass crosses the CPU-GPU link three times per block of
+// up to 16 vectors, the wave kernel twice per vector).
 static bool rule_pass(long long n, long long k, int dtype, bool host_factor)
 {
-    if (host_factor) return n >= 64;
+    if (host_factor) return n >= 64 && k >= 2;
     const double bytes = (double)(dtype == CHM_F64 ? 8 : 4) * n * n / 2;
     if (dtype == CHM_F64) return bytes >= 256e6 && k <= 2;
     return bytes >= 32e6;

@@ -537,7 +537,10 @@ __device__ __forceinline__ bool mb_wait(const SyncArgs &sy, unsigned long long *
     return true;
 }
 
-// Warps of the forward-substitution kernel and the chain block's roles.
+// Warps of the forward-substitution kernel and the chain block's roles: the
+// critical warp, the W warp, seven near warps (the last one, when no near
+// offset needs it, a second publisher), the far-sum stager, the loader and
+// the publisher.
 constexpr int kTrsmWarps = 12;
 constexpr int kWCrit = 0, kWZhat = 1, kWNear0 = 2;
 constexpr int kNearWarps = kTrsmWarps - 5;  // warps 2 .. 8
@@ -578,7 +581,7 @@ struct ChainSmem {
     T Tn[C::NEAR][C::RT][RW];             // F_{b-j,b}^T P_{b-j} per near offset j
     T Z[C::RZ][RW];                       // W_b
     T F[C::RF][RW];                       // far sums Zf_b
-    T w[RW];                              // W warp's work vector
+    T w[RW];                              // the W warp's work vector
     // full / empty rings: stage (G, Dinv), W, P, far sums; near warps' steps
     unsigned long long st_full[C::RS], st_empty[C::RS];
     unsigned long long w_full[C::RZ], w_empty[C::RZ];
@@ -645,8 +648,50 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }                                                                                      \
     } while (0)
 
+    // Publication of P for the workers: the blocks m = first, first + step, ...
+    // are stored, then one flag per block is released after its values.  The
+    // fence that orders them costs about as much as a chain step, so the
+    // last near warp, when no near offset needs it, takes every other block.
+    const int npub = nnw < kNearWarps ? 2 : 1;
+    auto publish = [&](int first, int step) {
+        for (int m = first; m < nb; m += step) {
+            MW(S.p_full, m, C::RP, m);
+            T v[KB];
+            row_load<T, KB>(S.P[m % C::RP], lane, v);
+            __syncwarp();
+            mb_arrive(&S.p_empty[m % C::RP]);
+            T *plain = A.P + ((size_t)m * kB + lane) * KB;
+#pragma unroll
+            for (int q = 0; q < KB; ++q) __stcg(plain + q, v[q]);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                st_release_gpu(A.pflag + m, A.epoch);
+            }
+            if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 4] = global_ns();
+        }
+    };
+
     if (warp == kWLoad) {
+        // G^(1..c) and Dinv of a step, prefetched to L2 16 steps ahead (the
+        // copies into the stage ring then come from L2 while the workers
+        // stream the factor from HBM)
+        constexpr int PF = 16;
+        auto prefetch = [&](int m) {
+            if (m >= nb) return;
+            constexpr int LINE = 128 / (int)sizeof(T);  // elements per 128-byte line
+            for (int j = 1; j <= cc && j <= m; ++j) {
+                const T *g = A.G + ((size_t)(j - 1) * nb + m) * kB * kB;
+                for (int e = lane * LINE; e < kB * kB; e += 32 * LINE) prefetch_l2(g + e);
+            }
+            if (m + 1 < nb) {
+                const T *di = A.Dinv + (size_t)(m + 1) * kB * kB;
+                for (int e = lane * LINE; e < kB * kB; e += 32 * LINE) prefetch_l2(di + e);
+            }
+        };
+        for (int m = 0; m < PF; ++m) prefetch(m);
         for (int m = 0; m < nb; ++m) {
+            prefetch(m + PF);
             const int st = m % C::RS;
             if (m >= C::RS) MW(S.st_empty, m - C::RS, C::RS, -10);
             if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 3] = global_ns();
@@ -679,7 +724,10 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
     } else if (warp >= kWNear0 && warp < kWNear0 + kNearWarps) {
         const int t = warp - kWNear0;
-        if (t >= nnw) return;
+        if (t >= nnw) {
+            if (t == kNearWarps - 1 && npub == 2) publish(1, 2);
+            return;
+        }
         // this warp's offsets' tiles, staged RS - 1 steps ahead (the factor as
         // it entered the pass: nothing to wait for)
         auto stage = [&](int m) {
@@ -716,6 +764,15 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
                 if (b >= nb) break;
                 T out[KB];
                 lane_mv<T, KB>(S.near[j - cc - 1][m % C::RS], pm, out, lane);
+                // the running sum of block b's near terms, offsets d, d - 1, ..., j:
+                // offset j + 1's warp left the terms above in its slot at step m - 1
+                if (j < d && j + 1 <= b) {
+                    MW(S.t_full[(j - cc) % kNearWarps], m - 1, C::RT, b);
+                    T up[KB];
+                    row_load<T, KB>(S.Tn[j - cc][b % C::RT], lane, up);
+#pragma unroll
+                    for (int q = 0; q < KB; ++q) out[q] += up[q];
+                }
                 row_store<T, KB>(S.Tn[j - cc - 1][b % C::RT], lane, out);
             }
             __syncwarp();
@@ -725,6 +782,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             if (A.trace && t == nnw - 1 && lane == 0) A.trace[(size_t)m * 16 + 12] = global_ns();
         }
     } else if (warp == kWZhat) {
+        T *wv = S.w;
         // Dinv_0 for W_0
         stage_dense(S.Di0, A.Dinv, lane);
         cp_commit();
@@ -746,16 +804,16 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
                     w[q] = (r0 + lane < n && q < A.kb && CHK_RECT(sy, r0 + lane + q * A.ldv, n, A.kb, A.ldv))
                                ? A.V[r0 + lane + q * A.ldv] : T(0);
             }
-            for (int j = cc + 1; j <= d && j <= b; ++j) {
-                const int t = (j - cc - 1) % kNearWarps;
-                MW(S.t_full[t], b - j, C::RT, b);
+            if (cc + 1 <= d && cc + 1 <= b) {
+                // the near terms, summed by the near warps (offset c + 1 holds all of them)
+                MW(S.t_full[0], b - cc - 1, C::RT, b);
                 T tn[KB];
-                row_load<T, KB>(S.Tn[j - cc - 1][b % C::RT], lane, tn);
+                row_load<T, KB>(S.Tn[0][b % C::RT], lane, tn);
 #pragma unroll
                 for (int q = 0; q < KB; ++q) w[q] -= tn[q];
             }
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 11] = global_ns();
-            row_store<T, KB>(S.w, lane, w);
+            row_store<T, KB>(wv, lane, w);
             __syncwarp();
             const T *Di = S.Di0;
             if (b >= 1) {
@@ -764,7 +822,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             }
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 6] = global_ns();
             T out[KB];
-            lane_mv<T, KB>(Di, S.w, out, lane);
+            lane_mv<T, KB>(Di, wv, out, lane);
             // W_{b - RZ}'s slot is free once the critical warp has used it
             if (b >= C::RZ) MW(S.w_empty, b - C::RZ, C::RZ, b);
             row_store<T, KB>(S.Z[b % C::RZ], lane, out);
@@ -807,24 +865,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 2] = global_ns();
         }
     } else if (warp == kWPub) {
-        for (int m = 0; m < nb; ++m) {
-            MW(S.p_full, m, C::RP, m);
-            T v[KB];
-            row_load<T, KB>(S.P[m % C::RP], lane, v);
-            __syncwarp();
-            mb_arrive(&S.p_empty[m % C::RP]);
-            T *plain = A.P + ((size_t)m * kB + lane) * KB;
-#pragma unroll
-            for (int q = 0; q < KB; ++q) __stcg(plain + q, v[q]);
-            // one flag per block (the workers poll these words only), released
-            // after the block's values
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                st_release_gpu(A.pflag + m, A.epoch);
-            }
-            if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 4] = global_ns();
-        }
+        publish(0, npub);
     }
 #undef MW
 }
@@ -893,10 +934,15 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
                 const unsigned not_ready = __ballot_sync(0xffffffffu, f != A.epoch);
                 int got = not_ready ? __ffs(not_ready) - 1 : 32;
                 if (got == 0) {
-                    // the next one is not out yet: lane 0 waits on its flag alone
+                    // the next one is not out yet: lane 0 waits on its flag
+                    // alone, polling often only near the block's last tiles
+                    // (the far sum is due when the chain reaches b - d; a
+                    // worker further back catches up in one burst)
+                    const unsigned max_ns = r + 4 >= nfar ? 64u : 1024u;
                     int ok = 1;
                     if (lane == 0)
-                        ok = bounded_wait(sy, [&] { return ld_relaxed_gpu(A.pflag + r) == A.epoch; }, [] {}, b) ? 1 : 0;
+                        ok = bounded_wait(sy, [&] { return ld_relaxed_gpu(A.pflag + r) == A.epoch; }, [] {}, b, max_ns)
+                                 ? 1 : 0;
                     if (!__shfl_sync(0xffffffffu, ok, 0)) {
                         cp_wait<0>();
                         return;

@@ -7,8 +7,9 @@ page-locked host memory across the CPU-GPU link; the device holds only the
 O(n k) workspace.  The arithmetic is the same as for a device-resident
 factor on the same path (the wave kernel or the pass kernels), so results
 must be bit-identical to it, and within the float64 tolerance of the
-oracle.  Under the automatic rule a host factor of order >= 64 takes the
-pass kernels (three crossings of the link per pass of up to 16 vectors).
+oracle.  Under the automatic rule a host factor of order >= 64 modified by
+k >= 2 vectors takes the pass kernels (three crossings of the link per pass
+of up to 16 vectors, against two per vector for the wave kernel).
 Pageable host memory is rejected on the host.
 """
 from __future__ import annotations
@@ -73,12 +74,12 @@ def test_host_resident_matches_device_resident(n, k, pad, dtype):
         if ref is not None:
             assert colscaled_err(host_L.numpy(), ref) <= TOL_F64
         by_path[path] = host_L
-    # the automatic rule: a host factor of order >= 64 on the pass kernels
+    # the automatic rule: a host factor of order >= 64 with k >= 2 on the pass kernels
     chm.config_set("path", chm.PATH_AUTO)
     host_L = pinned(L)
     assert chm.modify(host_L, pinned(V), sig) == chm.CHM_OK
     assert chm.status_sync()[0] == chm.CHM_OK
-    assert torch.equal(host_L, by_path[chm.PATH_PASS if n >= 64 else chm.PATH_WAVE]), (n, k)
+    assert torch.equal(host_L, by_path[chm.PATH_PASS if n >= 64 and k >= 2 else chm.PATH_WAVE]), (n, k)
 
 
 def test_mixed_residency_and_noalloc():
