@@ -104,7 +104,7 @@ struct PassSpace {
     // on the element type and the order), the (nb, d, seg) it was built for
     // (nb < 0: none; reset whenever the buffer is allocated) and its length
     const void *task_at = nullptr;
-    int task_nb = -1, task_d = -1, task_seg = -1, task_count = 0;
+    int task_nb = -1, task_d = -1, task_seg = -1, task_count = 0, post_count = 0;
 };
 // What a single-factor modification runs: the path and the pass kernels' parameters.
 struct PassChoice {
@@ -112,6 +112,7 @@ struct PassChoice {
     int kb;    // vectors per pass, 1 .. 16
     int d;     // lookahead of the substitution chain (each instantiation clamps it further)
     int seg;   // row blocks per sweep segment (0: by the order)
+    int fused; // 1: the substitution kernel's workers also form the coefficients and sweep (up to 8 vectors per pass)
 };
 // The choice for a modification of this shape: explicit settings, else the
 // tuner's candidate while it times one, else the tuning cache (device

@@ -22,6 +22,7 @@ std::atomic<int> g_path{0};      // 0 automatic, 1 wave kernel, 2 pass kernels
 std::atomic<int> g_pass_kb{0};   // vectors per pass (0: the largest, 16)
 std::atomic<int> g_pass_d{0};    // lookahead of the substitution chain (0: per type)
 std::atomic<int> g_pass_seg{0};  // row blocks per sweep segment (0: by the order)
+std::atomic<int> g_pass_fused{-1};  // 1 fused passes (up to 8 vectors), 0 the six-kernel pass (-1: default, 1)
 std::atomic<long long> g_check_cut{0};  // bounds-checked build: columns taken off a factor's extent
 
 int env_or(const char *name, int dflt)
@@ -48,6 +49,14 @@ static int seg_setting()
 {
     const int v = g_pass_seg.load();
     return v > 0 ? v : std::max(0, env_or("CHM_PASS_SEG", 0));
+}
+
+static int fused_setting()
+{
+    const int v = g_pass_fused.load();
+    if (v >= 0) return v;
+    const char *e = getenv("CHM_PASS_FUSED");
+    return e ? (atoi(e) != 0) : 1;
 }
 
 static int clamp_kb(int v) { return std::max(1, std::min(pass::kMaxKb, v)); }
@@ -106,6 +115,7 @@ PassChoice choose_path(long long n, long long k, int dtype, bool host_factor)
     c.kb = clamp_kb(c.kb);
     c.d = clamp_d(c.d, dtype);
     c.seg = std::max(0, c.seg);
+    c.fused = fused_setting();
     return c;
 }
 
@@ -119,7 +129,7 @@ bool use_pass_path(long long n, long long k, int dtype, bool host_factor)
 namespace {
 
 struct PassLayout {
-    size_t P, pflag, Ztag, Dinv, G, gram, H, coef, escale, dfac, snap, rst, tasks, ctl, bytes;
+    size_t P, Ptag, Htag, cflag, wprog, Ztag, Dinv, G, gram, H, coef, escale, dfac, snap, rst, tasks, post, ctl, bytes;
     int seg, nbound;  // row blocks per sweep segment; segment boundaries (the snapshots' count)
     size_t ntask_max;
 };
@@ -136,7 +146,10 @@ PassLayout pass_layout(long long n, int elt, int seg)
     // the tagged words and control words first: they are zeroed on
     // allocation (tag 0 matches no pass, whose epochs start at 1)
     const size_t words = elt / 4;
-    l.pflag = x; x = al(x + nb * 4);
+    l.Ptag = x; x = al(x + rows * KB * 2 * 8);
+    l.Htag = x; x = al(x + nb * KB * KB * 2 * 8);
+    l.cflag = x; x = al(x + nb * 4);
+    l.wprog = x; x = al(x + nb * 8);
     l.Ztag = x; x = al(x + rows * KB * words * 8);
     l.ctl = x; x = al(x + pass::kCtlInts * 4);
     l.P = x; x = al(x + rows * KB * elt);
@@ -154,6 +167,7 @@ PassLayout pass_layout(long long n, int elt, int seg)
     l.rst = x; x = al(x + (size_t)l.nbound * KB * (KB + 1) / 2 * 8);
     l.ntask_max = nb * (size_t)(1 + l.nbound);
     l.tasks = x; x = al(x + l.ntask_max * 8);
+    l.post = x; x = al(x + (nb + l.ntask_max) * 8);
     l.bytes = x;
     return l;
 }
@@ -231,37 +245,53 @@ int pass_setup(int dev, int *sweep_bps)
 // with the element type and the order) or (nb, d, seg) differs from the one
 // the workspace holds: the copy is ordered before this pass's kernels on
 // the stream, and every earlier pass has read its table by then.
-int sweep_tasks(PassSpace &ps, int nb, int d, int seg, int2 *dst, int *ntasks, cudaStream_t s)
+int sweep_tasks(PassSpace &ps, int nb, int d, int seg, int2 *dst, int2 *post, int *ntasks, int *npost,
+                cudaStream_t s)
 {
     if (!(ps.task_at == dst && ps.task_nb == nb && ps.task_d == d && ps.task_seg == seg)) {
         struct Item {
-            int len, b, s;
+            int len, b, s, last;  // tiles, column block, segment, its last row block
         };
         std::vector<Item> items;
         for (int b = 0; b < nb; ++b) {
             const int ns = 1 + std::max(0, (b - d - 1) / seg);
             for (int q = 0; q < ns; ++q) {
                 const int last_rb = q == ns - 1 ? b : (q + 1) * seg - 1;
-                items.push_back(Item{last_rb - q * seg + 1, b, q});
+                items.push_back(Item{last_rb - q * seg + 1, b, q, last_rb});
             }
         }
         std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
             return x.len != y.len ? x.len > y.len : x.b > y.b;
         });
+        // the sweep kernel's table: longest first
         std::vector<int2> tab(items.size());
         for (size_t i = 0; i < items.size(); ++i) tab[i] = make_int2(items[i].b, items[i].s);
-        // pageable source: the call returns once the data is staged, so the
-        // vector may go out of scope afterwards
+        // a fused pass's table: row block r's coefficients, then the segments
+        // that end at r (longest first), for r = 0 .. nb - 1; each task's
+        // inputs come from the chain, the far-sum workers or earlier tasks
+        std::vector<std::vector<int2>> at(nb);
+        for (const Item &it : items) at[it.last].push_back(make_int2(it.b, it.s));
+        std::vector<int2> pt;
+        pt.reserve(items.size() + nb);
+        for (int r = 0; r < nb; ++r) {
+            pt.push_back(make_int2(-1, r));
+            pt.insert(pt.end(), at[r].begin(), at[r].end());
+        }
+        // pageable sources: each call returns once the data is staged, so the
+        // vectors may go out of scope afterwards
         ps.task_nb = -1;
-        if (cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(post, pt.data(), pt.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return CHM_ERR_CUDA;
         ps.task_at = dst;
         ps.task_nb = nb;
         ps.task_d = d;
         ps.task_seg = seg;
         ps.task_count = (int)tab.size();
+        ps.post_count = (int)pt.size();
     }
     *ntasks = ps.task_count;
+    *npost = ps.post_count;
     return CHM_OK;
 }
 
@@ -276,10 +306,15 @@ int launch_pass(pass::Args<T> A, PassSpace &ps, cudaStream_t s)
     const int nb = A.nb;
     A.d = std::min(A.d, pass::ChainCfg<T, KB>::DMAX);
     A.c = std::min(A.d, pass::ChainCfg<T, KB>::CMAX);
-    if ((rc = sweep_tasks(ps, A.nb, A.d, A.seg, const_cast<int2 *>(A.tasks), &A.ntasks, s)) != CHM_OK) return rc;
+    // a fused pass (up to 8 vectors per pass)
+    A.fused = A.fused && pass::FusedCfg<T, KB>::ok;
+    if ((rc = sweep_tasks(ps, A.nb, A.d, A.seg, const_cast<int2 *>(A.tasks), const_cast<int2 *>(A.post), &A.ntasks,
+                          &A.npost, s)) != CHM_OK)
+        return rc;
     if (cudaMemsetAsync(A.ctl, 0, pass::kCtlInts * sizeof(int), s) != cudaSuccess) return CHM_ERR_CUDA;
     pass::prep_kernel<T><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::trsm_kernel<T, KB><<<nsm, pass::kTrsmWarps * 32, trsm_smem<T, KB>(), s>>>(A);
+    if (A.fused) return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
     pass::gram_kernel<T, KB><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::scan_kernel<T, KB><<<(KB * KB + 31) / 32, 1024, 0, s>>>(A);
     pass::coef_kernel<T, KB><<<std::min(nb, nsm * 8), 32, pass::Packed<KB>::smem, s>>>(A);
@@ -314,7 +349,8 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.nb = (int)((n + pass::kB - 1) / pass::kB);
     A.d = ch.d;
     A.P = reinterpret_cast<T *>(w + lay.P);
-    A.pflag = reinterpret_cast<int *>(w + lay.pflag);
+    A.Ptag = reinterpret_cast<long long *>(w + lay.Ptag);
+    A.Htag = reinterpret_cast<long long *>(w + lay.Htag);
     A.Ztag = reinterpret_cast<long long *>(w + lay.Ztag);
     A.Dinv = reinterpret_cast<T *>(w + lay.Dinv);
     A.G = reinterpret_cast<T *>(w + lay.G);
@@ -327,6 +363,10 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.snap = reinterpret_cast<T *>(w + lay.snap);
     A.rst = reinterpret_cast<double *>(w + lay.rst);
     A.tasks = reinterpret_cast<const int2 *>(w + lay.tasks);
+    A.post = reinterpret_cast<const int2 *>(w + lay.post);
+    A.cflag = reinterpret_cast<int *>(w + lay.cflag);
+    A.wprog = reinterpret_cast<long long *>(w + lay.wprog);
+    A.fused = ch.fused;
     A.seg = lay.seg;
     A.ws = w;
     A.ws_bytes = ps.bytes;
@@ -393,6 +433,11 @@ int chm_config_set(const char *key, int64_t value)
         chm::g_pass_seg.store((int)value);
         return CHM_OK;
     }
+    if (!strcmp(key, "pass_fused")) {
+        if (value < 0 || value > 1) return CHM_ERR_ARG;
+        chm::g_pass_fused.store((int)value);
+        return CHM_OK;
+    }
 #ifdef CHM_CHECK
     if (!strcmp(key, "check_cut")) {
         if (value < 0) return CHM_ERR_ARG;
@@ -411,6 +456,7 @@ int chm_config_get(const char *key, int64_t *value)
     else if (!strcmp(key, "pass_d_f32")) *value = chm::pass_d(CHM_F32_MIXED);
     else if (!strcmp(key, "pass_d_f64")) *value = chm::pass_d(CHM_F64);
     else if (!strcmp(key, "pass_seg")) *value = chm::seg_setting();
+    else if (!strcmp(key, "pass_fused")) *value = chm::fused_setting();
 #ifdef CHM_CHECK
     else if (!strcmp(key, "checked")) *value = 1;
     else if (!strcmp(key, "check_cut")) *value = chm::check_cut();

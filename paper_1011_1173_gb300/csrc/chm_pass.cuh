@@ -51,6 +51,7 @@ constexpr int kCtlWorkTicket = 0;   // next worker task of the forward substitut
 constexpr int kCtlRole = 1;         // thread blocks of the substitution started
 constexpr int kCtlSweepTicket = 2;  // next sweep task
 constexpr int kCtlAbort = 3;        // non-zero once a wait has timed out
+constexpr int kCtlPostTicket = 4;   // next coefficient or sweep task of a fused pass
 constexpr int kCtlInts = 16;
 
 template <typename T>
@@ -79,7 +80,16 @@ struct Args {
     const int2 *tasks;  // [ntasks]: the sweep's (column block, segment) tasks, longest first
     int ntasks;
     int seg;         // row blocks per sweep segment
-    int *pflag;      // [nb]: P of the block published (== epoch), with release
+    // fused pass (the substitution kernel's workers also compute the
+    // coefficients and sweep, each part as soon as its inputs are out)
+    int fused;
+    const int2 *post;   // [npost]: after the far sums, (-1, r) coefficients of row block r or
+                        // (b, s) sweep segment s of column block b, in an order their inputs allow
+    int npost;
+    int *cflag;         // [nb]: row block b's coefficients published (== epoch)
+    long long *wprog;   // [nb]: (epoch << 32) + row blocks the worker of column block b has consumed
+    long long *Ptag; // [nb * 32][KB][words of T]: P as epoch-tagged words, for readers within the launch
+    long long *Htag; // [nb][KB * KB][2]: a fused pass's prefix Grams H_b as tagged doubles
     long long *Ztag; // [nb][32][KB][words of T]: Zf as epoch-tagged words
     int *ctl;        // kCtlInts control words
     long long *status;     // sticky {status, row} of the stream
@@ -119,7 +129,8 @@ __device__ __forceinline__ bool ws_ok(const Args<T> &A, const SyncArgs &sy)
     return CHK_RECT(sy, (long long)A.kb, KB + 1, 1, 1 << 30) && CHK_RECT(sy, (long long)A.c, kMaxCrit + 1, 1, 1 << 30) &&
            CHK_RECT(sy, A.n, (long long)rows + 1, 1, 1ll << 62) &&
            CHK_REGION(sy, A.P, rows * KB * e, A.ws, A.ws_bytes) &&
-           CHK_REGION(sy, A.pflag, nb * sizeof(int), A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.Ptag, rows * KB * tagw * 8, A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.Htag, nb * KB * KB * 16, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.Ztag, rows * KB * tagw * 8, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.Dinv, nb * kB * kB * e, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.G, (size_t)A.c * nb * kB * kB * e, A.ws, A.ws_bytes) &&
@@ -131,7 +142,10 @@ __device__ __forceinline__ bool ws_ok(const Args<T> &A, const SyncArgs &sy)
            CHK_REGION(sy, A.snap, (nb > 1 ? (nb - 1) / (size_t)A.seg : 0) * rows * KB * e, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.rst, (nb > 1 ? (nb - 1) / (size_t)A.seg : 0) * KB * (KB + 1) / 2 * 8, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.tasks, (size_t)A.ntasks * sizeof(int2), A.ws, A.ws_bytes) &&
-           CHK_REGION(sy, A.ctl, kCtlInts * sizeof(int), A.ws, A.ws_bytes);
+           CHK_REGION(sy, A.ctl, kCtlInts * sizeof(int), A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.cflag, nb * sizeof(int), A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.wprog, nb * sizeof(long long), A.ws, A.ws_bytes) &&
+           CHK_REGION(sy, A.post, (size_t)A.npost * sizeof(int2), A.ws, A.ws_bytes);
 #else
     (void)A;
     (void)sy;
@@ -270,9 +284,33 @@ __device__ __forceinline__ void cp16(void *smem, const void *gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
+// The chain block's prefetches ask L2 to keep the lines (they are read a
+// few steps later, while the workers and the sweep stream the factor).
 __device__ __forceinline__ void prefetch_l2(const void *gmem)
 {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(gmem));
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(gmem));
+}
+// An L2 policy that evicts first: the sweep's tiles are read and written
+// once, so they should not push out what the chain block prefetched.
+__device__ __forceinline__ unsigned long long evict_first_policy()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void cp16_hint(void *smem, const void *gmem, unsigned long long pol)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "l"(pol)
+                 : "memory");
+}
+template <typename V>
+__device__ __forceinline__ void st16_hint(V *gmem, const V &v, unsigned long long pol)
+{
+    const unsigned *w = reinterpret_cast<const unsigned *>(&v);
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(gmem), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "l"(pol)
+                 : "memory");
 }
 
 // Warp-cooperative stage of the tile rows r0.. r0 + 31, columns c0 .. c0 + 31
@@ -447,6 +485,44 @@ __device__ __forceinline__ bool get_tag(const long long *w, long long ep64, doub
     return get_tagged(w, ep64, v);
 }
 
+// Every lane reads its KB tagged values (a row of P) until all of the
+// warp's words carry the epoch; sleeps between polls up to max_ns.  False if
+// the launch is being aborted or the wait ran out (recorded).
+template <typename T, int KB>
+__device__ __forceinline__ bool warp_tagged_row(const SyncArgs &sy, const long long *src, long long ep64, T (&v)[KB],
+                                                unsigned max_ns, long long who)
+{
+    constexpr int TW = Tag<T>::words;
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &v[q]) && ok;
+    if (__all_sync(0xffffffffu, ok)) return true;
+    const long long t0 = global_ns();
+    unsigned ns = 16;
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(ns);
+        if (ns < max_ns) ns <<= 1;
+        if (!ok) {
+            ok = true;
+#pragma unroll
+            for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &v[q]) && ok;
+        }
+        if (__all_sync(0xffffffffu, ok)) return true;
+        if ((it & 15u) == 0u) {
+            int bad = 0;
+            if ((threadIdx.x & 31) == 0) {
+                if (aborted(sy)) {
+                    bad = 1;
+                } else if (global_ns() - t0 > sy.timeout_ns || it > (1u << 26)) {
+                    record_error(sy, kStatusTimeout, who);
+                    bad = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+        }
+    }
+}
+
 // Warp-wide bounded wait on a shared-memory counter (every lane polls; the
 // verdict is lane 0's).  False if the block is stopping or the wait ran out.
 __device__ __forceinline__ bool warp_seq_wait(const SyncArgs &sy, const volatile int *seq, int want,
@@ -537,14 +613,52 @@ __device__ __forceinline__ bool mb_wait(const SyncArgs &sy, unsigned long long *
     return true;
 }
 
+// One entry of a block's Gram, sum over its 32 rows of P_iq P_ir, for the
+// prefix Grams (in double).  From double P: fused multiply-adds in double.
+// From float P (the mixed path) the FP64 rate, not the data, would bound a
+// single warp at one FP64 instruction per 64 cycles, so the sum is formed
+// on the FP32 pipes with no rounding lost: each product splits exactly into
+// hi + lo (hi = fl(a b), lo = fma(a, b, -hi)), the hi parts are summed with
+// Neumaier's compensation (the running sum s and its error c), the lo parts
+// in float (each below 2^-24 of its product), and s, c and the lo sum are
+// added in double: an error of about 32 u^2 of the sum of |a b| (u = 2^-24),
+// against about 32 u_d = 2^-48 of it for a sum in double.
+__device__ __forceinline__ double gram_entry(const double *pm, int KS, int q, int r)
+{
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll 8
+    for (int i = 0; i < kB; i += 2) {
+        s0 = fma(pm[i * KS + q], pm[i * KS + r], s0);
+        s1 = fma(pm[(i + 1) * KS + q], pm[(i + 1) * KS + r], s1);
+    }
+    return s0 + s1;
+}
+__device__ __forceinline__ double gram_entry(const float *pm, int KS, int q, int r)
+{
+    float s = 0.f, c = 0.f, l = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < kB; ++i) {
+        // the _rn intrinsics keep the compiler from fusing these operations
+        const float a = pm[i * KS + q], b = pm[i * KS + r];
+        const float hi = __fmul_rn(a, b);
+        const float lo = fmaf(a, b, -hi);
+        const float t = __fadd_rn(s, hi);
+        c = __fadd_rn(c, fabsf(s) >= fabsf(hi) ? __fadd_rn(__fsub_rn(s, t), hi) : __fadd_rn(__fsub_rn(hi, t), s));
+        s = t;
+        l = __fadd_rn(l, lo);
+    }
+    return (double)s + ((double)c + (double)l);
+}
+
 // Warps of the forward-substitution kernel and the chain block's roles: the
-// critical warp, the W warp, seven near warps (the last one, when no near
-// offset needs it, a second publisher), the far-sum stager, the loader and
-// the publisher.
-constexpr int kTrsmWarps = 12;
+// critical warp, the W warp, seven near warps, the far-sum stager, the
+// loader, two publishers (even and odd blocks: the fence that orders a
+// block's values before its flag costs about a chain step) and, in a fused
+// pass, the warp that forms the prefix Grams.
+constexpr int kTrsmWarps = 14;
 constexpr int kWCrit = 0, kWZhat = 1, kWNear0 = 2;
-constexpr int kNearWarps = kTrsmWarps - 5;  // warps 2 .. 8
-constexpr int kWZf = kTrsmWarps - 3, kWLoad = kTrsmWarps - 2, kWPub = kTrsmWarps - 1;
+constexpr int kNearWarps = 7;  // warps 2 .. 8
+constexpr int kWZf = 9, kWLoad = 10, kWPub = 11, kWPub2 = 12, kWH = 13;
 
 // Lookahead bound (d), offsets on the critical warp (c) and ring depths per
 // instantiation, sized to the 227 KB of shared memory.
@@ -557,11 +671,12 @@ struct ChainCfg {
     static constexpr int RT = DMAX;       // per near offset
     static constexpr int RZ = 4;          // W ring
     static constexpr int RF = 4;          // far-sum ring
+    static constexpr int RH = 4;          // prefix-Gram ring (fused passes)
     static constexpr size_t tile = sizeof(T) * kB * Stride<T>::value;
     static constexpr int NEAR = DMAX - CMAX > 1 ? DMAX - CMAX : 1;  // near offset slots (d - c of them used)
     static constexpr size_t rest = sizeof(T) * Rows<T, KB>::size *
                                        ((size_t)RP + (size_t)NEAR * RT + RZ + RF + 1) +
-                                   tile + 256;
+                                   tile + 256 + (size_t)RH * KB * KB * sizeof(double);
     // staged per step: G^(1..c) and Dinv on the loader, one tile per near offset on the near warps
     static constexpr size_t stage = (size_t)(CMAX + 1 + NEAR) * tile;
     static constexpr int fit = (int)((224u * 1024u - rest) / stage);
@@ -582,12 +697,14 @@ struct ChainSmem {
     T Z[C::RZ][RW];                       // W_b
     T F[C::RF][RW];                       // far sums Zf_b
     T w[RW];                              // the W warp's work vector
+    double Hr[C::RH][KB * KB];            // prefix Grams H_m on their way to the publisher
     // full / empty rings: stage (G, Dinv), W, P, far sums; near warps' steps
     unsigned long long st_full[C::RS], st_empty[C::RS];
     unsigned long long w_full[C::RZ], w_empty[C::RZ];
     unsigned long long p_full[C::RP], p_empty[C::RP];
     unsigned long long f_full[C::RF], f_empty[C::RF];
     unsigned long long t_full[kNearWarps][C::RT];
+    unsigned long long h_full[C::RH], h_empty[C::RH];
     int stop;
 };
 
@@ -629,7 +746,8 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
         for (int i = 0; i < C::RP; ++i) {
             mb_init(&S.p_full[i], 32);
-            mb_init(&S.p_empty[i], 32 * (1 + nnw));  // the publisher and the near warps
+            // the publisher, the near warps and, in a fused pass, the H warp
+            mb_init(&S.p_empty[i], 32 * (1 + nnw + (A.fused ? 1 : 0)));
         }
         for (int i = 0; i < C::RF; ++i) {
             mb_init(&S.f_full[i], 32);
@@ -637,6 +755,10 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
         for (int t = 0; t < kNearWarps; ++t)
             for (int i = 0; i < C::RT; ++i) mb_init(&S.t_full[t][i], 32);
+        for (int i = 0; i < C::RH; ++i) {
+            mb_init(&S.h_full[i], 32);
+            mb_init(&S.h_empty[i], 32);
+        }
         S.stop = 0;
     }
     __syncthreads();
@@ -648,11 +770,12 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }                                                                                      \
     } while (0)
 
-    // Publication of P for the workers: the blocks m = first, first + step, ...
-    // are stored, then one flag per block is released after its values.  The
-    // fence that orders them costs about as much as a chain step, so the
-    // last near warp, when no near offset needs it, takes every other block.
-    const int npub = nnw < kNearWarps ? 2 : 1;
+    // Publication of P: the blocks m = first, first + step, ... are stored
+    // plainly (for the kernels after this one) and as epoch-tagged words for
+    // the readers within this launch, which take a word once it carries this
+    // pass's epoch; no fence is needed (a fence waits for the stores to be
+    // acknowledged, which under the sweep's and the workers' traffic costs
+    // several chain steps).
     auto publish = [&](int first, int step) {
         for (int m = first; m < nb; m += step) {
             MW(S.p_full, m, C::RP, m);
@@ -661,14 +784,62 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             __syncwarp();
             mb_arrive(&S.p_empty[m % C::RP]);
             T *plain = A.P + ((size_t)m * kB + lane) * KB;
+            long long *tag = A.Ptag + ((size_t)m * kB + lane) * KB * TW;
 #pragma unroll
-            for (int q = 0; q < KB; ++q) __stcg(plain + q, v[q]);
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                st_release_gpu(A.pflag + m, A.epoch);
+            for (int q = 0; q < KB; ++q) {
+                __stcg(plain + q, v[q]);
+                put_tag(tag + q * TW, v[q], ep64);
+            }
+            if (A.fused) {
+                // H_m from the H warp, as tagged doubles
+                MW(S.h_full, m, C::RH, m);
+                long long *hg = A.Htag + (size_t)m * KB * KB * 2;
+                for (int e = lane; e < KB * KB; e += 32) put_tagged(hg + 2 * e, S.Hr[m % C::RH][e], ep64);
+                __syncwarp();
+                mb_arrive(&S.h_empty[m % C::RH]);
             }
             if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 4] = global_ns();
+        }
+    };
+
+    // Fused pass: the prefix Grams H_m = Sigma + sum_{i < m} P_i^T P_i (in
+    // double; the padding vectors' entries an identity) for the workers'
+    // coefficient tasks, handed to the publisher through a shared-memory
+    // ring and released with P_m under the publisher's one fence per block.
+    auto hwarp = [&]() {
+        constexpr int NE = KB * KB, NL = (NE + 31) / 32;
+        constexpr int KS = Rows<T, KB>::KS;
+        double h[NL];
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+            const int e = lane + 32 * u, q = e / KB, r = e % KB;
+            h[u] = (e < NE && q == r) ? (q < A.kb ? sigma_of(A, q) : 1.0) : 0.0;
+        }
+        for (int m = 0; m < nb; ++m) {
+            // H_m (it needs only the blocks before m) to the publisher first
+            if (m >= C::RH) MW(S.h_empty, m - C::RH, C::RH, m);
+            double *hs = S.Hr[m % C::RH];
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                const int e = lane + 32 * u;
+                if (e < NE) hs[e] = h[u];
+            }
+            __syncwarp();
+            mb_arrive(&S.h_full[m % C::RH]);
+            // then block m's Gram into the running sum
+            MW(S.p_full, m, C::RP, m);
+            const T *pm = S.P[m % C::RP];
+            double g[NL];
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                const int e = lane + 32 * u, q = e / KB, r = e % KB;
+                g[u] = 0.0;
+                if (e < NE) g[u] = gram_entry(pm, KS, q, r);
+            }
+            __syncwarp();
+            mb_arrive(&S.p_empty[m % C::RP]);
+#pragma unroll
+            for (int u = 0; u < NL; ++u) h[u] += g[u];
         }
     };
 
@@ -724,10 +895,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
     } else if (warp >= kWNear0 && warp < kWNear0 + kNearWarps) {
         const int t = warp - kWNear0;
-        if (t >= nnw) {
-            if (t == kNearWarps - 1 && npub == 2) publish(1, 2);
-            return;
-        }
+        if (t >= nnw) return;
         // this warp's offsets' tiles, staged RS - 1 steps ahead (the factor as
         // it entered the pass: nothing to wait for)
         auto stage = [&](int m) {
@@ -864,8 +1032,10 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             mb_arrive(&S.f_full[k % C::RF]);
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 2] = global_ns();
         }
-    } else if (warp == kWPub) {
-        publish(0, npub);
+    } else if (warp == kWPub || warp == kWPub2) {
+        publish(warp == kWPub ? 0 : 1, 2);
+    } else if (warp == kWH) {
+        if (A.fused) hwarp();
     }
 #undef MW
 }
@@ -882,14 +1052,16 @@ struct WorkerCfg {
                                      ? (int)((200u * 1024u) / warp_bytes) : kTrsmWarps;
 };
 
+// Returns true once the far-sum tasks are all taken (a fused pass's worker
+// then takes coefficient and sweep tasks), false if the launch is aborting.
 template <typename T, int KB>
-__device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
+__device__ bool trsm_workers(const Args<T> &A, unsigned char *smem)
 {
     using W = WorkerCfg<T, KB>;
     constexpr int SD = Stride<T>::value;
     constexpr int TW = Tag<T>::words;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp >= W::warps) return;
+    if (warp >= W::warps) return false;
     T *base = reinterpret_cast<T *>(smem + (size_t)warp * W::warp_bytes);
     T *Pr = base + (size_t)W::NS * kB * SD;  // Rows<T, KB>
     const long long n = A.n, ld = A.ld;
@@ -901,9 +1073,9 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
         int tk = 0;
         if (lane == 0) tk = ld_relaxed_gpu(A.ctl + kCtlAbort) ? -1 : atomicAdd(A.ctl + kCtlWorkTicket, 1);
         tk = __shfl_sync(0xffffffffu, tk, 0);
-        if (tk < 0) return;
+        if (tk < 0) return false;
         const int b = d + 1 + tk;
-        if (b >= nb) return;
+        if (b >= nb) return true;
         const long long c0 = (long long)b * kB;
         const bool col_ok = c0 + lane < n;
         T z[KB];
@@ -915,49 +1087,36 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
             stage_tile(sy, base + (size_t)(r % W::NS) * kB * SD, A.L, ld, (long long)r * kB, c0, n, kB, vec, lane);
             cp_commit();
         }
-        int avail = 0;  // blocks r .. avail - 1 are known to be published
         for (int r = 0; r < nfar; ++r) {
             if (r > 0 && r % A.seg == 0) {
                 // a sweep segment boundary: the residual before row block r
                 T *sn = A.snap + (((size_t)(r / A.seg - 1) * nb + b) * kB + lane) * KB;
 #pragma unroll
                 for (int q = 0; q < KB; ++q) sn[q] = z[q];
+                if (A.fused) {
+                    // tiles 0 .. r - 1 are read and the residual is out: the
+                    // sweep may now rewrite the tiles of the segment that ends here
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence();
+                        st_release_gpu(A.wprog + b, ep64 + r);
+                    }
+                }
             }
             const int rn = r + W::NS - 1;
             if (rn < nfar)
                 stage_tile(sy, base + (size_t)(rn % W::NS) * kB * SD, A.L, ld, (long long)rn * kB, c0, n, kB, vec, lane);
             cp_commit();
-            if (r >= avail) {
-                // one probe of the next 32 blocks' flags (lane l: block r + l);
-                // the published prefix needs no further look
-                const int f = (r + lane < nfar) ? ld_relaxed_gpu(A.pflag + r + lane) : A.epoch;
-                const unsigned not_ready = __ballot_sync(0xffffffffu, f != A.epoch);
-                int got = not_ready ? __ffs(not_ready) - 1 : 32;
-                if (got == 0) {
-                    // the next one is not out yet: lane 0 waits on its flag
-                    // alone, polling often only near the block's last tiles
-                    // (the far sum is due when the chain reaches b - d; a
-                    // worker further back catches up in one burst)
-                    const unsigned max_ns = r + 4 >= nfar ? 64u : 1024u;
-                    int ok = 1;
-                    if (lane == 0)
-                        ok = bounded_wait(sy, [&] { return ld_relaxed_gpu(A.pflag + r) == A.epoch; }, [] {}, b, max_ns)
-                                 ? 1 : 0;
-                    if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                        cp_wait<0>();
-                        return;
-                    }
-                    got = 1;
-                }
-                fence_acq_rel_gpu();
-                avail = r + got;
-            }
-            __syncwarp();
-            // P_r: every lane reads its row through L1 (shared with this SM's other warps)
+            // P_r: every lane takes its row as tagged words, polling until
+            // all carry this pass's epoch (often only near the block's last
+            // tiles: the far sum is due when the chain reaches b - d, and a
+            // worker further back catches up in one burst)
             T pv[KB];
-            const T *src = A.P + ((size_t)r * kB + lane) * KB;
-#pragma unroll
-            for (int q = 0; q < KB; ++q) pv[q] = src[q];
+            if (!warp_tagged_row<T, KB>(sy, A.Ptag + ((size_t)r * kB + lane) * KB * TW, ep64, pv,
+                                        r + 4 >= nfar ? 64u : 1024u, b)) {
+                cp_wait<0>();
+                return false;
+            }
             row_store<T, KB>(Pr, lane, pv);
             if (A.trace && lane == 0 && r == nfar - 1) A.trace[(size_t)b * 16 + 8] = global_ns();
             cp_wait<W::NS - 1>();
@@ -973,20 +1132,18 @@ __device__ void trsm_workers(const Args<T> &A, unsigned char *smem)
 #pragma unroll
         for (int q = 0; q < KB; ++q) put_tag(zt + q * TW, z[q], ep64);
         if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 9] = global_ns();
+        if (A.fused) {
+            // every tile of the far part read: the sweep's segments of this column may go
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                st_release_gpu(A.wprog + b, ep64 + nfar);
+            }
+        }
     }
 }
 
-template <typename T, int KB>
-__global__ void __launch_bounds__(kTrsmWarps * 32, 1) trsm_kernel(Args<T> A)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_role;
-    if (!ws_ok<T, KB>(A, sync_of(A))) return;
-    if (threadIdx.x == 0) s_role = atomicAdd(A.ctl + kCtlRole, 1);
-    __syncthreads();
-    if (s_role == 0) trsm_chain<T, KB>(A, smem);
-    else trsm_workers<T, KB>(A, smem);
-}
+
 
 // ---------------------------------------------------------------- Compute
 
@@ -1068,21 +1225,54 @@ struct Packed {
 };
 __device__ __forceinline__ int pidx(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 
+// One row block's coefficients (one warp); Hs: Packed<KB>::smem bytes of
+// shared memory.  P and H are read through L2 (a fused pass's workers read
+// what other SMs wrote during the launch).
 template <typename T, int KB>
-__global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
+__device__ bool coef_block(const Args<T> &A, const SyncArgs &sy, int b, double *Hs, bool tagged)
 {
     using PK = Packed<KB>;
     constexpr int NE = PK::entries, HS = PK::stride;
-    extern __shared__ double Hs[];  // [kB + 1][HS]
-    const int lane = threadIdx.x;
-    const SyncArgs sy = sync_of(A);
+    const int lane = threadIdx.x & 31;
     const long long n = A.n;
     const int kb = A.kb;
-    if (!ws_ok<T, KB>(A, sy)) return;
-    for (int b = blockIdx.x; b < A.nb; b += gridDim.x) {
-        const long long r0 = (long long)b * kB;
-        const int rows = (int)min((long long)kB, n - r0);
-        double p[KB];
+    const long long r0 = (long long)b * kB;
+    const int rows = (int)min((long long)kB, n - r0);
+    double p[KB];
+    if (tagged) {
+        // P_b and H_b as the chain block publishes them within the launch
+        constexpr int TW = Tag<T>::words;
+        const long long ep64 = (long long)A.epoch << 32;
+        T pv[KB];
+        if (!warp_tagged_row<T, KB>(sy, A.Ptag + (size_t)(r0 + lane) * KB * TW, ep64, pv, 256u, b)) return false;
+#pragma unroll
+        for (int q = 0; q < KB; ++q) p[q] = (q < kb) ? (double)pv[q] : 0.0;
+        for (int e0 = 0; e0 < NE; e0 += 32) {
+            const int e = e0 + lane;
+            double v = 0.0;
+            bool ok = true;
+            if (e < NE) {
+                int i = 0;
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                const long long *w = A.Htag + ((size_t)b * KB * KB + i * KB + (e - i * (i + 1) / 2)) * 2;
+                ok = get_tagged(w, ep64, &v);
+                const long long t0 = ok ? 0 : global_ns();
+                for (unsigned it = 0; !ok; ++it) {
+                    __nanosleep(128);
+                    ok = get_tagged(w, ep64, &v);
+                    if (!ok && (it & 255u) == 255u) {
+                        if (aborted(sy)) break;
+                        if (global_ns() - t0 > sy.timeout_ns || it > (1u << 26)) {
+                            record_error(sy, kStatusTimeout, b);
+                            break;
+                        }
+                    }
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            if (e < NE) Hs[e] = v;
+        }
+    } else {
         const T *prow = A.P + (size_t)(r0 + lane) * KB;
 #pragma unroll
         for (int q = 0; q < KB; ++q) p[q] = (q < kb) ? (double)__ldcg(prow + q) : 0.0;
@@ -1091,77 +1281,87 @@ __global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
         for (int e = lane; e < NE; e += 32) {
             int i = 0;
             while ((i + 1) * (i + 2) / 2 <= e) ++i;
-            Hs[e] = hb[i * KB + (e - i * (i + 1) / 2)];
+            Hs[e] = __ldcg(hb + i * KB + (e - i * (i + 1) / 2));
         }
-        double *mine = Hs + (size_t)(lane + 1) * HS;
-#pragma unroll
-        for (int i = 0; i < KB; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) mine[pidx(i, j)] = p[i] * p[j];
-        __syncwarp();
-        for (int e = lane; e < NE; e += 32) {
-            double acc = Hs[e];
-            for (int r = 1; r <= kB; ++r) {
-                acc += Hs[(size_t)r * HS + e];
-                Hs[(size_t)r * HS + e] = acc;
-            }
-        }
-        __syncwarp();
-        // this row's H (the prefix before it): row `lane`
-        double *h = Hs + (size_t)lane * HS;
-        for (int j = 0; j < kb; ++j) {
-            double dj = h[pidx(j, j)];
-            for (int m = 0; m < j; ++m) dj -= h[pidx(j, m)] * h[pidx(j, m)] * h[pidx(m, m)];
-            h[pidx(j, j)] = dj;
-            const double idj = rcp_refined(dj);
-            for (int i = j + 1; i < kb; ++i) {
-                double t = h[pidx(i, j)];
-                for (int m = 0; m < j; ++m) t -= h[pidx(i, m)] * h[pidx(j, m)] * h[pidx(m, m)];
-                h[pidx(i, j)] = t * idj;
-            }
-        }
-        // at a sweep segment boundary, the prefix Gram's LDL^T before the block
-        if (lane == 0 && b > 0 && b % A.seg == 0) {
-            double *dst = A.rst + (size_t)(b / A.seg - 1) * (KB * (KB + 1) / 2);
-            for (int e = 0; e < NE; ++e) dst[e] = h[e];
-        }
-        // z = L^{-1} p and the coefficients
-        double z[KB];
-        double Dc = 1.0;
-        bool bad = false;
-        T *cf = A.coef + (size_t)(r0 + lane) * 2 * KB;
-#pragma unroll
-        for (int q = 0; q < KB; ++q) {
-            if (q < kb) {
-                double zq = p[q];
-#pragma unroll
-                for (int m = 0; m < q; ++m) zq -= h[pidx(q, m)] * z[m];
-                z[q] = zq;
-                const double sg = sigma_of(A, q);
-                const double ad = sg * h[pidx(q, q)];  // |D_q|
-                bad = bad || !(ad > 0.0 && ad <= DBL_MAX);
-                Dc = fma(sg * zq, zq * rcp_refined(ad), Dc);
-                bad = bad || !(Dc > 0.0 && Dc <= DBL_MAX);
-                if (lane < rows) {
-                    cf[2 * q] = (T)(sg * zq);
-                    cf[2 * q + 1] = (T)(zq * rcp_refined(ad * Dc));
-                }
-            } else {
-                z[q] = 0.0;
-                if (lane < rows) {
-                    cf[2 * q] = T(0);
-                    cf[2 * q + 1] = T(0);
-                }
-            }
-        }
-        const double rD = rsqrt_refined(Dc);
-        if (lane < rows) {
-            A.escale[r0 + lane] = (T)rD;
-            A.dfac[r0 + lane] = Dc * rD;
-            if (bad) record_error(sy, kStatusNotPD, r0 + lane);
-        }
-        __syncwarp();
     }
+    double *mine = Hs + (size_t)(lane + 1) * HS;
+#pragma unroll
+    for (int i = 0; i < KB; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) mine[pidx(i, j)] = p[i] * p[j];
+    __syncwarp();
+    for (int e = lane; e < NE; e += 32) {
+        double acc = Hs[e];
+        for (int r = 1; r <= kB; ++r) {
+            acc += Hs[(size_t)r * HS + e];
+            Hs[(size_t)r * HS + e] = acc;
+        }
+    }
+    __syncwarp();
+    // this row's H (the prefix before it): row `lane`
+    double *h = Hs + (size_t)lane * HS;
+    for (int j = 0; j < kb; ++j) {
+        double dj = h[pidx(j, j)];
+        for (int m = 0; m < j; ++m) dj -= h[pidx(j, m)] * h[pidx(j, m)] * h[pidx(m, m)];
+        h[pidx(j, j)] = dj;
+        const double idj = rcp_refined(dj);
+        for (int i = j + 1; i < kb; ++i) {
+            double t = h[pidx(i, j)];
+            for (int m = 0; m < j; ++m) t -= h[pidx(i, m)] * h[pidx(j, m)] * h[pidx(m, m)];
+            h[pidx(i, j)] = t * idj;
+        }
+    }
+    // at a sweep segment boundary, the prefix Gram's LDL^T before the block
+    if (lane == 0 && b > 0 && b % A.seg == 0) {
+        double *dst = A.rst + (size_t)(b / A.seg - 1) * (KB * (KB + 1) / 2);
+        for (int e = 0; e < NE; ++e) dst[e] = h[e];
+    }
+    // z = L^{-1} p and the coefficients
+    double z[KB];
+    double Dc = 1.0;
+    bool bad = false;
+    T *cf = A.coef + (size_t)(r0 + lane) * 2 * KB;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+        if (q < kb) {
+            double zq = p[q];
+#pragma unroll
+            for (int m = 0; m < q; ++m) zq -= h[pidx(q, m)] * z[m];
+            z[q] = zq;
+            const double sg = sigma_of(A, q);
+            const double ad = sg * h[pidx(q, q)];  // |D_q|
+            bad = bad || !(ad > 0.0 && ad <= DBL_MAX);
+            Dc = fma(sg * zq, zq * rcp_refined(ad), Dc);
+            bad = bad || !(Dc > 0.0 && Dc <= DBL_MAX);
+            if (lane < rows) {
+                cf[2 * q] = (T)(sg * zq);
+                cf[2 * q + 1] = (T)(zq * rcp_refined(ad * Dc));
+            }
+        } else {
+            z[q] = 0.0;
+            if (lane < rows) {
+                cf[2 * q] = T(0);
+                cf[2 * q + 1] = T(0);
+            }
+        }
+    }
+    const double rD = rsqrt_refined(Dc);
+    if (lane < rows) {
+        A.escale[r0 + lane] = (T)rD;
+        A.dfac[r0 + lane] = Dc * rD;
+        if (bad) record_error(sy, kStatusNotPD, r0 + lane);
+    }
+    __syncwarp();
+    return true;
+}
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(32) coef_kernel(Args<T> A)
+{
+    extern __shared__ double Hs[];  // [kB + 1][HS]
+    const SyncArgs sy = sync_of(A);
+    if (!ws_ok<T, KB>(A, sy)) return;
+    for (int b = blockIdx.x; b < A.nb; b += gridDim.x) coef_block<T, KB>(A, sy, b, Hs, false);
 }
 
 // ---------------------------------------------------------------- sweep
@@ -1225,174 +1425,292 @@ __device__ __forceinline__ void rotate_full(T (&v)[kB], T (&uh)[KB], const T *cf
     }
 }
 
-template <typename T, int KB>
-__global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args<T> A)
+// Warp-wide bounded wait for a flag (== epoch) that another SM releases;
+// lane 0 polls and acquires, the warp barrier orders the other lanes' later
+// reads after it.  False if the launch is being aborted or the wait ran out.
+__device__ __forceinline__ bool warp_flag(const SyncArgs &sy, const int *f, int epoch, long long who)
 {
-    using C = SweepCfg<T, KB>;
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = wait_eq(sy, f, epoch, who) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+__device__ __forceinline__ bool warp_count(const SyncArgs &sy, const long long *w, long long want, long long who)
+{
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = wait_ge(sy, w, want, who) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+// Segment sg of column block b: row blocks rb .. re (the last segment ends
+// at the diagonal tile), tiles and their rows' coefficients staged through
+// NSLOT slots.  In a fused pass the segment first waits until nothing else
+// will read its tiles (the column's worker is past re, or for the last
+// segment the chain has published P_b, which needs every near term of b),
+// and each tile waits for its row block's coefficients.  Returns false if
+// the launch is being aborted.
+template <typename T, int KB, int NSLOT>
+__device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int sg, SweepSlot<T, KB> *slot)
+{
     constexpr int SD = Stride<T>::value;
     constexpr int E = 16 / (int)sizeof(T);
     constexpr int CPC = kB / E;         // 16-byte chunks per column segment
     constexpr int CPL = kB * CPC / 32;  // chunks per lane per tile
     using V = typename Vec16<T>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * C::NSLOT;
+    const int lane = threadIdx.x & 31;
     const long long n = A.n, ld = A.ld;
     const int nb = A.nb;
-    const SyncArgs sy = sync_of(A);
-    if (!ws_ok<T, KB>(A, sy)) return;
     const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
     // this lane's chunk of every staged column segment: chunk ch of columns
     // col0 + t * (32 / CPC), t = 0 .. CPL - 1
     const int ch = lane % CPC, col0 = lane / CPC, cstep = 32 / CPC;
+    const int nseg = 1 + max(0, (b - A.d - 1) / A.seg);
+    if (b < 0 || b >= nb || sg < 0 || sg >= nseg) {
+        // not a task of this pass (an internal invariant, checked in every build)
+        if (lane == 0) record_error(sy, kStatusBounds, (long long)b);
+        return false;
+    }
+    const int rb = sg * A.seg, re = sg == nseg - 1 ? b : rb + A.seg - 1;
+    const long long ep64 = (long long)A.epoch << 32;
+    const unsigned long long pol = evict_first_policy();
+    if (A.fused) {
+        // last segment: P_b out (its first tagged word) means the chain has
+        // consumed every near term of column block b
+        bool ok;
+        if (sg == nseg - 1) {
+            T pv[1];
+            ok = warp_tagged_row<T, 1>(sy, A.Ptag + (size_t)b * kB * KB * Tag<T>::words, ep64, pv, 256u, b);
+        } else {
+            ok = warp_count(sy, A.wprog + b, ep64 + re + 1, b);
+        }
+        if (!ok) return false;
+        if (sg > 0 && !warp_flag(sy, A.cflag + rb, A.epoch, b)) return false;  // its LDL^T at rb
+    }
+    const long long c0 = (long long)b * kB;
+    const bool active = c0 + lane < n;
+    T uh[KB];
+    if (sg == 0) {
+#pragma unroll
+        for (int q = 0; q < KB; ++q)
+            uh[q] = (active && q < A.kb && CHK_RECT(sy, c0 + lane + q * A.ldv, n, A.kb, A.ldv)) ? A.V[c0 + lane + q * A.ldv]
+                                                                                               : T(0);
+    } else {
+        // the carry entering row block rb, rebuilt from the substitution's
+        // residual w there: u_hat = |D|^{-1} L^{-1} w with H = L D L^T the
+        // prefix Gram before the block (the scaled rotations' carry is
+        // this linear image of the residual at every row)
+        const T *w = A.snap + (((size_t)(sg - 1) * nb + b) * kB + lane) * KB;
+        const double *h = A.rst + (size_t)(sg - 1) * (KB * (KB + 1) / 2);
+        double z[KB];
+#pragma unroll
+        for (int q = 0; q < KB; ++q) {
+            if (q < A.kb) {
+                double zq = active ? (double)__ldcg(w + q) : 0.0;
+#pragma unroll
+                for (int m = 0; m < q; ++m) zq -= __ldcg(h + pidx(q, m)) * z[m];
+                z[q] = zq;
+                uh[q] = (T)(zq / (sigma_of(A, q) * __ldcg(h + pidx(q, q))));
+            } else {
+                z[q] = 0.0;
+                uh[q] = T(0);
+            }
+        }
+    }
+    // per-lane addresses of the staged chunks (vector path)
+    const long long gofs = (long long)ch * E + (c0 + col0) * ld;
+    const T *gbase = A.L + gofs;
+    unsigned colmask = 0;
+#pragma unroll
+    for (int t = 0; t < CPL; ++t)
+        if (c0 + col0 + t * cstep < n) colmask |= 1u << t;
+    bool alive = true;
+    auto fetch = [&](int r) {
+        if (A.fused && alive) alive = warp_flag(sy, A.cflag + r, A.epoch, b);  // the row block's coefficients
+        if (!alive) return;
+        SweepSlot<T, KB> &sl = slot[r % NSLOT];
+        const long long r0 = (long long)r * kB;
+        if (r < b && vec) {
+            const T *g = gbase + r0;
+            T *d = sl.tile + col0 * SD + ch * E;
+#pragma unroll
+            for (int t = 0; t < CPL; ++t) {
+                if ((colmask >> t & 1u) && CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld, n, ld) &&
+                    CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld + E - 1, n, ld))
+                    cp16_hint(d + t * cstep * SD, g + (long long)t * cstep * ld, pol);
+                else {
+#pragma unroll
+                    for (int u = 0; u < E; ++u) d[t * cstep * SD + u] = T(0);
+                }
+            }
+        } else if (r < b) {
+            stage_tile(sy, sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
+        } else {
+            // the diagonal tile: rows <= column only
+            for (int col = 0; col < kB; ++col)
+                if (c0 + col < n && lane <= col && CHK_TRI(sy, (r0 + lane) + (c0 + col) * ld, n, ld))
+                    cp_elem(&sl.tile[col * SD + lane], A.L + (r0 + lane) + (c0 + col) * ld);
+        }
+        const T *cf = A.coef + (size_t)r0 * 2 * KB;
+        for (int c = lane; c < kB * 2 * KB / E; c += 32) cp16(sl.cf + c * E, cf + c * E);
+        if (lane < kB / E) cp16(sl.e + lane * E, A.escale + r0 + lane * E);
+        if (r == b && lane < kB / 2) cp16(sl.df + 2 * lane, A.dfac + r0 + 2 * lane);
+    };
+    for (int r = rb; r < rb + NSLOT - 1; ++r) {
+        if (r <= re) fetch(r);
+        cp_commit();
+    }
+    for (int r = rb; r <= re; ++r) {
+        if (r + NSLOT - 1 <= re) fetch(r + NSLOT - 1);
+        cp_commit();
+        cp_wait<NSLOT - 1>();
+        __syncwarp();
+        if (!alive) break;
+        SweepSlot<T, KB> &sl = slot[r % NSLOT];
+        const bool diag = r == b;
+        const long long r0 = (long long)r * kB;
+        T v[kB];
+        V *colv = reinterpret_cast<V *>(sl.tile + lane * SD);
+#pragma unroll
+        for (int c = 0; c < kB / E; ++c) {
+            const V x = colv[c];
+#pragma unroll
+            for (int u = 0; u < E; ++u) v[c * E + u] = vget<T>(x, u);
+        }
+        if (!diag) {
+            if (active) rotate_full<T, KB>(v, uh, sl.cf, sl.e);
+        } else if (active) {
+            // rows above the diagonal of column `lane`, then the diagonal
+#pragma unroll
+            for (int i = 0; i < kB; ++i) {
+                if (i < lane) {
+                    T x = v[i];
+#pragma unroll
+                    for (int q = 0; q < KB; ++q) {
+                        x = fma(sl.cf[i * 2 * KB + 2 * q], uh[q], x);
+                        uh[q] = fma(-sl.cf[i * 2 * KB + 2 * q + 1], x, uh[q]);
+                    }
+                    v[i] = x * sl.e[i];
+                } else if (i == lane) {
+                    v[i] = (T)((double)v[i] * sl.df[i]);
+                }
+            }
+        }
+        T *col = sl.tile + lane * SD;
+#pragma unroll
+        for (int c = 0; c < kB / E; ++c) {
+            V x;
+            T *xp = reinterpret_cast<T *>(&x);
+#pragma unroll
+            for (int u = 0; u < E; ++u) xp[u] = v[c * E + u];
+            reinterpret_cast<V *>(col)[c] = x;
+        }
+        __syncwarp();
+        if (!diag && vec) {
+            T *g = const_cast<T *>(gbase) + r0;
+            const T *d = sl.tile + col0 * SD + ch * E;
+#pragma unroll
+            for (int t = 0; t < CPL; ++t)
+                if ((colmask >> t & 1u) && CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld, n, ld) &&
+                    CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld + E - 1, n, ld))
+                    st16_hint(reinterpret_cast<V *>(g + (long long)t * cstep * ld), *reinterpret_cast<const V *>(d + t * cstep * SD),
+                              pol);
+        } else {
+#pragma unroll 8
+            for (int cc = 0; cc < kB; ++cc)
+                if (c0 + cc < n && (!diag || lane <= cc) && CHK_TRI(sy, (r0 + lane) + (c0 + cc) * ld, n, ld))
+                    A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
+        }
+        __syncwarp();
+    }
+    cp_wait<0>();
+    __syncwarp();
+    return alive;
+}
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args<T> A)
+{
+    using C = SweepCfg<T, KB>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * C::NSLOT;
+    const SyncArgs sy = sync_of(A);
+    if (!ws_ok<T, KB>(A, sy)) return;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = atomicAdd(A.ctl + kCtlSweepTicket, 1);
         tk = __shfl_sync(0xffffffffu, tk, 0);
         if (tk >= A.ntasks) return;
-        // segment sg of column block b: row blocks rb .. re (the last
-        // segment ends at the diagonal tile)
         const int2 task = __ldg(A.tasks + tk);
-        const int b = task.x, sg = task.y;
-        const int nseg = 1 + max(0, (b - A.d - 1) / A.seg);
-        if (b < 0 || b >= nb || sg < 0 || sg >= nseg) {
-            // not a task of this pass (an internal invariant, checked in every build)
-            if (lane == 0) record_error(sy, kStatusBounds, (long long)b);
+        if (!sweep_segment<T, KB, C::NSLOT>(A, sy, task.x, task.y, slot)) return;
+    }
+}
+
+// ---------------------------------------------------------------- fused pass
+
+// After the far sums are all taken, a worker warp of a fused pass takes the
+// coefficient and sweep tasks in the host's order: every task's inputs come
+// from the chain, the far-sum workers or tasks earlier in the order, so the
+// warps that wait always wait on work that is running.
+template <typename T, int KB>
+struct FusedCfg {
+    static constexpr size_t warp_bytes = WorkerCfg<T, KB>::warp_bytes;
+    static constexpr int fit = (int)(warp_bytes / sizeof(SweepSlot<T, KB>));
+    static constexpr int NSLOT = fit > 3 ? 3 : (fit < 2 ? 2 : fit);
+    // a worker warp's shared memory holds two sweep slots and a coefficient
+    // task's Gram rows (up to 8 vectors per pass)
+    static constexpr bool ok = fit >= 2 && Packed<KB>::smem <= warp_bytes;
+};
+
+template <typename T, int KB>
+__device__ void post_tasks(const Args<T> &A, const SyncArgs &sy, unsigned char *wsmem)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int tk = 0;
+        if (lane == 0) tk = aborted(sy) ? (1 << 30) : atomicAdd(A.ctl + kCtlPostTicket, 1);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk >= A.npost) return;
+        const int2 t = __ldg(A.post + tk);
+        if (t.x < 0) {
+            const int r = t.y;
+            if (r < 0 || r >= A.nb) {
+                if (lane == 0) record_error(sy, kStatusBounds, (long long)r);
+                return;
+            }
+            if (!coef_block<T, KB>(A, sy, r, reinterpret_cast<double *>(wsmem), true)) return;
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                st_release_gpu(A.cflag + r, A.epoch);
+            }
+        } else if (!sweep_segment<T, KB, FusedCfg<T, KB>::NSLOT>(A, sy, t.x, t.y,
+                                                                 reinterpret_cast<SweepSlot<T, KB> *>(wsmem))) {
             return;
         }
-        const int rb = sg * A.seg, re = sg == nseg - 1 ? b : rb + A.seg - 1;
-        const long long c0 = (long long)b * kB;
-        const bool active = c0 + lane < n;
-        T uh[KB];
-        if (sg == 0) {
-#pragma unroll
-            for (int q = 0; q < KB; ++q)
-                uh[q] = (active && q < A.kb && CHK_RECT(sy, c0 + lane + q * A.ldv, n, A.kb, A.ldv)) ? A.V[c0 + lane + q * A.ldv]
-                                                                                                   : T(0);
-        } else {
-            // the carry entering row block rb, rebuilt from the substitution's
-            // residual w there: u_hat = |D|^{-1} L^{-1} w with H = L D L^T the
-            // prefix Gram before the block (the scaled rotations' carry is
-            // this linear image of the residual at every row)
-            const T *w = A.snap + (((size_t)(sg - 1) * nb + b) * kB + lane) * KB;
-            const double *h = A.rst + (size_t)(sg - 1) * (KB * (KB + 1) / 2);
-            double z[KB];
-#pragma unroll
-            for (int q = 0; q < KB; ++q) {
-                if (q < A.kb) {
-                    double zq = active ? (double)w[q] : 0.0;
-#pragma unroll
-                    for (int m = 0; m < q; ++m) zq -= __ldg(h + pidx(q, m)) * z[m];
-                    z[q] = zq;
-                    uh[q] = (T)(zq / (sigma_of(A, q) * __ldg(h + pidx(q, q))));
-                } else {
-                    z[q] = 0.0;
-                    uh[q] = T(0);
-                }
-            }
-        }
-        // per-lane addresses of the staged chunks (vector path)
-        const long long gofs = (long long)ch * E + (c0 + col0) * ld;
-        const T *gbase = A.L + gofs;
-        unsigned colmask = 0;
-#pragma unroll
-        for (int t = 0; t < CPL; ++t)
-            if (c0 + col0 + t * cstep < n) colmask |= 1u << t;
-        auto fetch = [&](int r) {
-            SweepSlot<T, KB> &sl = slot[r % C::NSLOT];
-            const long long r0 = (long long)r * kB;
-            if (r < b && vec) {
-                const T *g = gbase + r0;
-                T *d = sl.tile + col0 * SD + ch * E;
-#pragma unroll
-                for (int t = 0; t < CPL; ++t) {
-                    if ((colmask >> t & 1u) && CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld, n, ld) &&
-                        CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld + E - 1, n, ld))
-                        cp16(d + t * cstep * SD, g + (long long)t * cstep * ld);
-                    else {
-#pragma unroll
-                        for (int u = 0; u < E; ++u) d[t * cstep * SD + u] = T(0);
-                    }
-                }
-            } else if (r < b) {
-                stage_tile(sy, sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
-            } else {
-                // the diagonal tile: rows <= column only
-                for (int col = 0; col < kB; ++col)
-                    if (c0 + col < n && lane <= col && CHK_TRI(sy, (r0 + lane) + (c0 + col) * ld, n, ld))
-                        cp_elem(&sl.tile[col * SD + lane], A.L + (r0 + lane) + (c0 + col) * ld);
-            }
-            const T *cf = A.coef + (size_t)r0 * 2 * KB;
-            for (int c = lane; c < kB * 2 * KB / E; c += 32) cp16(sl.cf + c * E, cf + c * E);
-            if (lane < kB / E) cp16(sl.e + lane * E, A.escale + r0 + lane * E);
-            if (r == b && lane < kB / 2) cp16(sl.df + 2 * lane, A.dfac + r0 + 2 * lane);
-        };
-        for (int r = rb; r < rb + C::NSLOT - 1; ++r) {
-            if (r <= re) fetch(r);
-            cp_commit();
-        }
-        for (int r = rb; r <= re; ++r) {
-            if (r + C::NSLOT - 1 <= re) fetch(r + C::NSLOT - 1);
-            cp_commit();
-            cp_wait<C::NSLOT - 1>();
-            __syncwarp();
-            SweepSlot<T, KB> &sl = slot[r % C::NSLOT];
-            const bool diag = r == b;
-            const long long r0 = (long long)r * kB;
-            T v[kB];
-            V *colv = reinterpret_cast<V *>(sl.tile + lane * SD);
-#pragma unroll
-            for (int c = 0; c < kB / E; ++c) {
-                const V x = colv[c];
-#pragma unroll
-                for (int u = 0; u < E; ++u) v[c * E + u] = vget<T>(x, u);
-            }
-            if (!diag) {
-                if (active) rotate_full<T, KB>(v, uh, sl.cf, sl.e);
-            } else if (active) {
-                // rows above the diagonal of column `lane`, then the diagonal
-#pragma unroll
-                for (int i = 0; i < kB; ++i) {
-                    if (i < lane) {
-                        T x = v[i];
-#pragma unroll
-                        for (int q = 0; q < KB; ++q) {
-                            x = fma(sl.cf[i * 2 * KB + 2 * q], uh[q], x);
-                            uh[q] = fma(-sl.cf[i * 2 * KB + 2 * q + 1], x, uh[q]);
-                        }
-                        v[i] = x * sl.e[i];
-                    } else if (i == lane) {
-                        v[i] = (T)((double)v[i] * sl.df[i]);
-                    }
-                }
-            }
-            T *col = sl.tile + lane * SD;
-#pragma unroll
-            for (int c = 0; c < kB / E; ++c) {
-                V x;
-                T *xp = reinterpret_cast<T *>(&x);
-#pragma unroll
-                for (int u = 0; u < E; ++u) xp[u] = v[c * E + u];
-                reinterpret_cast<V *>(col)[c] = x;
-            }
-            __syncwarp();
-            if (!diag && vec) {
-                T *g = const_cast<T *>(gbase) + r0;
-                const T *d = sl.tile + col0 * SD + ch * E;
-#pragma unroll
-                for (int t = 0; t < CPL; ++t)
-                    if ((colmask >> t & 1u) && CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld, n, ld) &&
-                        CHK_TRI(sy, gofs + r0 + (long long)t * cstep * ld + E - 1, n, ld))
-                        *reinterpret_cast<V *>(g + (long long)t * cstep * ld) = *reinterpret_cast<const V *>(d + t * cstep * SD);
-            } else {
-#pragma unroll 8
-                for (int cc = 0; cc < kB; ++cc)
-                    if (c0 + cc < n && (!diag || lane <= cc) && CHK_TRI(sy, (r0 + lane) + (c0 + cc) * ld, n, ld))
-                        A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
-            }
-            __syncwarp();
-        }
-        cp_wait<0>();
+    }
+}
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(kTrsmWarps * 32, 1) trsm_kernel(Args<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_role;
+    if (!ws_ok<T, KB>(A, sync_of(A))) return;
+    if (threadIdx.x == 0) s_role = atomicAdd(A.ctl + kCtlRole, 1);
+    __syncthreads();
+    if (s_role == 0) {
+        trsm_chain<T, KB>(A, smem);
+        return;
+    }
+    const bool more = trsm_workers<T, KB>(A, smem);
+    if constexpr (FusedCfg<T, KB>::ok) {
+        const int warp = threadIdx.x >> 5;
+        if (A.fused && more && warp < WorkerCfg<T, KB>::warps)
+            post_tasks<T, KB>(A, sync_of(A), smem + (size_t)warp * WorkerCfg<T, KB>::warp_bytes);
     }
 }
 

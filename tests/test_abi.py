@@ -241,3 +241,13 @@ def test_tuning_cache_file_round_trip_and_lookup(tmp_path):
     assert chm.chm_tune(10, 1, 5, None) == chm.CHM_ERR_ARG
     assert chm.chm_tune_clear() == chm.CHM_OK
     assert chm.path_for(3000, 6, chm.CHM_F32_MIXED) == chm.PATH_WAVE
+
+
+def test_fused_pass_setting():
+    assert chm.config_get("pass_fused") == 1
+    assert chm.chm_config_set(b"pass_fused", 2) == chm.CHM_ERR_ARG
+    chm.config_set("pass_fused", 0)
+    try:
+        assert chm.config_get("pass_fused") == 0
+    finally:
+        chm.config_set("pass_fused", 1)

@@ -47,11 +47,16 @@ def ref(L, V, sig):
     return st, info, o
 
 
+@pytest.mark.parametrize("fused", [1, 0])
 @pytest.mark.parametrize("kb", [1, 2, 3, 8, 16])
 @pytest.mark.parametrize("d", [2, 3, 8])
-def test_vectors_per_pass_and_lookahead(kb, d):
+def test_vectors_per_pass_and_lookahead(kb, d, fused):
+    """Both forms of a pass: fused (the substitution kernel's workers form
+    the coefficients and sweep as their inputs arrive; up to 8 vectors per
+    pass) and the six-kernel sequence."""
     chm.config_set("pass_kb", kb)
     chm.config_set("pass_d", d)
+    chm.config_set("pass_fused", fused)
     try:
         for n, k, pad in [(33, 5, 1), (200, 16, 0), (611, 19, 3)]:
             seed = 77 + n + k + kb
@@ -65,11 +70,13 @@ def test_vectors_per_pass_and_lookahead(kb, d):
     finally:
         chm.config_set("pass_kb", 0)
         chm.config_set("pass_d", 0)
+        chm.config_set("pass_fused", 1)
 
 
+@pytest.mark.parametrize("fused", [1, 0])
 @pytest.mark.parametrize("seg", [1, 2, 5])
 @pytest.mark.parametrize("kb,d", [(1, 2), (3, 4), (16, 3)])
-def test_sweep_segments_restart_from_residuals(seg, kb, d):
+def test_sweep_segments_restart_from_residuals(seg, kb, d, fused):
     """Short sweep segments (every seg row blocks a column's carry is rebuilt
     from the substitution's partial residual and the prefix Gram's LDL^T
     there), so that most tiles of these shapes lie in restarted segments:
@@ -77,6 +84,7 @@ def test_sweep_segments_restart_from_residuals(seg, kb, d):
     chm.config_set("pass_seg", seg)
     chm.config_set("pass_kb", kb)
     chm.config_set("pass_d", d)
+    chm.config_set("pass_fused", fused)
     try:
         for n, k, pad in [(200, 16, 0), (611, 19, 3), (1025, 2, 1)]:
             seed = 31 + n + k + seg
@@ -103,6 +111,7 @@ def test_sweep_segments_restart_from_residuals(seg, kb, d):
         chm.config_set("pass_seg", 0)
         chm.config_set("pass_kb", 0)
         chm.config_set("pass_d", 0)
+        chm.config_set("pass_fused", 1)
 
 
 @pytest.mark.parametrize("n,k", [(1, 1), (2, 2), (31, 1), (32, 16), (64, 1), (95, 4), (1025, 2), (2049, 33)])
