@@ -117,15 +117,18 @@ def measured_fp32_tflops():
     return _ALU["f32"]
 
 
-def launches_per_modification(path, k):
+def launches_per_modification(path, k, dtype="f64"):
     """Kernels of this library one modification launches: the wave kernel once
-    per 64 vectors; the pass kernels six per pass of up to 16 vectors (the
-    inverse diagonal blocks, the forward substitution, the block Grams, their
-    prefix, the coefficients, the sweep)."""
+    per 64 vectors; the pass kernels per pass of up to 16 vectors either two
+    (a fused pass of up to 8: the inverse diagonal blocks, then the forward
+    substitution whose workers also form the coefficients and sweep) or six
+    (the inverse diagonal blocks, the forward substitution, the block Grams,
+    their prefix, the coefficients, the sweep)."""
     from paper_1011_1173_gb300 import chm
     if path == chm.PATH_PASS:
-        kb = chm.config_get("pass_kb")
-        return 6 * ((k + kb - 1) // kb)
+        kb = chm.config_get("pass_kb_f32" if dtype == "f32" else "pass_kb_f64")
+        per = 2 if (kb <= 8 and chm.config_get("pass_fused")) else 6
+        return per * ((k + kb - 1) // kb)
     return (k + 63) // 64
 
 
@@ -339,6 +342,48 @@ def bench_solve(dev, L, reps=5):
     return {"workload": "solve with the bench factor after the timed steps, n=%d float64" % n, "runs": runs}
 
 
+def time_modify_solve(L, L0, U, stream, flush, reps):
+    """One right-hand side: chm_modify_solve (the forward half of the solve
+    fused into the modification's last pass) against the modification
+    followed by chm_solve on the same stream; median ms of each, L and B
+    restored before every timed call."""
+    import torch
+
+    from paper_1011_1173_gb300 import chm, inputs
+    n = L.shape[0]
+    g = torch.Generator(device=L.device).manual_seed(inputs.config_seed(4))
+    B0 = torch.randn((1, n), generator=g, dtype=torch.float64, device=L.device).to(L.dtype)
+    B = B0.clone()
+
+    def timed(fn):
+        ts = []
+        for r in range(reps + 1):
+            L.copy_(L0)
+            B.copy_(B0)
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                ts.append(a.elapsed_time(b))
+        chm.check(chm.status_sync(stream)[0], "modify_solve status")
+        return statistics.median(ts)
+
+    def fused():
+        chm.check(chm.modify_solve(L, U, B, 1, stream=stream), "modify_solve")
+
+    def separate():
+        chm.check(chm.modify(L, U, 1, stream=stream), "modify")
+        chm.check(chm.solve(L, B, stream=stream), "solve")
+
+    out = {"nrhs": 1, "fused_ms": timed(fused), "modify_then_solve_ms": timed(separate)}
+    del B, B0
+    return out
+
+
 def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n=32768, reps=4, tune=True):
     """The large single-factor configuration (n = 32768, an update by U then
     the cancellation-stressed downdate by 0.9 U, the factor built on the
@@ -398,7 +443,9 @@ def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n
             "ms_per_modification": ms, "GBps": gbs, "hbm_frac": gbs / peak_hbm,
             "TFLOPs": flops, "alu_frac": flops / alu_peak,
             "bound": bound, "binding_frac": max(t_hbm, t_alu) / (ms / 1e3),
-            "launches_per_modification": launches_per_modification(path, k)}
+            "launches_per_modification": launches_per_modification(path, k, dt)}
+        if k == 1:
+            rec["modify_solve"] = time_modify_solve(L, L0, U, stream, flush, reps)
         if tune:
             # the autotuner's choice for this shape (chm_tune), then the same
             # timing with the tuned configuration from the cache
@@ -904,7 +951,7 @@ def main():
                 "large": large,
                 "batched": batch, "batched_mixed": batch_mixed, "served": serve, "served_f64": serve_f64,
                 "solve": solve, "host_resident": host,
-                "gpu_launches": 2 * args.steps * launches_per_modification(path, k),
+                "gpu_launches": 2 * args.steps * launches_per_modification(path, k, args.dtype),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -324,6 +324,33 @@ int chm_solve(const void *L, int64_t n, int64_t ld, void *B, int64_t ldb, int64_
               chm_stream_t stream);
 
 /*
+ * Modify, then solve with the modified factor (Sec. 1: the factor is kept
+ * up to date in order to solve with the modified matrix): L <- L~ as
+ * chm_modify_ex does, then B <- (L~^T L~)^{-1} B as chm_solve does.
+ *   L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info  as for
+ *          chm_modify_ex
+ *   B, ldb, nrhs  as for chm_solve (B must not overlap L or V)
+ * Where the modification runs on the pass kernels (large factors, see
+ * chm_config_set), the forward half of the solve is fused into its last
+ * pass: appending L^{-T} B to the factor as extra columns (the factor of
+ * [[A, B], [B^T, c]]), the last pass's substitution carries B's columns
+ * beside V's and a recurrence task applies the pass's rotations to them,
+ * which leaves L~^{-T} B without another crossing of the factor; up to
+ * 8 - (vectors of the last pass) right-hand sides ride that way, the others
+ * take a substitution with the new factor of their own; each group ends
+ * with the back substitution.  Otherwise the two calls follow each other on
+ * the stream.  Precision: CHM_F64 in double; CHM_F32_MIXED as each part of
+ * the pair: a carried right-hand side's forward half in float like the
+ * pass's Apply, the back substitution with double arithmetic on float data.
+ * d_info receives the modification's status; a failure of the solve part
+ * (a diagonal entry not positive) goes to the stream's status word
+ * (chm_status_sync).  k == 0 is chm_solve alone, nrhs == 0 chm_modify_ex
+ * alone.  Returns CHM_OK, CHM_ERR_ARG, CHM_ERR_NOMEM or CHM_ERR_CUDA.
+ */
+int chm_modify_solve(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k, const int8_t *sigma,
+                     int sign, void *B, int64_t ldb, int64_t nrhs, int dtype, chm_stream_t stream, int64_t *d_info);
+
+/*
  * Device memory that chm_update / chm_downdate / chm_modify_ex hold for one
  * factor of order n modified by k vectors (the per-stream workspace; the
  * factor and V themselves are the caller's), for the path the "path"
@@ -388,12 +415,19 @@ int chm_microbench(int which, double *out, int nout);
  * chm_downdate, chm_modify_ex), for tuning and tests; they take effect on
  * the next call and may be changed at any time from one thread.
  *   "path"     0 automatic (default), 1 the wave kernel, 2 the pass kernels
- *   "pass_kb"  update vectors per pass of the pass kernels, 1..16 (0: 16)
+ *   "pass_kb"  update vectors per pass of the pass kernels, 1..16 (0: by
+ *              type, 8 float, 4 double)
  *   "pass_d"   lookahead of the pass kernels' forward-substitution chain in
  *              row blocks, clamped to 2..10 (float) or 2..6 (double) and
  *              further by what the chain block's shared memory holds for
  *              the pass's vectors; 0 is the default per type (10 float,
  *              4 double)
+ *   "pass_seg" row blocks per segment of the pass kernels' sweep tasks
+ *              (0: max(64, row blocks / 16))
+ *   "pass_fused" 1 (default): up to 8 vectors per pass, the substitution
+ *              kernel's worker warps also form the coefficients and sweep,
+ *              each segment as soon as its inputs are out; 0: the sweep
+ *              and the Compute kernels run after the substitution
  * The two paths compute the same factor by the same method (Algorithm 1's
  * rotations, restated exactly) with different work splits:
  *   wave  one persistent launch per 64 vectors; each vector is a wave that
@@ -405,12 +439,13 @@ int chm_microbench(int which, double *out, int nout);
  *         in double), and one sweep that reads and writes each tile of the
  *         factor once for the whole block of vectors.
  * The automatic rule takes the pass kernels when the factor's upper
- * triangle is at least 32 MB (float) or 256 MB with k <= 2 (double), and
+ * triangle is at least 32 MB (float) or 256 MB with k <= 8 (double), and
  * for a factor of order >= 64 in page-locked host memory modified by two or
  * more vectors (it then crosses the CPU-GPU link three times per pass of up
  * to 16 vectors; the wave kernel twice per vector).
- * chm_config_get also answers "pass_d_f32" and "pass_d_f64" (the values in
- * effect) and "checked" (1 in the bounds-checked build).  The bounds-checked
+ * chm_config_get also answers "pass_d_f32", "pass_d_f64", "pass_kb_f32"
+ * and "pass_kb_f64" (the values in effect, tuning cache aside) and
+ * "checked" (1 in the bounds-checked build).  The bounds-checked
  * build also takes "check_cut" (>= 0, default 0): its checks treat each
  * factor as that many columns narrower than declared, so that they report
  * accesses to real, valid memory (a test of the checks themselves; the

@@ -88,6 +88,7 @@ def _open(path, build_if_missing):
         "chm_downdate": ([vp, i64, i64, vp, i64, i32, vp], i32),
         "chm_modify_ex": ([vp, i64, i64, vp, i64, i64, vp, i32, i32, vp, vp], i32),
         "chm_modify_noalloc": ([vp, i64, i64, vp, i64, i64, vp, i32, i32, vp, vp], i32),
+        "chm_modify_solve": ([vp, i64, i64, vp, i64, i64, vp, i32, vp, i64, i64, i32, vp, vp], i32),
         "chm_status_sync": ([vp, vp], i32),
         "chm_status_string": ([i32], ctypes.c_char_p),
         "chm_version": ([], i32),
@@ -292,6 +293,10 @@ def chm_solve(L, n, ld, B, ldb, nrhs, dtype, stream):
     return load().chm_solve(L, n, ld, B, ldb, nrhs, dtype, stream)
 
 
+def chm_modify_solve(L, n, ld, V, ldv, k, sigma, sign, B, ldb, nrhs, dtype, stream, d_info):
+    return load().chm_modify_solve(L, n, ld, V, ldv, k, sigma, sign, B, ldb, nrhs, dtype, stream, d_info)
+
+
 def chm_workspace_bytes(n, k, dtype, out):
     return load().chm_workspace_bytes(n, k, dtype, out)
 
@@ -376,6 +381,27 @@ def solve(L: torch.Tensor, B: torch.Tensor, n=None, stream=None) -> int:
     n = _check_layout(L, B, n)
     return chm_solve(L.data_ptr(), n, L.shape[1], B.data_ptr(), B.shape[1], B.shape[0], dtype_code(L),
                      _stream_handle(stream))
+
+
+def modify_solve(L: torch.Tensor, V: torch.Tensor, B: torch.Tensor, sigma=1, n=None, stream=None,
+                 d_info=None) -> int:
+    """Enqueue L <- modified factor and B <- (L~^T L~)^{-1} B
+    (chm_modify_solve); returns the call's status.
+
+    ``V`` and ``B`` are contiguous (k, ldv) and (nrhs, ldb) tensors (row r =
+    vector or right-hand side r); ``sigma`` is +1, -1, or k signs."""
+    n = _check_layout(L, V, n)
+    _check_layout(L, B, n)
+    k = V.shape[0]
+    if isinstance(sigma, int):
+        sig_ptr, sign = None, int(sigma)
+        keep = None
+    else:
+        keep = (ctypes.c_int8 * k)(*[int(s) for s in sigma])
+        sig_ptr, sign = ctypes.cast(keep, ctypes.c_void_p), 1
+    info_ptr = None if d_info is None else d_info.data_ptr()
+    return chm_modify_solve(L.data_ptr(), n, L.shape[1], V.data_ptr(), V.shape[1], k, sig_ptr, sign,
+                            B.data_ptr(), B.shape[1], B.shape[0], dtype_code(L), _stream_handle(stream), info_ptr)
 
 
 def status_sync(stream=None):

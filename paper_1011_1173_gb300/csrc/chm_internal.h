@@ -118,6 +118,8 @@ struct PassChoice {
 // tuner's candidate while it times one, else the tuning cache (device
 // factors), else the built-in rule and defaults.
 PassChoice choose_path(long long n, long long k, int dtype, bool host_factor);
+// The built-in rule and defaults alone (no settings, no tuning cache).
+PassChoice builtin_choice(long long n, long long k, int dtype, bool host_factor);
 // The tuning cache (chm_tune.cu): the entry for (dtype, floor(log2 n), ceil(log2 k)).
 bool tune_lookup(int dtype, long long n, long long k, PassChoice *out);
 // The configuration the tuner is timing on this thread (null outside chm_tune).
@@ -145,9 +147,22 @@ int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtyp
 // of `words` timestamps that chm_trace_dump writes out (null otherwise).
 // Called under the workspaces' lock.
 long long *trace_buffer(size_t words, cudaStream_t stream);
-// Enqueue the passes of one modification (kb <= 16 vectors each).
+// Enqueue the passes of one modification (kb <= 16 vectors each).  With
+// right-hand sides (B, nrhs > 0; chm_modify_solve) B is then overwritten by
+// (L~^T L~)^{-1} B: the last pass's substitution carries up to 8 - (its
+// update vectors) of them when passes are fused, and its recurrence task
+// turns them into L~^{-T} B; the rest take a substitution of their own with
+// the new factor; each group ends with a back substitution (chm_solve.cu).
+// `sc` must hold the solve's scratch (solve_need) when nrhs > 0.
 int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
                  const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
-                 const PassChoice &ch, const Scratch &sc, PassSpace &ps);
+                 const PassChoice &ch, const Scratch &sc, PassSpace &ps, void *B = nullptr, long long ldb = 0,
+                 long long nrhs = 0);
+// The solve's scratch for a factor of order n (chm_solve.cu).
+ScratchNeed solve_need(long long n);
+// Back substitution with the upper factor L: B <- L^{-1} Y, row i of
+// right-hand side c of Y at Y[i * ys + c * cs] (element type of dtype).
+int solve_back_enqueue(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs,
+                       const void *Y, long long ys, long long cs, int dtype, const Scratch &sc, cudaStream_t stream);
 
 }  // namespace chm

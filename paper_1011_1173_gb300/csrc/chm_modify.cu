@@ -477,6 +477,46 @@ static int modify_dispatch(void *L, long long n, long long ld, const void *V, lo
     });
 }
 
+// chm_modify_solve: the modification, then B <- (L~^T L~)^{-1} B.  On the
+// pass kernels the forward half rides in the last pass (the substitution
+// carries B's columns beside V's, and the recurrence task turns F^{-T} B
+// into L~^{-T} B with the pass's rotations), so that it costs no crossing
+// of the factor of its own; the back substitution follows.  On the wave
+// kernel (factors that stay in L2) the modification and chm_solve follow
+// each other on the stream.
+static int modify_solve_dispatch(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
+                                 const int8_t *sigma, int sign, void *B, long long ldb, long long nrhs, int dtype,
+                                 cudaStream_t stream, long long *d_info)
+{
+    int rc = check_args(L, n, ld, V, ldv, k, sigma, sign, dtype);
+    if (rc != CHM_OK) return rc;
+    const size_t elt = dtype == CHM_F64 ? 8 : 4;
+    if (nrhs < 0 || ldb < std::max(1ll, n)) return CHM_ERR_ARG;
+    if (n > 0 && nrhs > 0 && (!B || ((uintptr_t)B % elt))) return CHM_ERR_ARG;
+    if (n == 0 || nrhs == 0) return modify_dispatch(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info);
+    if (k == 0) {
+        if ((rc = info_init(d_info, 1, stream)) != CHM_OK) return rc;
+        return chm_solve(L, n, ld, B, ldb, nrhs, dtype, (chm_stream_t)stream);
+    }
+    if ((rc = check_reachable(L)) != CHM_OK || (rc = check_reachable(V)) != CHM_OK ||
+        (rc = check_reachable(B)) != CHM_OK)
+        return rc;
+    const PassChoice ch = choose_path(n, k, dtype, is_host_memory(L));
+    if (ch.path == 2) {
+        // the solve's scratch first (the stream's workspace, grown under its
+        // own hold of the lock), then the passes on the same workspace
+        if ((rc = with_stream_scratch(stream, solve_need(n), [](const Scratch &) { return (int)CHM_OK; })) != CHM_OK)
+            return rc;
+        return with_pass_workspace(stream, pass_workspace_bytes(n, dtype, ch.seg), n, dtype,
+                                   [&](const Scratch &sc, PassSpace &ps) {
+                                       return pass_enqueue(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info,
+                                                           ch, sc, ps, B, ldb, nrhs);
+                                   });
+    }
+    if ((rc = modify_dispatch(L, n, ld, V, ldv, k, sigma, sign, dtype, stream, d_info)) != CHM_OK) return rc;
+    return chm_solve(L, n, ld, B, ldb, nrhs, dtype, (chm_stream_t)stream);
+}
+
 int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtype,
                         const std::function<int(const Scratch &, PassSpace &)> &fn)
 {
@@ -645,6 +685,13 @@ int chm_modify_ex(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, in
 {
     return chm::modify_dispatch(L, n, ld, V, ldv, k, sigma, sign, dtype, (cudaStream_t)stream,
                                 reinterpret_cast<long long *>(d_info));
+}
+
+int chm_modify_solve(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k, const int8_t *sigma,
+                     int sign, void *B, int64_t ldb, int64_t nrhs, int dtype, chm_stream_t stream, int64_t *d_info)
+{
+    return chm::modify_solve_dispatch(L, n, ld, V, ldv, k, sigma, sign, B, ldb, nrhs, dtype, (cudaStream_t)stream,
+                                      reinterpret_cast<long long *>(d_info));
 }
 
 int chm_modify_noalloc(void *L, int64_t n, int64_t ld, const void *V, int64_t ldv, int64_t k,

@@ -63,7 +63,15 @@ static int clamp_kb(int v) { return std::max(1, std::min(pass::kMaxKb, v)); }
 // each instantiation clamps the lookahead further to what its shared memory holds
 static int clamp_d(int v, int dtype) { return std::max(2, std::min(dtype == CHM_F64 ? 6 : 10, v)); }
 
-static int pass_kb_max() { return clamp_kb(kb_setting() > 0 ? kb_setting() : pass::kMaxKb); }
+// Vectors per pass by default: the largest block a fused pass takes in
+// float (8); in double 4, where the chain block's FP64 issue rate, which
+// grows with the vectors, sets a step's time (measured at n = 32768: a
+// rank-16 modification takes 7.1 ms in float with 8 vectors per pass
+// against 7.8 with 16 and 8.3 with 4; in double 50.1 ms with 4 or 8
+// against 77 with 16).
+static int default_kb(int dtype) { return dtype == CHM_F64 ? 4 : 8; }
+
+static int pass_kb_of(int dtype) { return clamp_kb(kb_setting() > 0 ? kb_setting() : default_kb(dtype)); }
 
 static int pass_d(int dtype) { return clamp_d(d_setting() > 0 ? d_setting() : (dtype == CHM_F64 ? 4 : 10), dtype); }
 
@@ -86,23 +94,29 @@ int path_setting()
 
 // The built-in rule: the pass path once the factor is larger than about a
 // third of L2 (where the wave kernel's waves start to re-stream it); in
-// float64 only for few vectors, where the wave kernel's chain, not the FP64
-// rate, bounds it; and for a factor in page-locked host memory with two or
-// more vectors (the pass crosses the CPU-GPU link three times per block of
-// up to 16 vectors, the wave kernel twice per vector).
+// float64 only up to 8 vectors: beyond that both paths run at the FP64 rate
+// (n = 32768: 25.0 against 25.9 ms at k = 8, 50.1 against 50.1 at k = 16,
+// the wave kernel ahead at k = 64); and for a factor in page-locked host
+// memory with two or more vectors (the pass crosses the CPU-GPU link three
+// times per block of vectors, the wave kernel twice per vector).
 static bool rule_pass(long long n, long long k, int dtype, bool host_factor)
 {
     if (host_factor) return n >= 64 && k >= 2;
     const double bytes = (double)(dtype == CHM_F64 ? 8 : 4) * n * n / 2;
-    if (dtype == CHM_F64) return bytes >= 256e6 && k <= 2;
+    if (dtype == CHM_F64) return bytes >= 256e6 && k <= 8;
     return bytes >= 32e6;
+}
+
+PassChoice builtin_choice(long long n, long long k, int dtype, bool host_factor)
+{
+    return PassChoice{rule_pass(n, k, dtype, host_factor) ? 2 : 1, default_kb(dtype), dtype == CHM_F64 ? 4 : 10, 0, 1};
 }
 
 PassChoice choose_path(long long n, long long k, int dtype, bool host_factor)
 {
     // precedence: explicit settings, then the tuner's candidate while it
     // times one, then the tuning cache (device factors), then the defaults
-    PassChoice base{rule_pass(n, k, dtype, host_factor) ? 2 : 1, pass::kMaxKb, dtype == CHM_F64 ? 4 : 10, 0};
+    PassChoice base = builtin_choice(n, k, dtype, host_factor);
     PassChoice tuned;
     if (const PassChoice *o = tune_override()) base = *o;
     else if (!host_factor && tune_lookup(dtype, n, k, &tuned)) base = tuned;
@@ -306,15 +320,16 @@ int launch_pass(pass::Args<T> A, PassSpace &ps, cudaStream_t s)
     const int nb = A.nb;
     A.d = std::min(A.d, pass::ChainCfg<T, KB>::DMAX);
     A.c = std::min(A.d, pass::ChainCfg<T, KB>::CMAX);
-    // a fused pass (up to 8 vectors per pass)
-    A.fused = A.fused && pass::FusedCfg<T, KB>::ok;
+    // a fused pass (up to 8 vectors per pass); a pass that rotates nothing
+    // (right-hand sides only) is the substitution alone
+    A.fused = A.fused && pass::FusedCfg<T, KB>::ok && A.kr > 0;
     if ((rc = sweep_tasks(ps, A.nb, A.d, A.seg, const_cast<int2 *>(A.tasks), const_cast<int2 *>(A.post), &A.ntasks,
                           &A.npost, s)) != CHM_OK)
         return rc;
     if (cudaMemsetAsync(A.ctl, 0, pass::kCtlInts * sizeof(int), s) != cudaSuccess) return CHM_ERR_CUDA;
     pass::prep_kernel<T><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::trsm_kernel<T, KB><<<nsm, pass::kTrsmWarps * 32, trsm_smem<T, KB>(), s>>>(A);
-    if (A.fused) return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
+    if (A.fused || A.kr == 0) return cudaGetLastError() == cudaSuccess ? CHM_OK : CHM_ERR_CUDA;
     pass::gram_kernel<T, KB><<<std::min(nb, nsm * 16), 32, 0, s>>>(A);
     pass::scan_kernel<T, KB><<<(KB * KB + 31) / 32, 1024, 0, s>>>(A);
     pass::coef_kernel<T, KB><<<std::min(nb, nsm * 8), 32, pass::Packed<KB>::smem, s>>>(A);
@@ -333,10 +348,13 @@ int launch_pass_kb(const pass::Args<T> &A, PassSpace &ps, cudaStream_t s)
     return launch_pass<T, 16>(A, ps, s);
 }
 
+// The kernels' instantiation for kb vectors: the next power of two (P's row stride).
+int kb_instance(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : kb <= 8 ? 8 : 16; }
+
 template <typename T>
 int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, long long k,
                    const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
-                   const PassChoice &ch, const Scratch &sc, PassSpace &ps)
+                   const PassChoice &ch, const Scratch &sc, PassSpace &ps, T *B, long long ldb, long long nrhs)
 {
     const PassLayout lay = pass_layout(n, sizeof(T), ch.seg);
     char *w = ps.buf;
@@ -374,18 +392,44 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.status = sc.status;
     A.user_info = d_info;
     A.timeout_ns = timeout_ns();
+    A.ldb = ldb;
     const int kbmax = ch.kb;
+    // right-hand sides the last pass carries: as many as keep it a fused
+    // pass of at most 8 vectors (its recurrence task then follows the chain)
+    const int kr_last = k > 0 ? (int)(k - ((k - 1) / kbmax) * kbmax) : 0;
+    const long long nr1 = (nrhs > 0 && k > 0 && ch.fused) ? std::min<long long>(nrhs, std::max(0, 8 - kr_last)) : 0;
     for (long long q0 = 0; q0 < k; q0 += kbmax) {
-        const int kb = (int)std::min<long long>(kbmax, k - q0);
+        const int kr = (int)std::min<long long>(kbmax, k - q0);
+        const int nr = q0 + kbmax >= k ? (int)nr1 : 0;
         A.V = V + q0 * ldv;
-        A.kb = kb;
+        A.kr = kr;
+        A.kb = kr + nr;
+        A.B = nr > 0 ? B : nullptr;
         unsigned long long mask = 0;
-        for (int q = 0; q < kb; ++q)
+        for (int q = 0; q < kr; ++q)
             if ((sigma ? sigma[q0 + q] : sign) < 0) mask |= 1ull << q;
         A.down_mask = mask;
         A.epoch = ++ps.epoch;
         A.trace = trace_buffer((size_t)A.nb * 16, stream);  // the last pass's, with CHM_TRACE=1
-        const int rc = launch_pass_kb<T>(A, ps, stream);
+        int rc = launch_pass_kb<T>(A, ps, stream);
+        // the carried right-hand sides: L~^{-T} B stands in P's columns kr ..
+        if (rc == CHM_OK && nr > 0)
+            rc = solve_back_enqueue(L, n, ld, B, ldb, nr, A.P + kr, kb_instance(A.kb), 1, dtype, sc, stream);
+        if (rc != CHM_OK) return rc;
+    }
+    // the other right-hand sides, up to 16 at a time: the substitution with
+    // the new factor (a pass that rotates nothing), then the back substitution
+    for (long long r0 = nr1; r0 < nrhs; r0 += pass::kMaxKb) {
+        const int nr = (int)std::min<long long>(pass::kMaxKb, nrhs - r0);
+        A.V = nullptr;
+        A.kr = 0;
+        A.kb = nr;
+        A.B = B + r0 * ldb;
+        A.down_mask = 0;
+        A.epoch = ++ps.epoch;
+        A.trace = nullptr;
+        int rc = launch_pass_kb<T>(A, ps, stream);
+        if (rc == CHM_OK) rc = solve_back_enqueue(L, n, ld, B + r0 * ldb, ldb, nr, A.P, kb_instance(nr), 1, dtype, sc, stream);
         if (rc != CHM_OK) return rc;
     }
     return CHM_OK;
@@ -395,15 +439,16 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
 
 int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
                  const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
-                 const PassChoice &ch, const Scratch &sc, PassSpace &ps)
+                 const PassChoice &ch, const Scratch &sc, PassSpace &ps, void *B, long long ldb, long long nrhs)
 {
     int rc = info_init(d_info, 1, stream);
     if (rc != CHM_OK) return rc;
     if (dtype == CHM_F64)
         return enqueue_passes<double>(static_cast<double *>(L), n, ld, static_cast<const double *>(V), ldv, k,
-                                      sigma, sign, dtype, stream, d_info, ch, sc, ps);
+                                      sigma, sign, dtype, stream, d_info, ch, sc, ps, static_cast<double *>(B), ldb,
+                                      nrhs);
     return enqueue_passes<float>(static_cast<float *>(L), n, ld, static_cast<const float *>(V), ldv, k, sigma,
-                                 sign, dtype, stream, d_info, ch, sc, ps);
+                                 sign, dtype, stream, d_info, ch, sc, ps, static_cast<float *>(B), ldb, nrhs);
 }
 
 }  // namespace chm
@@ -452,7 +497,9 @@ int chm_config_get(const char *key, int64_t *value)
 {
     if (!key || !value) return CHM_ERR_ARG;
     if (!strcmp(key, "path")) *value = chm::g_path.load();
-    else if (!strcmp(key, "pass_kb")) *value = chm::pass_kb_max();
+    else if (!strcmp(key, "pass_kb")) *value = chm::kb_setting();  // 0: by type
+    else if (!strcmp(key, "pass_kb_f32")) *value = chm::pass_kb_of(CHM_F32_MIXED);
+    else if (!strcmp(key, "pass_kb_f64")) *value = chm::pass_kb_of(CHM_F64);
     else if (!strcmp(key, "pass_d_f32")) *value = chm::pass_d(CHM_F32_MIXED);
     else if (!strcmp(key, "pass_d_f64")) *value = chm::pass_d(CHM_F64);
     else if (!strcmp(key, "pass_seg")) *value = chm::seg_setting();

@@ -52,6 +52,7 @@ constexpr int kCtlRole = 1;         // thread blocks of the substitution started
 constexpr int kCtlSweepTicket = 2;  // next sweep task
 constexpr int kCtlAbort = 3;        // non-zero once a wait has timed out
 constexpr int kCtlPostTicket = 4;   // next coefficient or sweep task of a fused pass
+constexpr int kCtlAugTicket = 5;    // the right-hand sides' recurrence (one task)
 constexpr int kCtlInts = 16;
 
 template <typename T>
@@ -61,6 +62,11 @@ struct Args {
     long long n, ld, ldv;
     int nb;                         // row blocks
     int kb;                         // vectors of this pass (<= KB of the kernels)
+    int kr;                         // the first kr of them rotate the factor (update vectors);
+                                    // vectors kr .. kb - 1 are right-hand sides the substitution
+                                    // carries along (chm_modify_solve): columns of B
+    const T *B;                     // right-hand sides: vector q >= kr is column q - kr of B
+    long long ldb;
     int d;                          // lookahead of the substitution chain (near tiles)
     int c;                          // offsets the chain's critical warp takes (G^(1..c))
     int epoch;                      // tags this pass's flags
@@ -117,6 +123,19 @@ __device__ __forceinline__ SyncArgs sync_of(const Args<T> &A)
     return s;
 }
 
+// Entry (row, q) of the pass's input vectors: column q of V for the update
+// vectors (q < kr), column q - kr of B for the right-hand sides (q < kb),
+// zero past them and past the order.
+template <typename T>
+__device__ __forceinline__ T vin(const Args<T> &A, const SyncArgs &sy, long long row, int q)
+{
+    (void)sy;
+    if (row >= A.n || q >= A.kb) return T(0);
+    if (q < A.kr) return CHK_RECT(sy, row + q * A.ldv, A.n, A.kr, A.ldv) ? A.V[row + q * A.ldv] : T(0);
+    const int c = q - A.kr;
+    return CHK_RECT(sy, row + c * A.ldb, A.n, A.kb - A.kr, A.ldb) ? A.B[row + c * A.ldb] : T(0);
+}
+
 // Bounds-checked builds: every workspace region a kernel with KB vectors
 // per pass indexes lies inside the workspace allocation, and the pass's
 // shape fits the regions (the kernel returns at once otherwise).
@@ -126,7 +145,8 @@ __device__ __forceinline__ bool ws_ok(const Args<T> &A, const SyncArgs &sy)
 #ifdef CHM_CHECK
     const size_t nb = (size_t)A.nb, rows = nb * kB, e = sizeof(T);
     const size_t tagw = e / 4;  // 64-bit words of one tagged value
-    return CHK_RECT(sy, (long long)A.kb, KB + 1, 1, 1 << 30) && CHK_RECT(sy, (long long)A.c, kMaxCrit + 1, 1, 1 << 30) &&
+    return CHK_RECT(sy, (long long)A.kb, KB + 1, 1, 1 << 30) && CHK_RECT(sy, (long long)A.kr, (long long)A.kb + 1, 1, 1 << 30) &&
+           CHK_RECT(sy, (long long)A.c, kMaxCrit + 1, 1, 1 << 30) &&
            CHK_RECT(sy, A.n, (long long)rows + 1, 1, 1ll << 62) &&
            CHK_REGION(sy, A.P, rows * KB * e, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.Ptag, rows * KB * tagw * 8, A.ws, A.ws_bytes) &&
@@ -289,6 +309,11 @@ __device__ __forceinline__ void cp16(void *smem, const void *gmem)
 __device__ __forceinline__ void prefetch_l2(const void *gmem)
 {
     asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(gmem));
+}
+// A plain prefetch into L2 (normal eviction priority).
+__device__ __forceinline__ void prefetch_l2n(const void *gmem)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(gmem));
 }
 // An L2 policy that evicts first: the sweep's tiles are read and written
 // once, so they should not push out what the chain block prefetched.
@@ -488,6 +513,12 @@ __device__ __forceinline__ bool get_tag(const long long *w, long long ep64, doub
 // Every lane reads its KB tagged values (a row of P) until all of the
 // warp's words carry the epoch; sleeps between polls up to max_ns.  False if
 // the launch is being aborted or the wait ran out (recorded).
+//
+// While the row is not out, the warp polls one word of it (the last word
+// lane 31's row gets, the publisher's last store): one L2 request per poll
+// instead of 32 KB words.  A thousand worker warps may be waiting on the
+// same row at the front of the chain, and their full-row polls, KB times
+// heavier, slow the L2 slices that the chain's own stores go to.
 template <typename T, int KB>
 __device__ __forceinline__ bool warp_tagged_row(const SyncArgs &sy, const long long *src, long long ep64, T (&v)[KB],
                                                 unsigned max_ns, long long who)
@@ -498,16 +529,30 @@ __device__ __forceinline__ bool warp_tagged_row(const SyncArgs &sy, const long l
     for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &v[q]) && ok;
     if (__all_sync(0xffffffffu, ok)) return true;
     const long long t0 = global_ns();
+    const long long *probe = reinterpret_cast<const long long *>(
+                                 __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(src), 31)) +
+                             (KB - 1) * TW;
+    bool probing = true;  // warp-uniform: the probe phase, then the full-row phase
     unsigned ns = 16;
     for (unsigned it = 1;; ++it) {
         __nanosleep(ns);
         if (ns < max_ns) ns <<= 1;
-        if (!ok) {
-            ok = true;
-#pragma unroll
-            for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &v[q]) && ok;
+        if (probing) {
+            // every lane loads the same word: one request for the warp
+            const bool out = (ld_relaxed_gpu(probe) & ~0xffffffffll) == ep64;
+            if (__any_sync(0xffffffffu, out)) {
+                probing = false;
+                ns = 16;
+            }
         }
-        if (__all_sync(0xffffffffu, ok)) return true;
+        if (!probing) {
+            if (!ok) {
+                ok = true;
+#pragma unroll
+                for (int q = 0; q < KB; ++q) ok = get_tag(src + q * TW, ep64, &v[q]) && ok;
+            }
+            if (__all_sync(0xffffffffu, ok)) return true;
+        }
         if ((it & 15u) == 0u) {
             int bad = 0;
             if ((threadIdx.x & 31) == 0) {
@@ -813,7 +858,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 #pragma unroll
         for (int u = 0; u < NL; ++u) {
             const int e = lane + 32 * u, q = e / KB, r = e % KB;
-            h[u] = (e < NE && q == r) ? (q < A.kb ? sigma_of(A, q) : 1.0) : 0.0;
+            h[u] = (e < NE && q == r) ? (q < A.kr ? sigma_of(A, q) : 1.0) : 0.0;
         }
         for (int m = 0; m < nb; ++m) {
             // H_m (it needs only the blocks before m) to the publisher first
@@ -834,7 +879,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             for (int u = 0; u < NL; ++u) {
                 const int e = lane + 32 * u, q = e / KB, r = e % KB;
                 g[u] = 0.0;
-                if (e < NE) g[u] = gram_entry(pm, KS, q, r);
+                if (e < NE && q < A.kr && r < A.kr) g[u] = gram_entry(pm, KS, q, r);  // update vectors only
             }
             __syncwarp();
             mb_arrive(&S.p_empty[m % C::RP]);
@@ -969,8 +1014,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             } else {
 #pragma unroll
                 for (int q = 0; q < KB; ++q)
-                    w[q] = (r0 + lane < n && q < A.kb && CHK_RECT(sy, r0 + lane + q * A.ldv, n, A.kb, A.ldv))
-                               ? A.V[r0 + lane + q * A.ldv] : T(0);
+                    w[q] = vin(A, sy, r0 + lane, q);
             }
             if (cc + 1 <= d && cc + 1 <= b) {
                 // the near terms, summed by the near warps (offset c + 1 holds all of them)
@@ -1047,6 +1091,9 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 template <typename T, int KB>
 struct WorkerCfg {
     static constexpr int NS = 3;  // staged tiles per warp
+    // tiles prefetched to L2 ahead of the one in use: about 32 KB per warp,
+    // 32 MB over a thousand workers at the front of the chain
+    static constexpr int PF = (int)(32768 / (sizeof(T) * kB * kB));
     static constexpr size_t warp_bytes = sizeof(T) * ((size_t)NS * kB * Stride<T>::value + Rows<T, KB>::size);
     static constexpr int warps = (int)((200u * 1024u) / warp_bytes) < kTrsmWarps
                                      ? (int)((200u * 1024u) / warp_bytes) : kTrsmWarps;
@@ -1081,7 +1128,7 @@ __device__ bool trsm_workers(const Args<T> &A, unsigned char *smem)
         T z[KB];
 #pragma unroll
         for (int q = 0; q < KB; ++q)
-            z[q] = (col_ok && q < A.kb && CHK_RECT(sy, c0 + lane + q * A.ldv, n, A.kb, A.ldv)) ? A.V[c0 + lane + q * A.ldv] : T(0);
+            z[q] = col_ok ? vin(A, sy, c0 + lane, q) : T(0);
         const int nfar = b - d;
         for (int r = 0; r < W::NS - 1 && r < nfar; ++r) {
             stage_tile(sy, base + (size_t)(r % W::NS) * kB * SD, A.L, ld, (long long)r * kB, c0, n, kB, vec, lane);
@@ -1107,6 +1154,16 @@ __device__ bool trsm_workers(const Args<T> &A, unsigned char *smem)
             if (rn < nfar)
                 stage_tile(sy, base + (size_t)(rn % W::NS) * kB * SD, A.L, ld, (long long)rn * kB, c0, n, kB, vec, lane);
             cp_commit();
+            // the tile W::PF ahead into L2, so that its staging a few steps
+            // later waits on L2 rather than on HBM (a worker keeps up with
+            // the chain only if a tile arrives within a chain step or two)
+            if (r + W::PF < nfar) {
+                const long long off = (long long)(r + W::PF) * kB + (c0 + lane) * ld;
+                if (col_ok && CHK_TRI(sy, off, n, ld) && CHK_TRI(sy, off + kB - 1, n, ld)) {
+                    prefetch_l2n(A.L + off);
+                    if (sizeof(T) * kB > 128) prefetch_l2n(A.L + off + 128 / sizeof(T));
+                }
+            }
             // P_r: every lane takes its row as tagged words, polling until
             // all carry this pass's epoch (often only near the block's last
             // tiles: the far sum is due when the chain reaches b - d, and a
@@ -1197,7 +1254,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(Args<T> A)
     if (valid) {
         const int q = e / KB, r = e % KB;
         pre = (q == r) ? sigma_of(A, q) : 0.0;
-        if (q >= A.kb || r >= A.kb) pre = (q == r) ? 1.0 : 0.0;  // padding vectors: identity
+        if (q >= A.kr || r >= A.kr) pre = (q == r) ? 1.0 : 0.0;  // padding and right-hand sides: identity
         for (int s2 = 0; s2 < s; ++s2) pre += seg[s2][threadIdx.x & 31];
         for (int b = b0; b < b1; ++b) {
             A.H[(size_t)b * KB * KB + e] = pre;
@@ -1235,7 +1292,7 @@ __device__ bool coef_block(const Args<T> &A, const SyncArgs &sy, int b, double *
     constexpr int NE = PK::entries, HS = PK::stride;
     const int lane = threadIdx.x & 31;
     const long long n = A.n;
-    const int kb = A.kb;
+    const int kb = A.kr;  // the update vectors (right-hand sides take no part in the Compute)
     const long long r0 = (long long)b * kB;
     const int rows = (int)min((long long)kB, n - r0);
     double p[KB];
@@ -1495,8 +1552,7 @@ __device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int s
     if (sg == 0) {
 #pragma unroll
         for (int q = 0; q < KB; ++q)
-            uh[q] = (active && q < A.kb && CHK_RECT(sy, c0 + lane + q * A.ldv, n, A.kb, A.ldv)) ? A.V[c0 + lane + q * A.ldv]
-                                                                                               : T(0);
+            uh[q] = (active && q < A.kr) ? vin(A, sy, c0 + lane, q) : T(0);
     } else {
         // the carry entering row block rb, rebuilt from the substitution's
         // residual w there: u_hat = |D|^{-1} L^{-1} w with H = L D L^T the
@@ -1507,7 +1563,7 @@ __device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int s
         double z[KB];
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
-            if (q < A.kb) {
+            if (q < A.kr) {
                 double zq = active ? (double)__ldcg(w + q) : 0.0;
 #pragma unroll
                 for (int m = 0; m < q; ++m) zq -= __ldcg(h + pidx(q, m)) * z[m];
@@ -1630,6 +1686,91 @@ __device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int s
     return alive;
 }
 
+// The right-hand sides' column (chm_modify_solve).  Bordering A with B,
+//   [[A, B], [B^T, c]] = [[F, Y], [0, g]]^T [[F, Y], [0, g]],  Y = F^{-T} B,
+// and modifying the bordered matrix by V with zero rows below n leaves the
+// border's column of the new factor at L~^{-T} B: the pass's rotations
+// applied to Y as to one more column of the factor, with carries that start
+// at zero (V has no entries there).  So after the substitution has carried
+// B along (P's columns kr .. kb - 1 hold Y), this task runs the sweep's
+// two-FMA recurrence down Y, row block by row block behind the chain, and
+// writes L~^{-T} B over Y in P (read by the solve that follows the pass).
+// One warp; lane = right-hand side.  `sm`: Aug<T, KB>::bytes of shared
+// memory.  In a fused pass a row block waits for its coefficients (and
+// P_r as tagged words); after the pass's Compute kernels it waits for
+// nothing.  Returns false if the launch is being aborted.
+template <typename T, int KB>
+struct Aug {
+    static constexpr int YS = KB + 1;  // row stride of the staged Y rows
+    static constexpr size_t bytes = sizeof(T) * (size_t)kB * (YS + 2 * KB + 1);
+};
+template <typename T, int KB>
+__device__ bool aug_task(const Args<T> &A, const SyncArgs &sy, T *sm, bool fused)
+{
+    constexpr int YS = Aug<T, KB>::YS;
+    constexpr int TW = Tag<T>::words;
+    const int lane = threadIdx.x & 31;
+    const int kr = A.kr, nr = A.kb - A.kr;
+    const long long n = A.n;
+    const long long ep64 = (long long)A.epoch << 32;
+    T *Ys = sm;                      // [32][YS]: row i's P entries
+    T *cf = Ys + kB * YS;            // [32][2 KB]: row i's (a_q, b_q)
+    T *es = cf + kB * 2 * KB;        // [32]: row i's scale
+    T uh[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) uh[q] = T(0);
+    for (int r = 0; r < A.nb; ++r) {
+        const long long r0 = (long long)r * kB;
+        const int rows = (int)min((long long)kB, n - r0);
+        T pv[KB];
+        if (fused) {
+            if (!warp_flag(sy, A.cflag + r, A.epoch, r)) return false;  // row block r's coefficients
+            if (!warp_tagged_row<T, KB>(sy, A.Ptag + (size_t)(r0 + lane) * KB * TW, ep64, pv, 256u, r)) return false;
+        } else {
+#pragma unroll
+            for (int q = 0; q < KB; ++q) pv[q] = __ldcg(A.P + (size_t)(r0 + lane) * KB + q);
+        }
+#pragma unroll
+        for (int q = 0; q < KB; ++q) Ys[lane * YS + q] = pv[q];
+        if (lane < rows) {
+#pragma unroll
+            for (int q = 0; q < 2 * KB; ++q) cf[lane * 2 * KB + q] = __ldcg(A.coef + (size_t)(r0 + lane) * 2 * KB + q);
+            es[lane] = __ldcg(A.escale + r0 + lane);
+        }
+        __syncwarp();
+        if (lane < nr) {
+            for (int i = 0; i < rows; ++i) {
+                T x = Ys[i * YS + kr + lane];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) {
+                    if (q < kr) {
+                        x = fma(cf[i * 2 * KB + 2 * q], uh[q], x);
+                        uh[q] = fma(-cf[i * 2 * KB + 2 * q + 1], x, uh[q]);
+                    }
+                }
+                Ys[i * YS + kr + lane] = x * es[i];
+            }
+        }
+        __syncwarp();
+        if (lane < rows) {
+            for (int q = kr; q < A.kb; ++q) A.P[(size_t)(r0 + lane) * KB + q] = Ys[lane * YS + q];
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// The one task of the right-hand sides' column, if this pass carries any
+// (and rotates anything): taken by the first warp that asks.
+template <typename T, int KB>
+__device__ __forceinline__ bool take_aug(const Args<T> &A)
+{
+    if (A.kb <= A.kr || A.kr == 0) return false;
+    int t = 1;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(A.ctl + kCtlAugTicket, 1);
+    return __shfl_sync(0xffffffffu, t, 0) == 0;
+}
+
 template <typename T, int KB>
 __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args<T> A)
 {
@@ -1639,6 +1780,8 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
     SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * C::NSLOT;
     const SyncArgs sy = sync_of(A);
     if (!ws_ok<T, KB>(A, sy)) return;
+    static_assert(Aug<T, KB>::bytes <= C::NSLOT * sizeof(SweepSlot<T, KB>), "a sweep warp's slots hold the task");
+    if (take_aug<T, KB>(A) && !aug_task<T, KB>(A, sy, reinterpret_cast<T *>(slot), false)) return;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = atomicAdd(A.ctl + kCtlSweepTicket, 1);
@@ -1669,6 +1812,8 @@ template <typename T, int KB>
 __device__ void post_tasks(const Args<T> &A, const SyncArgs &sy, unsigned char *wsmem)
 {
     const int lane = threadIdx.x & 31;
+    static_assert(Aug<T, KB>::bytes <= WorkerCfg<T, KB>::warp_bytes, "a worker warp's shared memory holds the task");
+    if (take_aug<T, KB>(A) && !aug_task<T, KB>(A, sy, reinterpret_cast<T *>(wsmem), true)) return;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = aborted(sy) ? (1 << 30) : atomicAdd(A.ctl + kCtlPostTicket, 1);

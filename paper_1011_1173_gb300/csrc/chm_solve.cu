@@ -44,6 +44,11 @@ struct SolveArgs {
     long long ldb;
     int nb;           // blocks of kW rows
     int nr;           // right-hand sides of this launch (1 .. R)
+    // back substitution only: y = L^{-T} b is given, row i of right-hand
+    // side r at Y[i * ys + r * cs] (chm_modify_solve's pass forms it)
+    const T *Y;
+    long long ys, cs;
+    int back_only;
     double *inv;      // [nb][kW][kW]: U_b = D_b^{-1}, row i at i * kW
     int *yflag;       // [nb]: y_b and U_b published (== epoch)
     long long *ytag;  // [nb][kW][R][2]: y_b as tagged doubles
@@ -152,10 +157,16 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
                             ? (double)__ldg(a.L + c0 - kW + i + (c0 + j) * ld) : 0.0;
     }
     double rhs[R];
+    if (a.back_only) {
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        rhs[r] = (active && r < a.nr && CHK_RECT(sy, c0 + lane + r * a.ldb, a.n, a.nr, a.ldb))
-                     ? (double)a.B[c0 + lane + r * a.ldb] : 0.0;
+        for (int r = 0; r < R; ++r)
+            rhs[r] = (active && r < a.nr) ? (double)__ldcg(a.Y + (c0 + lane) * a.ys + r * a.cs) : 0.0;
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            rhs[r] = (active && r < a.nr && CHK_RECT(sy, c0 + lane + r * a.ldb, a.n, a.nr, a.ldb))
+                         ? (double)a.B[c0 + lane + r * a.ldb] : 0.0;
+    }
     __syncthreads();
 
     if (warp == 0) {
@@ -184,6 +195,17 @@ __device__ void forward_task(const SolveArgs<T> &a, const SyncArgs &sy, long lon
     }
 
     __syncthreads();  // U in shared memory
+
+    if (a.back_only) {
+        // y_b is given: publish it with U_b for this block's backward task
+        if (warp == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) put_tagged(a.ytag + tag_at<R>(b, lane, r), rhs[r], ep64);
+            __syncwarp();
+            if (lane == 0) st_release_gpu(a.yflag + b, sy.epoch);
+        }
+        return;
+    }
 
     // G = U^T S.T^T, the rows j of S.T split over the warps:
     // g[jj] = G[lane][warp * 8 + jj] = sum_m U[m][lane] S.T[warp * 8 + jj][m]
@@ -467,7 +489,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs<T> a)
 
 template <typename T, int R>
 int launch_solve(const void *L, long long n, long long ld, void *B, long long ldb, int nr, const Scratch &sc,
-                 cudaStream_t stream)
+                 cudaStream_t stream, const T *Y = nullptr, long long ys = 0, long long cs = 0)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CHM_ERR_CUDA;
@@ -489,6 +511,10 @@ int launch_solve(const void *L, long long n, long long ld, void *B, long long ld
     a.ldb = ldb;
     a.nb = nb;
     a.nr = nr;
+    a.Y = Y;
+    a.ys = ys;
+    a.cs = cs;
+    a.back_only = Y != nullptr;
     a.inv = reinterpret_cast<double *>(sc.data);
     a.yflag = sc.iflags;
     a.ytag = sc.progress;
@@ -522,6 +548,46 @@ int solve_all(const void *L, long long n, long long ld, void *B, long long ldb, 
     return CHM_OK;
 }
 
+}  // namespace
+
+ScratchNeed solve_need(long long n)
+{
+    const size_t nb = (size_t)((n + kW - 1) / kW);
+    ScratchNeed need;
+    need.iflags = (nb + 63) & ~(size_t)63;
+    need.progress = 2 * nb * kW * kSolveRhs * 2;
+    need.data = nb * kW * kW * sizeof(double);
+    return need;
+}
+
+namespace {
+template <typename T>
+int solve_back_t(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs, const T *Y,
+                 long long ys, long long cs, const Scratch &sc, cudaStream_t stream)
+{
+    T *b = static_cast<T *>(B);
+    for (long long r0 = 0; r0 < nrhs; r0 += kSolveRhs) {
+        const int nr = (int)std::min<long long>(kSolveRhs, nrhs - r0);
+        const T *y = Y + r0 * cs;
+        const int rc = nr == 1 ? launch_solve<T, 1>(L, n, ld, b + r0 * ldb, ldb, 1, sc, stream, y, ys, cs)
+                               : launch_solve<T, kSolveRhs>(L, n, ld, b + r0 * ldb, ldb, nr, sc, stream, y, ys, cs);
+        if (rc != CHM_OK) return rc;
+    }
+    return CHM_OK;
+}
+}  // namespace
+
+int solve_back_enqueue(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs,
+                       const void *Y, long long ys, long long cs, int dtype, const Scratch &sc, cudaStream_t stream)
+{
+    if (n <= 0 || nrhs <= 0) return CHM_OK;
+    return dtype == CHM_F64
+               ? solve_back_t<double>(L, n, ld, B, ldb, nrhs, static_cast<const double *>(Y), ys, cs, sc, stream)
+               : solve_back_t<float>(L, n, ld, B, ldb, nrhs, static_cast<const float *>(Y), ys, cs, sc, stream);
+}
+
+namespace {
+
 int solve_dispatch(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs, int dtype,
                    cudaStream_t stream)
 {
@@ -535,12 +601,7 @@ int solve_dispatch(const void *L, long long n, long long ld, void *B, long long 
     int rc = check_reachable(L);
     if (rc == CHM_OK) rc = check_reachable(B);
     if (rc != CHM_OK) return rc;
-    const size_t nb = (size_t)((n + kW - 1) / kW);
-    ScratchNeed need;
-    need.iflags = (nb + 63) & ~(size_t)63;
-    need.progress = 2 * nb * kW * kSolveRhs * 2;
-    need.data = nb * kW * kW * sizeof(double);
-    return with_stream_scratch(stream, need, [&](const Scratch &sc) {
+    return with_stream_scratch(stream, solve_need(n), [&](const Scratch &sc) {
         return dtype == CHM_F64 ? solve_all<double>(L, n, ld, B, ldb, nrhs, sc, stream)
                                 : solve_all<float>(L, n, ld, B, ldb, nrhs, sc, stream);
     });

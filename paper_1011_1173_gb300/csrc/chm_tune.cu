@@ -144,7 +144,7 @@ int tune_t(long long n, long long k, int dtype, int64_t *result)
         tune_fill<T><<<1024, 256, 0, s>>>(L, n, V, k);
         if (cudaGetLastError() != cudaSuccess) rc = CHM_ERR_CUDA;
     }
-    PassChoice def{1, 16, dtype == CHM_F64 ? 4 : 10, 0};
+    PassChoice def{1, 16, dtype == CHM_F64 ? 4 : 10, 0, 1};
     PassChoice best{};
     double best_ms = -1.0, def_ms = -1.0;
     auto consider = [&](const PassChoice &c) {
@@ -162,11 +162,10 @@ int tune_t(long long n, long long k, int dtype, int64_t *result)
     };
     if (rc == CHM_OK) {
         // the built-in choice for this shape, without the cache
-        const double bytes = (double)sizeof(T) * n * n / 2;
-        const bool rule = dtype == CHM_F64 ? (bytes >= 256e6 && k <= 2) : bytes >= 32e6;
-        def = PassChoice{rule ? 2 : 1, (int)std::min<long long>(k, 16), dtype == CHM_F64 ? 4 : 10, 0};
+        def = builtin_choice(n, k, dtype, false);
+        def.kb = (int)std::min<long long>(k, def.kb);
         def_ms = consider(def);
-        if (def.path == 2) consider(PassChoice{1, 16, def.d, 0});
+        if (def.path == 2) consider(PassChoice{1, 16, def.d, 0, 1});
         // vectors per pass: min(k, 16) and the two powers of two below it
         const int kb0 = (int)std::min<long long>(k, 16);
         std::vector<int> kbs{kb0};

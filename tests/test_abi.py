@@ -142,7 +142,8 @@ def test_pass_workspace_is_linear_in_n_and_independent_of_k():
 
 def test_path_settings_and_automatic_rule():
     """Host-only: the settings interface and the size rule that picks the
-    pass kernels (float: upper triangle >= 32 MB; double: >= 256 MB and k <= 2)."""
+    pass kernels (float: upper triangle >= 32 MB; double: >= 256 MB and k <= 8)
+    and the default vectors per pass (8 in float, 4 in double)."""
     F32, F64 = chm.CHM_F32_MIXED, chm.CHM_F64
     assert chm.config_get("path") == chm.PATH_AUTO
     assert chm.path_for(2048, 4, F32) == chm.PATH_WAVE
@@ -150,15 +151,18 @@ def test_path_settings_and_automatic_rule():
     assert chm.path_for(32768, 64, F32) == chm.PATH_PASS
     assert chm.path_for(5000, 16, F64) == chm.PATH_WAVE
     assert chm.path_for(8192, 1, F64) == chm.PATH_PASS
-    assert chm.path_for(32768, 3, F64) == chm.PATH_WAVE
+    assert chm.path_for(32768, 8, F64) == chm.PATH_PASS
+    assert chm.path_for(32768, 9, F64) == chm.PATH_WAVE
     for p in (chm.PATH_WAVE, chm.PATH_PASS):
         chm.config_set("path", p)
         assert chm.path_for(100, 1, F64) == p and chm.path_for(40000, 1, F32) == p
     chm.config_set("path", chm.PATH_AUTO)
     chm.config_set("pass_kb", 5)
     assert chm.config_get("pass_kb") == 5
+    assert chm.config_get("pass_kb_f32") == 5 and chm.config_get("pass_kb_f64") == 5
     chm.config_set("pass_kb", 0)
-    assert chm.config_get("pass_kb") == 16
+    assert chm.config_get("pass_kb") == 0
+    assert chm.config_get("pass_kb_f32") == 8 and chm.config_get("pass_kb_f64") == 4
     chm.config_set("pass_d", 9)
     assert chm.config_get("pass_d_f32") == 9 and chm.config_get("pass_d_f64") == 6
     chm.config_set("pass_d", 0)
@@ -181,6 +185,24 @@ def test_solve_argument_errors_without_gpu():
     # nothing to do: no CUDA call
     assert chm.chm_solve(None, 0, 1, None, 1, 3, chm.CHM_F64, None) == chm.CHM_OK
     assert chm.chm_solve(8, 5, 5, None, 5, 0, chm.CHM_F64, None) == chm.CHM_OK
+
+
+def test_modify_solve_argument_errors_without_gpu():
+    E = chm.CHM_ERR_ARG
+    F64 = chm.CHM_F64
+    ms = chm.chm_modify_solve
+    # (L, n, ld, V, ldv, k, sigma, sign, B, ldb, nrhs, dtype, stream, d_info)
+    assert ms(8, -1, 1, 8, 1, 1, None, 1, 8, 1, 1, F64, None, None) == E      # n < 0
+    assert ms(8, 4, 3, 8, 4, 1, None, 1, 8, 4, 1, F64, None, None) == E       # ld < n
+    assert ms(8, 4, 4, 8, 4, 1, None, 0, 8, 4, 1, F64, None, None) == E       # sign 0
+    assert ms(8, 4, 4, 8, 4, 1, None, 1, 8, 3, 1, F64, None, None) == E       # ldb < n
+    assert ms(8, 4, 4, 8, 4, 1, None, 1, 8, 4, -1, F64, None, None) == E      # nrhs < 0
+    assert ms(8, 4, 4, 8, 4, 1, None, 1, None, 4, 1, F64, None, None) == E    # NULL B
+    assert ms(8, 4, 4, 8, 4, 1, None, 1, 12, 4, 1, F64, None, None) == E      # misaligned B
+    assert ms(8, 4, 4, 8, 4, 1, None, 1, 8, 4, 1, 3, None, None) == E         # dtype
+    # nothing to do: no CUDA call
+    assert ms(None, 0, 1, None, 1, 2, None, 1, None, 1, 2, F64, None, None) == chm.CHM_OK
+    assert ms(8, 5, 5, None, 5, 0, None, 1, 8, 5, 0, F64, None, None) == chm.CHM_OK
 
 
 def test_checked_build_exports_the_same_symbols_and_reports_itself():

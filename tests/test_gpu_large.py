@@ -142,7 +142,7 @@ def test_n32768_mixed_update_then_downdate(factor, k):
     # float emulation of the same operations on the leading rows, with the
     # path's group of vectors per launch or pass
     path = chm.path_for(N, k, chm.CHM_F32_MIXED)
-    group = min(k, chm.config_get("pass_kb")) if path == chm.PATH_PASS else min(k, 64)
+    group = min(k, chm.config_get("pass_kb_f32")) if path == chm.PATH_PASS else min(k, 64)
     h32 = Lf0.cpu().numpy()
     u32 = U32.numpy()
     assert oracle.modify_mixed32(h32, u32, 1, m_rows=M_ROWS, group=group)[0] == 0

@@ -26,7 +26,7 @@ def mixed_group(k):
     """Vectors whose diagonals the current path carries in double at once."""
     path = chm.config_get("path")
     if path == chm.PATH_PASS:
-        return min(k, chm.config_get("pass_kb"))
+        return min(k, chm.config_get("pass_kb_f32"))
     return min(k, 64)
 
 
