@@ -342,6 +342,36 @@ def bench_solve(dev, L, reps=5):
     return {"workload": "solve with the bench factor after the timed steps, n=%d float64" % n, "runs": runs}
 
 
+def time_host_large(L0, U, U9, stream, reps=2):
+    """The same modification with the factor in page-locked host memory
+    (the pass kernels read and write it across the CPU-GPU link, three
+    crossings per pass; the device holds only the workspace): median ms of
+    one modification."""
+    import torch
+
+    from paper_1011_1173_gb300 import chm
+    Lh = torch.empty(L0.shape, dtype=L0.dtype, pin_memory=True)
+    ts = []
+    for r in range(reps):
+        Lh.copy_(L0)
+        for V, sg in ((U, 1), (U9, -1)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            chm.check(chm.modify(Lh, V, sg, stream=stream), "host-resident")
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+    chm.check(chm.status_sync(stream)[0], "host-resident status")
+    n, k = L0.shape[0], U.shape[0]
+    out = {"ms_per_modification": statistics.median(ts),
+           # a factor in page-locked host memory takes the pass kernels from two vectors on
+           "path": "pass" if k >= 2 or chm.path_for(n, k, chm.dtype_code(L0)) == chm.PATH_PASS else "wave",
+           "device_workspace_bytes": chm.workspace_bytes(n, k, chm.dtype_code(L0))}
+    del Lh
+    return out
+
+
 def time_modify_solve(L, L0, U, stream, flush, reps):
     """One right-hand side: chm_modify_solve (the forward half of the solve
     fused into the modification's last pass) against the modification
@@ -446,6 +476,8 @@ def bench_large(dev, cases=((1, "f64"), (16, "f64"), (1, "f32"), (16, "f32")), n
             "launches_per_modification": launches_per_modification(path, k, dt)}
         if k == 1:
             rec["modify_solve"] = time_modify_solve(L, L0, U, stream, flush, reps)
+        if k >= 16:
+            rec["host_resident"] = time_host_large(L0, U, U9, stream)
         if tune:
             # the autotuner's choice for this shape (chm_tune), then the same
             # timing with the tuned configuration from the cache

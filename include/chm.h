@@ -335,11 +335,13 @@ int chm_solve(const void *L, int64_t n, int64_t ld, void *B, int64_t ldb, int64_
  * pass: appending L^{-T} B to the factor as extra columns (the factor of
  * [[A, B], [B^T, c]]), the last pass's substitution carries B's columns
  * beside V's and a recurrence task applies the pass's rotations to them,
- * which leaves L~^{-T} B without another crossing of the factor; up to
- * 8 - (vectors of the last pass) right-hand sides ride that way, the others
- * take a substitution with the new factor of their own; each group ends
- * with the back substitution.  Otherwise the two calls follow each other on
- * the stream.  Precision: CHM_F64 in double; CHM_F32_MIXED as each part of
+ * which leaves L~^{-T} B without another crossing of the factor, and the
+ * back substitution follows.  In float up to 8 - (vectors of the last pass)
+ * right-hand sides ride that way and the others take a substitution with the
+ * new factor of their own; in double only as many as fill the last pass's
+ * unused vector columns (its chain is bound by the FP64 rate), the others
+ * take chm_solve's two substitutions.  Otherwise the two calls follow each
+ * other on the stream.  Precision: CHM_F64 in double; CHM_F32_MIXED as each part of
  * the pair: a carried right-hand side's forward half in float like the
  * pass's Apply, the back substitution with double arithmetic on float data.
  * d_info receives the modification's status; a failure of the solve part

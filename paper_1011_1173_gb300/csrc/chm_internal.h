@@ -149,10 +149,12 @@ int with_pass_workspace(cudaStream_t stream, size_t bytes, long long n, int dtyp
 long long *trace_buffer(size_t words, cudaStream_t stream);
 // Enqueue the passes of one modification (kb <= 16 vectors each).  With
 // right-hand sides (B, nrhs > 0; chm_modify_solve) B is then overwritten by
-// (L~^T L~)^{-1} B: the last pass's substitution carries up to 8 - (its
-// update vectors) of them when passes are fused, and its recurrence task
-// turns them into L~^{-T} B; the rest take a substitution of their own with
-// the new factor; each group ends with a back substitution (chm_solve.cu).
+// (L~^T L~)^{-1} B: when passes are fused the last pass's substitution
+// carries some of them (float: up to 8 - its update vectors; double: as
+// many as fill its kernels' unused vector columns) and its recurrence task
+// turns them into L~^{-T} B, then a back substitution; the rest take, in
+// float, a substitution of their own with the new factor and a back
+// substitution, in double chm_solve's two substitutions (chm_solve.cu).
 // `sc` must hold the solve's scratch (solve_need) when nrhs > 0.
 int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ldv, long long k,
                  const int8_t *sigma, int sign, int dtype, cudaStream_t stream, long long *d_info,
@@ -160,6 +162,9 @@ int pass_enqueue(void *L, long long n, long long ld, const void *V, long long ld
                  long long nrhs = 0);
 // The solve's scratch for a factor of order n (chm_solve.cu).
 ScratchNeed solve_need(long long n);
+// chm_solve's forward and back substitution on `sc` (which holds solve_need).
+int solve_enqueue(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs, int dtype,
+                  const Scratch &sc, cudaStream_t stream);
 // Back substitution with the upper factor L: B <- L^{-1} Y, row i of
 // right-hand side c of Y at Y[i * ys + c * cs] (element type of dtype).
 int solve_back_enqueue(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs,

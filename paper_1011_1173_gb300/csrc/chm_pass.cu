@@ -394,10 +394,17 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
     A.timeout_ns = timeout_ns();
     A.ldb = ldb;
     const int kbmax = ch.kb;
-    // right-hand sides the last pass carries: as many as keep it a fused
-    // pass of at most 8 vectors (its recurrence task then follows the chain)
+    // right-hand sides the last pass carries.  In float as many as keep it
+    // a fused pass of at most 8 vectors (its recurrence task then follows
+    // the chain).  In double only those that fill the instantiation's unused
+    // columns: the chain block's step there is bound by its FP64 issue,
+    // which grows with the kernels' vector count (at n = 32768, k = 1, one
+    // carried right-hand side took the pass from 4.4 to about 10 ms, more
+    // than chm_solve's whole forward half, whose tasks spread over the SMs).
     const int kr_last = k > 0 ? (int)(k - ((k - 1) / kbmax) * kbmax) : 0;
-    const long long nr1 = (nrhs > 0 && k > 0 && ch.fused) ? std::min<long long>(nrhs, std::max(0, 8 - kr_last)) : 0;
+    const bool dbl = sizeof(T) == 8;
+    const int room = dbl ? kb_instance(kr_last) - kr_last : std::max(0, 8 - kr_last);
+    const long long nr1 = (nrhs > 0 && k > 0 && ch.fused) ? std::min<long long>(nrhs, room) : 0;
     for (long long q0 = 0; q0 < k; q0 += kbmax) {
         const int kr = (int)std::min<long long>(kbmax, k - q0);
         const int nr = q0 + kbmax >= k ? (int)nr1 : 0;
@@ -417,8 +424,11 @@ int enqueue_passes(T *L, long long n, long long ld, const T *V, long long ldv, l
             rc = solve_back_enqueue(L, n, ld, B, ldb, nr, A.P + kr, kb_instance(A.kb), 1, dtype, sc, stream);
         if (rc != CHM_OK) return rc;
     }
-    // the other right-hand sides, up to 16 at a time: the substitution with
-    // the new factor (a pass that rotates nothing), then the back substitution
+    // the other right-hand sides: in double chm_solve's forward and back
+    // substitution with the new factor; in float, up to 16 at a time, the
+    // substitution (a pass that rotates nothing, one chain step about
+    // 1.3 us against chm_solve's 2 to 3) then the back substitution
+    if (dbl && nr1 < nrhs) return solve_enqueue(L, n, ld, B + nr1 * ldb, ldb, nrhs - nr1, dtype, sc, stream);
     for (long long r0 = nr1; r0 < nrhs; r0 += pass::kMaxKb) {
         const int nr = (int)std::min<long long>(pass::kMaxKb, nrhs - r0);
         A.V = nullptr;

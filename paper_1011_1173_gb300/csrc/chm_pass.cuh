@@ -482,6 +482,46 @@ __device__ __forceinline__ void lane_mv(const T *M, const T *x, T (&out)[KB], in
 #pragma unroll
     for (int q = 0; q < KB; ++q) out[q] = a0[q] + a1[q];
 }
+// The same with this lane's row of M in registers (the same order of
+// operations, so the same result bit for bit).
+template <typename T, int KB>
+__device__ __forceinline__ void lane_mv_reg(const T (&mrow)[kB], const T *x, T (&out)[KB])
+{
+    constexpr int E = Vec16<T>::n;
+    constexpr int XS = Rows<T, KB>::KS;
+    using V = typename Vec16<T>::type;
+    T a0[KB], a1[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+        a0[q] = T(0);
+        a1[q] = T(0);
+    }
+#pragma unroll
+    for (int l = 0; l < kB; ++l) {
+        const T mv = mrow[l];
+        if (KB % E == 0) {
+            const V *xr = reinterpret_cast<const V *>(x + l * XS);
+#pragma unroll
+            for (int g = 0; g < KB / E; ++g) {
+                const V xv = xr[g];
+#pragma unroll
+                for (int w = 0; w < E; ++w) {
+                    const int q = g * E + w;
+                    if (l & 1) a1[q] = fma(mv, vget<T>(xv, w), a1[q]);
+                    else a0[q] = fma(mv, vget<T>(xv, w), a0[q]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < KB; ++q) {
+                if (l & 1) a1[q] = fma(mv, x[l * XS + q], a1[q]);
+                else a0[q] = fma(mv, x[l * XS + q], a0[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) out[q] = a0[q] + a1[q];
+}
 
 // A value published as epoch-tagged 64-bit words (one per 32 bits of T):
 // each 8-byte store is single-copy atomic, so a reader that sees every word
@@ -721,9 +761,9 @@ struct ChainCfg {
     static constexpr int NEAR = DMAX - CMAX > 1 ? DMAX - CMAX : 1;  // near offset slots (d - c of them used)
     static constexpr size_t rest = sizeof(T) * Rows<T, KB>::size *
                                        ((size_t)RP + (size_t)NEAR * RT + RZ + RF + 1) +
-                                   tile + 256 + (size_t)RH * KB * KB * sizeof(double);
-    // staged per step: G^(1..c) and Dinv on the loader, one tile per near offset on the near warps
-    static constexpr size_t stage = (size_t)(CMAX + 1 + NEAR) * tile;
+                                   256 + (size_t)RH * KB * KB * sizeof(double);
+    // staged per step: G^(1..c) on the loader, one tile per near offset on the near warps
+    static constexpr size_t stage = (size_t)(CMAX + NEAR) * tile;
     static constexpr int fit = (int)((224u * 1024u - rest) / stage);
     static constexpr int RS = fit > 4 ? 4 : fit;
 };
@@ -734,9 +774,7 @@ struct ChainSmem {
     static constexpr int S = Stride<T>::value;
     static constexpr int RW = Rows<T, KB>::size;
     T G[C::RS][C::CMAX][kB * S];          // G^(j)_m, j = 1 .. c, of step m
-    T Di[C::RS][kB * S];                  // Dinv_{m+1}
     T near[C::NEAR][C::RS][kB * S];       // per near offset: tiles (m, m + j), [column][row]
-    T Di0[kB * S];                        // Dinv_0
     T P[C::RP][RW];
     T Tn[C::NEAR][C::RT][RW];             // F_{b-j,b}^T P_{b-j} per near offset j
     T Z[C::RZ][RW];                       // W_b
@@ -761,8 +799,9 @@ struct ChainSmem {
 //   W_m = Dinv_m (Zf_m - sum_{j=c+1}^{d} F_{m-j,m}^T P_{m-j}),
 // so the critical warp's step waits on no other warp's work of the last c
 // steps: the near warps (offsets c + 1 .. d) and the W warp have c steps of
-// slack.  The loader stages G^(1..c) and Dinv (its copies arrive on the
-// stage's barrier when they land), each near warp stages its own tiles, the
+// slack.  The loader stages G^(1..c) (its copies arrive on the stage's
+// barrier when they land) and prefetches Dinv to L2, from where the W warp
+// loads its row of it, each near warp stages its own tiles, the
 // far-sum warp polls the workers' tagged sums ahead of use, the publisher
 // writes each P as tagged words.
 template <typename T, int KB>
@@ -783,7 +822,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::RS; ++i) {
             mb_init(&S.st_full[i], 32);
-            mb_init(&S.st_empty[i], 64);  // the critical warp and the W warp
+            mb_init(&S.st_empty[i], 32);  // the critical warp
         }
         for (int i = 0; i < C::RZ; ++i) {
             mb_init(&S.w_full[i], 32);
@@ -890,8 +929,8 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 
     if (warp == kWLoad) {
         // G^(1..c) and Dinv of a step, prefetched to L2 16 steps ahead (the
-        // copies into the stage ring then come from L2 while the workers
-        // stream the factor from HBM)
+        // copies into the stage ring, and the W warp's loads of Dinv, then
+        // come from L2 while the workers stream the factor from HBM)
         constexpr int PF = 16;
         auto prefetch = [&](int m) {
             if (m >= nb) return;
@@ -913,7 +952,6 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             if (A.trace && lane == 0) A.trace[(size_t)m * 16 + 3] = global_ns();
             for (int j = 1; j <= cc && j <= m; ++j)
                 stage_dense(S.G[st][j - 1], A.G + ((size_t)(j - 1) * nb + m) * kB * kB, lane);
-            if (m + 1 < nb) stage_dense(S.Di[st], A.Dinv + (size_t)(m + 1) * kB * kB, lane);
             mb_arrive_cp(&S.st_full[st]);
         }
         cp_wait<0>();
@@ -996,13 +1034,24 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
     } else if (warp == kWZhat) {
         T *wv = S.w;
-        // Dinv_0 for W_0
-        stage_dense(S.Di0, A.Dinv, lane);
-        cp_commit();
-        cp_wait<0>();
-        __syncwarp();
         for (int b = 0; b < nb; ++b) {
             const long long r0 = (long long)b * kB;
+            // row `lane` of Dinv_b into registers first (the loader
+            // prefetched it to L2 16 steps ahead): the loads complete while
+            // the warp waits for the step's sums, and the warp waits on no
+            // stage of the loader's
+            T drow[kB];
+            {
+                using V = typename Vec16<T>::type;
+                constexpr int E = Vec16<T>::n;
+                const V *src = reinterpret_cast<const V *>(A.Dinv + (size_t)b * kB * kB + (size_t)lane * kB);
+#pragma unroll
+                for (int c = 0; c < kB / E; ++c) {
+                    const V x = __ldcg(src + c);
+#pragma unroll
+                    for (int u = 0; u < E; ++u) drow[c * E + u] = vget<T>(x, u);
+                }
+            }
             // w = Zf_b - sum_{j=c+1}^{d} F_{b-j,b}^T P_{b-j}
             T w[KB];
             if (b > d) {
@@ -1027,20 +1076,14 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 11] = global_ns();
             row_store<T, KB>(wv, lane, w);
             __syncwarp();
-            const T *Di = S.Di0;
-            if (b >= 1) {
-                MW(S.st_full, b - 1, C::RS, b);  // stage b - 1 holds Dinv_b
-                Di = S.Di[(b - 1) % C::RS];
-            }
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 6] = global_ns();
             T out[KB];
-            lane_mv<T, KB>(Di, wv, out, lane);
+            lane_mv_reg<T, KB>(drow, wv, out);
             // W_{b - RZ}'s slot is free once the critical warp has used it
             if (b >= C::RZ) MW(S.w_empty, b - C::RZ, C::RZ, b);
             row_store<T, KB>(S.Z[b % C::RZ], lane, out);
             __syncwarp();
             mb_arrive(&S.w_full[b % C::RZ]);
-            if (b >= 1) mb_arrive(&S.st_empty[(b - 1) % C::RS]);
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 1] = global_ns();
         }
     } else if (warp == kWZf) {

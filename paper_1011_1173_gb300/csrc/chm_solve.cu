@@ -577,6 +577,14 @@ int solve_back_t(const void *L, long long n, long long ld, void *B, long long ld
 }
 }  // namespace
 
+int solve_enqueue(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs, int dtype,
+                  const Scratch &sc, cudaStream_t stream)
+{
+    if (n <= 0 || nrhs <= 0) return CHM_OK;
+    return dtype == CHM_F64 ? solve_all<double>(L, n, ld, B, ldb, nrhs, sc, stream)
+                            : solve_all<float>(L, n, ld, B, ldb, nrhs, sc, stream);
+}
+
 int solve_back_enqueue(const void *L, long long n, long long ld, void *B, long long ldb, long long nrhs,
                        const void *Y, long long ys, long long cs, int dtype, const Scratch &sc, cudaStream_t stream)
 {

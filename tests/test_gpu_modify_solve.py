@@ -6,11 +6,14 @@ kept up to date to solve with the modified matrix).
 On the pass kernels the forward half rides in the last pass: the
 substitution carries B's columns beside V's and a recurrence task applies
 the pass's rotations to them (the bordered factor's extra column is
-L~^{-T} B).  The cases below cover right-hand sides carried that way, those
-that take a substitution of their own (more than the last pass has room for,
-a last pass of 8 vectors, passes not fused), both at once, the wave-kernel
-form (modification then chm_solve), ragged orders, padded leading
-dimensions and mixed signs.
+L~^{-T} B).  In float the last pass carries up to 8 - (its vectors) of them
+and the others take a substitution of their own with the new factor; in
+double it carries as many as fill its kernels' unused vector columns and
+the others take chm_solve.  The cases below cover right-hand sides carried
+that way, those that take the other route (more than the last pass has room
+for, a last pass of 8 vectors, passes not fused), both at once, the
+wave-kernel form (modification then chm_solve), ragged orders, padded
+leading dimensions and mixed signs, in both precisions.
 
 Tolerances.  The factor: the column-scaled 1e-11 of the other float64
 parity tests.  The solution: per right-hand side max |x_gpu - x_oracle| <=
@@ -73,17 +76,20 @@ def run(L0, V, B0, sig, n):
     return Ld.cpu(), Bd.cpu()
 
 
-# (n, k, nrhs, pad, path, vectors per pass, fused)
+# (n, k, nrhs, pad, path, vectors per pass, fused); in double a pass's
+# kernels take the next power of two of its vectors, and the right-hand
+# sides fill the columns left over
 CASES = [
     (300, 3, 1, 1, chm.PATH_AUTO, 0, 1),     # the wave kernel, then chm_solve
-    (100, 1, 1, 0, chm.PATH_PASS, 0, 1),     # one pass, one carried right-hand side
-    (257, 3, 2, 2, chm.PATH_PASS, 4, 1),     # ragged order
-    (1000, 5, 4, 0, chm.PATH_PASS, 4, 1),    # passes of 4 and 1; 4 carried
-    (2049, 9, 7, 1, chm.PATH_PASS, 4, 1),    # 7 carried by a last pass of 1 vector
-    (1000, 8, 3, 0, chm.PATH_PASS, 8, 1),    # a last pass of 8: all 3 take a substitution of their own
-    (700, 2, 20, 3, chm.PATH_PASS, 4, 1),    # 6 carried, 14 in a pass of their own
-    (500, 3, 2, 0, chm.PATH_PASS, 4, 0),     # passes not fused: a pass of their own
-    (64, 2, 40, 0, chm.PATH_PASS, 2, 1),     # 6 carried, then 16, 16 and 2
+    (100, 1, 1, 0, chm.PATH_PASS, 0, 1),     # one pass of 1: chm_solve after it
+    (257, 3, 2, 2, chm.PATH_PASS, 4, 1),     # a last pass of 3: 1 carried, 1 by chm_solve
+    (900, 5, 3, 1, chm.PATH_PASS, 8, 1),     # a last pass of 5: all 3 carried
+    (600, 7, 3, 2, chm.PATH_PASS, 8, 1),     # a last pass of 7: 1 carried, 2 by chm_solve
+    (2049, 11, 2, 1, chm.PATH_PASS, 4, 1),   # passes of 4, 4 and 3, ragged: 1 carried
+    (1000, 5, 4, 0, chm.PATH_PASS, 4, 1),    # passes of 4 and 1: none carried
+    (1000, 8, 3, 0, chm.PATH_PASS, 8, 1),    # a last pass of 8: none carried
+    (500, 3, 2, 0, chm.PATH_PASS, 4, 0),     # passes not fused: none carried
+    (64, 2, 40, 0, chm.PATH_PASS, 2, 1),     # many right-hand sides, none carried
 ]
 
 
@@ -116,10 +122,19 @@ def test_modify_solve_matches_oracle_f64(n, k, nrhs, pad, path, kb, fused):
         chm.config_set("pass_fused", 1)
 
 
-@pytest.mark.parametrize("n,k,nrhs,kb", [(700, 3, 2, 8), (1500, 6, 5, 4)])
-def test_modify_solve_mixed_precision(n, k, nrhs, kb):
+@pytest.mark.parametrize("n,k,nrhs,kb,fused", [
+    (700, 3, 2, 8, 1),      # both carried
+    (1500, 6, 5, 4, 1),     # passes of 4 and 2; 5 carried
+    (1000, 8, 3, 8, 1),     # a last pass of 8: all 3 in a pass of their own
+    (700, 2, 20, 4, 1),     # 6 carried, 14 in a pass of their own
+    (64, 2, 40, 2, 1),      # 6 carried, then passes of 16, 16 and 2
+    (500, 3, 2, 4, 0),      # passes not fused: a pass of their own
+    (257, 1, 1, 1, 1),      # ragged order, one vector, one right-hand side
+])
+def test_modify_solve_mixed_precision(n, k, nrhs, kb, fused):
     chm.config_set("path", chm.PATH_PASS)
     chm.config_set("pass_kb", kb)
+    chm.config_set("pass_fused", fused)
     try:
         seed = 1700 + n + k
         L64 = inputs.spd_factor(n, seed)
@@ -144,6 +159,7 @@ def test_modify_solve_mixed_precision(n, k, nrhs, kb):
     finally:
         chm.config_set("path", 0)
         chm.config_set("pass_kb", 0)
+        chm.config_set("pass_fused", 1)
 
 
 def test_modify_solve_full_size_f64():
@@ -169,3 +185,37 @@ def test_modify_solve_full_size_f64():
     print("n=32768: factor %.2e, solution %.2e" % (e_l, e_x))
     assert e_l <= TOL_F64
     assert e_x <= TOL_X
+
+
+def test_modify_solve_full_size_mixed():
+    """n = 32768 in float storage, rank-1 update, one right-hand side carried
+    by the pass (the library's own choice): the solution against the
+    oracle's double solve with the GPU's own factor, and the factor's
+    leading rows against the emulation."""
+    n, k, nrhs, m_rows = 32768, 1, 1, 48
+    seed = inputs.config_seed(2)
+    Ld = inputs.spd_factor(n, seed, device="cuda").float()
+    L0 = Ld.cpu()
+    V = inputs.update_block(n, k, seed + 1).float()
+    B0 = rhs(n, nrhs, seed, n).float()
+    assert chm.path_for(n, k, chm.CHM_F32_MIXED) == chm.PATH_PASS
+    Vd, Bd = V.cuda(), B0.cuda()
+    assert chm.modify_solve(Ld, Vd, Bd, 1) == chm.CHM_OK
+    assert chm.status_sync() == (chm.CHM_OK, -1)
+    got_L = Ld.cpu()
+    ref_X = B0.double().numpy().copy()
+    assert oracle.solve(got_L.double().numpy(), ref_X)[0] == oracle.OK
+    e_x = rel_err(Bd.cpu().double().numpy(), ref_X, n)
+    # rows i < m_rows of every column (storage entries [j, i]) depend only on those rows
+    emu = L0.numpy().copy()
+    assert oracle.modify_mixed32(emu, V.numpy(), [1], m_rows=m_rows, group=1)[0] == oracle.OK
+    g = got_L[:, :m_rows].double().numpy()
+    r = emu[:, :m_rows].astype(np.float64)
+    mask = np.arange(m_rows)[None, :] <= np.arange(n)[:, None]
+    scale = np.maximum(np.abs(r), np.max(np.where(mask, np.abs(r), 0.0), axis=1, keepdims=True))
+    e_l = float(np.where(mask, np.abs(g - r) / np.where(scale == 0, 1.0, scale), 0.0).max())
+    bound = 32 * U_F32 * np.sqrt(n * (k + 1))
+    print("mixed n=32768: leading rows %.2e (bound %.2e), solution %.2e (bound %.2e)"
+          % (e_l, tol_mixed(m_rows, k), e_x, bound))
+    assert e_l <= tol_mixed(m_rows, k)
+    assert e_x <= bound
