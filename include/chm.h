@@ -422,8 +422,9 @@ int chm_microbench(int which, double *out, int nout);
  *   "pass_d"   lookahead of the pass kernels' forward-substitution chain in
  *              row blocks, clamped to 2..10 (float) or 2..6 (double) and
  *              further by what the chain block's shared memory holds for
- *              the pass's vectors; 0 is the default per type (10 float,
- *              4 double)
+ *              the pass's vectors; 0 is the default by type and vectors
+ *              per pass (float: 4 up to 2 vectors, 6 up to 4, 10 beyond;
+ *              double: 3)
  *   "pass_seg" row blocks per segment of the pass kernels' sweep tasks
  *              (0: max(64, row blocks / 16))
  *   "pass_fused" 1 (default): up to 8 vectors per pass, the substitution

@@ -73,7 +73,18 @@ static int default_kb(int dtype) { return dtype == CHM_F64 ? 4 : 8; }
 
 static int pass_kb_of(int dtype) { return clamp_kb(kb_setting() > 0 ? kb_setting() : default_kb(dtype)); }
 
-static int pass_d(int dtype) { return clamp_d(d_setting() > 0 ? d_setting() : (dtype == CHM_F64 ? 4 : 10), dtype); }
+// Lookahead by default, by type and vectors per pass (measured at
+// n = 32768, one modification: float with 1 vector 1.48 ms at d = 2..5
+// against 1.64 at 10, the near warps' running sums then lagging the chain;
+// 4 vectors 1.94 ms at d = 6; 8 vectors flat from d = 5 to 10; double
+// 4.43 ms at d = 2..3 against 4.64 at 6).
+static int default_d(int dtype, int kb)
+{
+    if (dtype == CHM_F64) return 3;
+    return kb <= 2 ? 4 : kb <= 4 ? 6 : 10;
+}
+
+static int pass_d(int dtype) { return clamp_d(d_setting() > 0 ? d_setting() : default_d(dtype, default_kb(dtype)), dtype); }
 
 // Row blocks per segment of the sweep's column tasks: a column block's
 // tiles are split at multiples of this, each segment starting from the
@@ -109,7 +120,9 @@ static bool rule_pass(long long n, long long k, int dtype, bool host_factor)
 
 PassChoice builtin_choice(long long n, long long k, int dtype, bool host_factor)
 {
-    return PassChoice{rule_pass(n, k, dtype, host_factor) ? 2 : 1, default_kb(dtype), dtype == CHM_F64 ? 4 : 10, 0, 1};
+    const int kb = default_kb(dtype);
+    return PassChoice{rule_pass(n, k, dtype, host_factor) ? 2 : 1, kb,
+                      default_d(dtype, (int)std::min<long long>(std::max(1ll, k), kb)), 0, 1};
 }
 
 PassChoice choose_path(long long n, long long k, int dtype, bool host_factor)
@@ -118,12 +131,15 @@ PassChoice choose_path(long long n, long long k, int dtype, bool host_factor)
     // times one, then the tuning cache (device factors), then the defaults
     PassChoice base = builtin_choice(n, k, dtype, host_factor);
     PassChoice tuned;
-    if (const PassChoice *o = tune_override()) base = *o;
-    else if (!host_factor && tune_lookup(dtype, n, k, &tuned)) base = tuned;
+    bool d_given = d_setting() > 0;
+    if (const PassChoice *o = tune_override()) base = *o, d_given = true;
+    else if (!host_factor && tune_lookup(dtype, n, k, &tuned)) base = tuned, d_given = true;
     PassChoice c = base;
     const int p = path_setting();
     if (p != 0) c.path = p;
     if (kb_setting() > 0) c.kb = kb_setting();
+    // the default lookahead follows the vectors of the pass actually run
+    if (!d_given) c.d = default_d(dtype, (int)std::min<long long>(std::max(1ll, k), clamp_kb(c.kb)));
     if (d_setting() > 0) c.d = d_setting();
     if (seg_setting() > 0) c.seg = seg_setting();
     c.kb = clamp_kb(c.kb);

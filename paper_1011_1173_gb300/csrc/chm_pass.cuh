@@ -1034,24 +1034,25 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
     } else if (warp == kWZhat) {
         T *wv = S.w;
+        // row `lane` of Dinv_b in registers, loaded from L2 (the loader
+        // prefetched it 16 steps ahead) as soon as W_{b-1} is out, so that
+        // the load completes while the warp waits for step b's sums; the
+        // warp waits on no stage of the loader's
+        T drow[kB];
+        auto load_drow = [&](int b) {
+            using V = typename Vec16<T>::type;
+            constexpr int E = Vec16<T>::n;
+            const V *src = reinterpret_cast<const V *>(A.Dinv + (size_t)b * kB * kB + (size_t)lane * kB);
+#pragma unroll
+            for (int c = 0; c < kB / E; ++c) {
+                const V x = __ldcg(src + c);
+#pragma unroll
+                for (int u = 0; u < E; ++u) drow[c * E + u] = vget<T>(x, u);
+            }
+        };
+        load_drow(0);
         for (int b = 0; b < nb; ++b) {
             const long long r0 = (long long)b * kB;
-            // row `lane` of Dinv_b into registers first (the loader
-            // prefetched it to L2 16 steps ahead): the loads complete while
-            // the warp waits for the step's sums, and the warp waits on no
-            // stage of the loader's
-            T drow[kB];
-            {
-                using V = typename Vec16<T>::type;
-                constexpr int E = Vec16<T>::n;
-                const V *src = reinterpret_cast<const V *>(A.Dinv + (size_t)b * kB * kB + (size_t)lane * kB);
-#pragma unroll
-                for (int c = 0; c < kB / E; ++c) {
-                    const V x = __ldcg(src + c);
-#pragma unroll
-                    for (int u = 0; u < E; ++u) drow[c * E + u] = vget<T>(x, u);
-                }
-            }
             // w = Zf_b - sum_{j=c+1}^{d} F_{b-j,b}^T P_{b-j}
             T w[KB];
             if (b > d) {
@@ -1084,6 +1085,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
             row_store<T, KB>(S.Z[b % C::RZ], lane, out);
             __syncwarp();
             mb_arrive(&S.w_full[b % C::RZ]);
+            if (b + 1 < nb) load_drow(b + 1);
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 1] = global_ns();
         }
     } else if (warp == kWZf) {

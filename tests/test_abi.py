@@ -166,7 +166,7 @@ def test_path_settings_and_automatic_rule():
     chm.config_set("pass_d", 9)
     assert chm.config_get("pass_d_f32") == 9 and chm.config_get("pass_d_f64") == 6
     chm.config_set("pass_d", 0)
-    assert chm.config_get("pass_d_f32") == 10 and chm.config_get("pass_d_f64") == 4
+    assert chm.config_get("pass_d_f32") == 10 and chm.config_get("pass_d_f64") == 3
     for key, val in (("path", 3), ("pass_kb", 17), ("pass_kb", -1), ("nope", 1)):
         assert chm.chm_config_set(key, val) == chm.CHM_ERR_ARG
 
