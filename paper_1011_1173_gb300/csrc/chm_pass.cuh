@@ -1547,91 +1547,48 @@ __device__ __forceinline__ bool warp_count(const SyncArgs &sy, const long long *
     return ok != 0;
 }
 
-// Segment sg of column block b: row blocks rb .. re (the last segment ends
-// at the diagonal tile), tiles and their rows' coefficients staged through
-// NSLOT slots.  In a fused pass the segment first waits until nothing else
-// will read its tiles (the column's worker is past re, or for the last
-// segment the chain has published P_b, which needs every near term of b),
-// and each tile waits for its row block's coefficients.  Returns false if
-// the launch is being aborted.
-template <typename T, int KB, int NSLOT>
-__device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int sg, SweepSlot<T, KB> *slot)
-{
-    constexpr int SD = Stride<T>::value;
-    constexpr int E = 16 / (int)sizeof(T);
-    constexpr int CPC = kB / E;         // 16-byte chunks per column segment
-    constexpr int CPL = kB * CPC / 32;  // chunks per lane per tile
+// Per-lane addressing of column block b's tiles for the sweep: staging of
+// a tile (rows r0 .. r0 + 31, the diagonal tile's rows <= column only) and
+// of its rows' coefficients into a slot with cp.async, and the rotation of a
+// staged tile (lane = column, the carries uh in registers) with its store.
+template <typename T, int KB>
+struct TileIO {
+    static constexpr int SD = Stride<T>::value;
+    static constexpr int E = 16 / (int)sizeof(T);
+    static constexpr int CPC = kB / E;         // 16-byte chunks per column segment
+    static constexpr int CPL = kB * CPC / 32;  // chunks per lane per tile
     using V = typename Vec16<T>::type;
-    const int lane = threadIdx.x & 31;
-    const long long n = A.n, ld = A.ld;
-    const int nb = A.nb;
-    const bool vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
-    // this lane's chunk of every staged column segment: chunk ch of columns
-    // col0 + t * (32 / CPC), t = 0 .. CPL - 1
-    const int ch = lane % CPC, col0 = lane / CPC, cstep = 32 / CPC;
-    const int nseg = 1 + max(0, (b - A.d - 1) / A.seg);
-    if (b < 0 || b >= nb || sg < 0 || sg >= nseg) {
-        // not a task of this pass (an internal invariant, checked in every build)
-        if (lane == 0) record_error(sy, kStatusBounds, (long long)b);
-        return false;
+    const Args<T> &A;
+    const SyncArgs &sy;
+    int b, lane, ch, col0, cstep;
+    long long n, ld, c0, gofs;
+    bool vec, active;
+    const T *gbase;
+    unsigned colmask;
+    unsigned long long pol;
+    __device__ TileIO(const Args<T> &a, const SyncArgs &s, int b_) : A(a), sy(s), b(b_)
+    {
+        lane = threadIdx.x & 31;
+        n = A.n;
+        ld = A.ld;
+        vec = ((ld * (long long)sizeof(T)) & 15) == 0 && (reinterpret_cast<uintptr_t>(A.L) & 15) == 0;
+        // this lane's chunk of every staged column segment: chunk ch of columns
+        // col0 + t * (32 / CPC), t = 0 .. CPL - 1
+        ch = lane % CPC;
+        col0 = lane / CPC;
+        cstep = 32 / CPC;
+        c0 = (long long)b * kB;
+        active = c0 + lane < n;
+        gofs = (long long)ch * E + (c0 + col0) * ld;
+        gbase = A.L + gofs;
+        colmask = 0;
+#pragma unroll
+        for (int t = 0; t < CPL; ++t)
+            if (c0 + col0 + t * cstep < n) colmask |= 1u << t;
+        pol = evict_first_policy();
     }
-    const int rb = sg * A.seg, re = sg == nseg - 1 ? b : rb + A.seg - 1;
-    const long long ep64 = (long long)A.epoch << 32;
-    const unsigned long long pol = evict_first_policy();
-    if (A.fused) {
-        // last segment: P_b out (its first tagged word) means the chain has
-        // consumed every near term of column block b
-        bool ok;
-        if (sg == nseg - 1) {
-            T pv[1];
-            ok = warp_tagged_row<T, 1>(sy, A.Ptag + (size_t)b * kB * KB * Tag<T>::words, ep64, pv, 256u, b);
-        } else {
-            ok = warp_count(sy, A.wprog + b, ep64 + re + 1, b);
-        }
-        if (!ok) return false;
-        if (sg > 0 && !warp_flag(sy, A.cflag + rb, A.epoch, b)) return false;  // its LDL^T at rb
-    }
-    const long long c0 = (long long)b * kB;
-    const bool active = c0 + lane < n;
-    T uh[KB];
-    if (sg == 0) {
-#pragma unroll
-        for (int q = 0; q < KB; ++q)
-            uh[q] = (active && q < A.kr) ? vin(A, sy, c0 + lane, q) : T(0);
-    } else {
-        // the carry entering row block rb, rebuilt from the substitution's
-        // residual w there: u_hat = |D|^{-1} L^{-1} w with H = L D L^T the
-        // prefix Gram before the block (the scaled rotations' carry is
-        // this linear image of the residual at every row)
-        const T *w = A.snap + (((size_t)(sg - 1) * nb + b) * kB + lane) * KB;
-        const double *h = A.rst + (size_t)(sg - 1) * (KB * (KB + 1) / 2);
-        double z[KB];
-#pragma unroll
-        for (int q = 0; q < KB; ++q) {
-            if (q < A.kr) {
-                double zq = active ? (double)__ldcg(w + q) : 0.0;
-#pragma unroll
-                for (int m = 0; m < q; ++m) zq -= __ldcg(h + pidx(q, m)) * z[m];
-                z[q] = zq;
-                uh[q] = (T)(zq / (sigma_of(A, q) * __ldcg(h + pidx(q, q))));
-            } else {
-                z[q] = 0.0;
-                uh[q] = T(0);
-            }
-        }
-    }
-    // per-lane addresses of the staged chunks (vector path)
-    const long long gofs = (long long)ch * E + (c0 + col0) * ld;
-    const T *gbase = A.L + gofs;
-    unsigned colmask = 0;
-#pragma unroll
-    for (int t = 0; t < CPL; ++t)
-        if (c0 + col0 + t * cstep < n) colmask |= 1u << t;
-    bool alive = true;
-    auto fetch = [&](int r) {
-        if (A.fused && alive) alive = warp_flag(sy, A.cflag + r, A.epoch, b);  // the row block's coefficients
-        if (!alive) return;
-        SweepSlot<T, KB> &sl = slot[r % NSLOT];
+    __device__ void stage_tile(SweepSlot<T, KB> &sl, int r) const
+    {
         const long long r0 = (long long)r * kB;
         if (r < b && vec) {
             const T *g = gbase + r0;
@@ -1647,29 +1604,24 @@ __device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int s
                 }
             }
         } else if (r < b) {
-            stage_tile(sy, sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
+            ::chm::pass::stage_tile(sy, sl.tile, A.L, ld, r0, c0, n, kB, false, lane);
         } else {
             // the diagonal tile: rows <= column only
             for (int col = 0; col < kB; ++col)
                 if (c0 + col < n && lane <= col && CHK_TRI(sy, (r0 + lane) + (c0 + col) * ld, n, ld))
                     cp_elem(&sl.tile[col * SD + lane], A.L + (r0 + lane) + (c0 + col) * ld);
         }
+    }
+    __device__ void stage_coef(SweepSlot<T, KB> &sl, int r) const
+    {
+        const long long r0 = (long long)r * kB;
         const T *cf = A.coef + (size_t)r0 * 2 * KB;
         for (int c = lane; c < kB * 2 * KB / E; c += 32) cp16(sl.cf + c * E, cf + c * E);
         if (lane < kB / E) cp16(sl.e + lane * E, A.escale + r0 + lane * E);
         if (r == b && lane < kB / 2) cp16(sl.df + 2 * lane, A.dfac + r0 + 2 * lane);
-    };
-    for (int r = rb; r < rb + NSLOT - 1; ++r) {
-        if (r <= re) fetch(r);
-        cp_commit();
     }
-    for (int r = rb; r <= re; ++r) {
-        if (r + NSLOT - 1 <= re) fetch(r + NSLOT - 1);
-        cp_commit();
-        cp_wait<NSLOT - 1>();
-        __syncwarp();
-        if (!alive) break;
-        SweepSlot<T, KB> &sl = slot[r % NSLOT];
+    __device__ void rotate_store(SweepSlot<T, KB> &sl, int r, T (&uh)[KB]) const
+    {
         const bool diag = r == b;
         const long long r0 = (long long)r * kB;
         T v[kB];
@@ -1725,6 +1677,92 @@ __device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int s
                     A.L[(r0 + lane) + (c0 + cc) * ld] = sl.tile[cc * SD + lane];
         }
         __syncwarp();
+    }
+};
+
+// Segment sg of column block b: row blocks rb .. re (the last segment ends
+// at the diagonal tile), tiles and their rows' coefficients staged through
+// NSLOT slots.  In a fused pass the segment first waits until nothing else
+// will read its tiles (the column's worker is past re, or for the last
+// segment the chain has published P_b, which needs every near term of b),
+// and each tile waits for its row block's coefficients.  Returns false if
+// the launch is being aborted.
+template <typename T, int KB, int NSLOT>
+__device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int sg, SweepSlot<T, KB> *slot)
+{
+    const int lane = threadIdx.x & 31;
+    const long long n = A.n;
+    const int nb = A.nb;
+    const int nseg = 1 + max(0, (b - A.d - 1) / A.seg);
+    if (b < 0 || b >= nb || sg < 0 || sg >= nseg) {
+        // not a task of this pass (an internal invariant, checked in every build)
+        if (lane == 0) record_error(sy, kStatusBounds, (long long)b);
+        return false;
+    }
+    const int rb = sg * A.seg, re = sg == nseg - 1 ? b : rb + A.seg - 1;
+    const long long ep64 = (long long)A.epoch << 32;
+    if (A.fused) {
+        // last segment: P_b out (its first tagged word) means the chain has
+        // consumed every near term of column block b
+        bool ok;
+        if (sg == nseg - 1) {
+            T pv[1];
+            ok = warp_tagged_row<T, 1>(sy, A.Ptag + (size_t)b * kB * KB * Tag<T>::words, ep64, pv, 256u, b);
+        } else {
+            ok = warp_count(sy, A.wprog + b, ep64 + re + 1, b);
+        }
+        if (!ok) return false;
+        if (sg > 0 && !warp_flag(sy, A.cflag + rb, A.epoch, b)) return false;  // its LDL^T at rb
+    }
+    const long long c0 = (long long)b * kB;
+    const bool active = c0 + lane < n;
+    T uh[KB];
+    if (sg == 0) {
+#pragma unroll
+        for (int q = 0; q < KB; ++q)
+            uh[q] = (active && q < A.kr) ? vin(A, sy, c0 + lane, q) : T(0);
+    } else {
+        // the carry entering row block rb, rebuilt from the substitution's
+        // residual w there: u_hat = |D|^{-1} L^{-1} w with H = L D L^T the
+        // prefix Gram before the block (the scaled rotations' carry is
+        // this linear image of the residual at every row)
+        const T *w = A.snap + (((size_t)(sg - 1) * nb + b) * kB + lane) * KB;
+        const double *h = A.rst + (size_t)(sg - 1) * (KB * (KB + 1) / 2);
+        double z[KB];
+#pragma unroll
+        for (int q = 0; q < KB; ++q) {
+            if (q < A.kr) {
+                double zq = active ? (double)__ldcg(w + q) : 0.0;
+#pragma unroll
+                for (int m = 0; m < q; ++m) zq -= __ldcg(h + pidx(q, m)) * z[m];
+                z[q] = zq;
+                uh[q] = (T)(zq / (sigma_of(A, q) * __ldcg(h + pidx(q, q))));
+            } else {
+                z[q] = 0.0;
+                uh[q] = T(0);
+            }
+        }
+    }
+    const TileIO<T, KB> io(A, sy, b);
+    bool alive = true;
+    auto fetch = [&](int r) {
+        if (A.fused && alive) alive = warp_flag(sy, A.cflag + r, A.epoch, b);  // the row block's coefficients
+        if (!alive) return;
+        SweepSlot<T, KB> &sl = slot[r % NSLOT];
+        io.stage_tile(sl, r);
+        io.stage_coef(sl, r);
+    };
+    for (int r = rb; r < rb + NSLOT - 1; ++r) {
+        if (r <= re) fetch(r);
+        cp_commit();
+    }
+    for (int r = rb; r <= re; ++r) {
+        if (r + NSLOT - 1 <= re) fetch(r + NSLOT - 1);
+        cp_commit();
+        cp_wait<NSLOT - 1>();
+        __syncwarp();
+        if (!alive) break;
+        io.rotate_store(slot[r % NSLOT], r, uh);
     }
     cp_wait<0>();
     __syncwarp();

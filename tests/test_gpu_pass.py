@@ -53,7 +53,8 @@ def ref(L, V, sig):
 def test_vectors_per_pass_and_lookahead(kb, d, fused):
     """Both forms of a pass: fused (the substitution kernel's workers form
     the coefficients and sweep as their inputs arrive; up to 8 vectors per
-    pass) and the six-kernel sequence."""
+    pass) and the six-kernel sequence; float64 against the oracle, float
+    storage against the emulation."""
     chm.config_set("pass_kb", kb)
     chm.config_set("pass_d", d)
     chm.config_set("pass_fused", fused)
@@ -67,6 +68,15 @@ def test_vectors_per_pass_and_lookahead(kb, d, fused):
             ost, _, o = ref(L, V, sig)
             assert st == ost == 0
             assert colscaled_err(g, o) <= TOL_F64, (n, k, kb, d)
+            L32, V32 = L.astype(np.float32), V.astype(np.float32)
+            st, info, g32 = run(L32, V32, sig, dtype=torch.float32)
+            o32 = np.array(L32, copy=True)
+            assert oracle.modify_mixed32(o32, np.ascontiguousarray(V32), sig, n=n, group=kb)[0] == 0
+            o64 = np.array(L32, dtype=np.float64, copy=True)
+            assert oracle.modify_b(o64, np.ascontiguousarray(V32, dtype=np.float64), sig, n=n)[0] == 0
+            dm = colscaled_err(g32, o32, n=n)
+            assert st == 0 and dm <= tol_mixed(n, k), (n, k, kb, d, dm)
+            assert accuracy_as_serial(colscaled_err(g32, o64, n=n), colscaled_err(o32, o64, n=n))
     finally:
         chm.config_set("pass_kb", 0)
         chm.config_set("pass_d", 0)
@@ -155,6 +165,8 @@ def test_first_failing_row(kb):
         st, info, _ = run(np.eye(n), V, [1, 1, -1])
         ost, oinfo, _ = ref(np.eye(n), V, [1, 1, -1])
         assert ost == oracle.ERR_NOT_PD and oinfo == 130
+        assert st == chm.CHM_ERR_NOT_PD and info == 130
+        st, info, _ = run(np.eye(n, dtype=np.float32), V.astype(np.float32), [1, 1, -1], dtype=torch.float32)
         assert st == chm.CHM_ERR_NOT_PD and info == 130
         # a non-positive diagonal on entry
         L = np.eye(n)
