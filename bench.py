@@ -73,7 +73,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # the sha256 (first 16 hex digits) of the kernel sources it was taken with and
 # the shape (n, k); a capture of an older kernel version reads as null.
 NCU_TRAFFIC = {("wave_kernel<double>", "4ab9131a4a9fb172", 5000, 16): 210.58e6,
-               ("wave_kernel<float>", "4ab9131a4a9fb172", 8192, 16): 307.99e6}
+               ("wave_kernel<float>", "4ab9131a4a9fb172", 8192, 16): 307.99e6,
+               ("wave_kernel<double>", "1732a41a06476ee3", 5000, 16): 209.77e6}
 KERNEL_SOURCES = ("paper_1011_1173_gb300/csrc/chm_wave.cuh", "paper_1011_1173_gb300/csrc/chm_device.cuh",
                   "paper_1011_1173_gb300/csrc/chm_layout.h", "paper_1011_1173_gb300/csrc/chm_modify.cu")
 

@@ -35,6 +35,7 @@ def _device():
     torch.cuda.set_device(0)
     yield
     chm.config_set("path", chm.PATH_AUTO)
+    chm.config_set("pass_kb", 0)
 
 
 def pinned(t):
@@ -61,6 +62,10 @@ def test_host_resident_matches_device_resident(n, k, pad, dtype):
         ref = L.numpy().copy()
         assert oracle.modify_b(ref, V.numpy(), sig)[0] == 0
     by_path = {}
+    # a factor in host memory takes 16 vectors per pass by default (each pass
+    # crosses the CPU-GPU link); the device factor is given the same here, so
+    # that the two run the same passes
+    chm.config_set("pass_kb", 16)
     for path in (chm.PATH_WAVE, chm.PATH_PASS):
         chm.config_set("path", path)
         dev_L = L.cuda()
@@ -74,8 +79,10 @@ def test_host_resident_matches_device_resident(n, k, pad, dtype):
         if ref is not None:
             assert colscaled_err(host_L.numpy(), ref) <= TOL_F64
         by_path[path] = host_L
-    # the automatic rule: a host factor of order >= 64 with k >= 2 on the pass kernels
+    # the automatic rule: a host factor of order >= 64 with k >= 2 on the pass
+    # kernels, with 16 vectors per pass
     chm.config_set("path", chm.PATH_AUTO)
+    chm.config_set("pass_kb", 0)
     host_L = pinned(L)
     assert chm.modify(host_L, pinned(V), sig) == chm.CHM_OK
     assert chm.status_sync()[0] == chm.CHM_OK
