@@ -1135,12 +1135,14 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 // P_r polled as tagged words, Zf_b published as tagged words.
 template <typename T, int KB>
 struct WorkerCfg {
-    // staged tiles per warp: deeper in float with one or two vectors, where
-    // a worker that falls a few tiles behind the chain must catch up before
-    // its column is due (n = 32768, rank 1: 1.48 ms with 3, 1.40 with 4,
-    // 1.31 with 5, 1.40 with 6, the last leaving fewer workers than columns);
-    // in float64 three, which keeps a worker per column
-    static constexpr int NS = (sizeof(T) == 4 && KB <= 2) ? 5 : 3;
+    // staged tiles per warp: five in float, where a worker that falls a few
+    // tiles behind the chain must catch up before its column is due
+    // (n = 32768: rank 1 1.48 ms with 3, 1.40 with 4, 1.31 with 5, 1.40 with
+    // 6, which leaves fewer workers than columns; 4 vectors per pass 2.06 /
+    // 1.89 / 1.87 ms with 3 / 4 / 5; rank 16 7.8 / 6.8 / 6.6; rank 64
+    // 31.1 / 26.1 / 25.0); in float64 three, which keeps a worker per column
+    // (four: rank 1 5.46 against 4.51 ms)
+    static constexpr int NS = sizeof(T) == 4 ? 5 : 3;
     // tiles prefetched to L2 ahead of the one in use: about 32 KB per warp,
     // 32 MB over a thousand workers at the front of the chain
     static constexpr int PF = (int)(32768 / (sizeof(T) * kB * kB));
