@@ -45,6 +45,10 @@ constexpr int kPad = 33;   // shared-memory row stride of a 32 x 32 matrix
 constexpr int kMaxKb = 16; // vectors per pass
 // Offsets the substitution's critical warp takes itself, at most (through G^(j) = Dinv F_{b-j,b}^T).
 constexpr int kMaxCrit = 4;
+// Offsets whose G^(j) the pass forms, at most: the lookahead's bound (the
+// near warps' terms are G^(j) P as well, so that W_m needs no product
+// with Dinv_m on the chain block).
+constexpr int kMaxG = 10;
 
 // Control words of a pass (zeroed before each pass).
 constexpr int kCtlWorkTicket = 0;   // next worker task of the forward substitution
@@ -74,7 +78,7 @@ struct Args {
     // workspace
     T *P;            // [nb * 32][KB]: F^T P = V, rows past n zero
     T *Dinv;         // [nb][32][32]: (D_b^T)^{-1}, D_b the diagonal block, row-major
-    T *G;            // [c][nb][32][32]: G^(j)_b = Dinv_b F_{b-j,b}^T, row-major
+    T *G;            // [d][nb][32][32]: G^(j)_b = Dinv_b F_{b-j,b}^T, row-major
     double *gram;    // [nb][KB][KB]: sum over the block's rows of p p^T
     double *H;       // [nb][KB][KB]: Sigma + sum over earlier blocks
     T *coef;         // [nb * 32][2 KB]: (a_q, b_q) of each row
@@ -153,7 +157,8 @@ __device__ __forceinline__ bool ws_ok(const Args<T> &A, const SyncArgs &sy)
            CHK_REGION(sy, A.Htag, nb * KB * KB * 16, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.Ztag, rows * KB * tagw * 8, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.Dinv, nb * kB * kB * e, A.ws, A.ws_bytes) &&
-           CHK_REGION(sy, A.G, (size_t)A.c * nb * kB * kB * e, A.ws, A.ws_bytes) &&
+           CHK_RECT(sy, (long long)A.d, kMaxG + 1, 1, 1 << 30) &&
+           CHK_REGION(sy, A.G, (size_t)A.d * nb * kB * kB * e, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.gram, nb * KB * KB * 8, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.H, nb * KB * KB * 8, A.ws, A.ws_bytes) &&
            CHK_REGION(sy, A.coef, rows * 2 * KB * e, A.ws, A.ws_bytes) &&
@@ -197,7 +202,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // ---------------------------------------------------------------- prep
 
 // Per diagonal block b (one warp): Dinv_b = (D_b^T)^{-1} and
-// G^(j)_b = Dinv_b F_{b-j,b}^T, j = 1 .. c, from the factor as it enters the pass, and the
+// G^(j)_b = Dinv_b F_{b-j,b}^T, j = 1 .. d, from the factor as it enters the pass, and the
 // check that its diagonal is positive and finite (Algorithm 1's Compute
 // needs L_ii > 0).  Rows and columns past n are the identity.
 template <typename T>
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(32) prep_kernel(Args<T> A)
             dg[i * kB + lane] = x[i];
         }
         __syncwarp();
-        for (int j = 1; j <= A.c && j <= b; ++j) {
+        for (int j = 1; j <= A.d && j <= b; ++j) {
             // the tile j blocks above the diagonal block: rows of block b - j (all < n), columns of block b
             const long long rj = c0 - (long long)j * kB;
 #pragma unroll 4
@@ -794,16 +799,17 @@ struct ChainSmem {
 // The chain block: every role is one warp, linked by mbarrier rings (full /
 // empty per resource slot; an item m uses slot m % R with phase parity
 // (m / R) & 1, and no producer can lap a consumer by construction).  With
-// G^(j)_m = Dinv_m F_{m-j,m}^T for the c nearest offsets,
+// G^(j)_m = Dinv_m F_{m-j,m}^T for the d nearest offsets,
 //   P_m = W_m - sum_{j=1}^{c} G^(j)_m P_{m-j},
-//   W_m = Dinv_m (Zf_m - sum_{j=c+1}^{d} F_{m-j,m}^T P_{m-j}),
+//   W_m = Dinv_m Zf_m - sum_{j=c+1}^{d} G^(j)_m P_{m-j},
 // so the critical warp's step waits on no other warp's work of the last c
 // steps: the near warps (offsets c + 1 .. d) and the W warp have c steps of
-// slack.  The loader stages G^(1..c) (its copies arrive on the stage's
+// slack, and the W warp, whose far part Dinv_m Zf_m the workers post, only
+// subtracts.  The loader stages G^(1..c) (its copies arrive on the stage's
 // barrier when they land) and prefetches Dinv to L2, from where the W warp
-// loads its row of it, each near warp stages its own tiles, the
-// far-sum warp polls the workers' tagged sums ahead of use, the publisher
-// writes each P as tagged words.
+// loads its row of it for the first d + 1 blocks, each near warp stages its
+// own G^(j), the far-sum warp polls the workers' tagged sums ahead of use,
+// the publisher writes each P as tagged words.
 template <typename T, int KB>
 __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 {
@@ -979,25 +985,29 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
     } else if (warp >= kWNear0 && warp < kWNear0 + kNearWarps) {
         const int t = warp - kWNear0;
         if (t >= nnw) return;
-        // this warp's offsets' tiles, staged RS - 1 steps ahead (the factor as
-        // it entered the pass: nothing to wait for)
+        // this warp's offsets' matrices G^(j)_b = Dinv_b F_{m,b}^T (b = m + j,
+        // formed by prep_kernel from the factor as it entered the pass), staged
+        // RS - 1 steps ahead: the running sums are then Dinv_b times the near
+        // part, and W_b needs no product with Dinv_b on this block
         auto stage = [&](int m) {
             if (m < nb) {
                 for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
                     const int b = m + j;
                     if (b >= nb) break;
-                    stage_tile(sy, S.near[j - cc - 1][m % C::RS], A.L, ld, (long long)m * kB, (long long)b * kB, n, kB,
-                               vec, lane);
+                    stage_dense(S.near[j - cc - 1][m % C::RS], A.G + ((size_t)(j - 1) * nb + b) * kB * kB, lane);
                 }
             }
             cp_commit();
         };
-        // and, further ahead, the same tiles into L2 (one line per column segment)
+        // and, further ahead, the same matrices into L2
         auto prefetch = [&](int m) {
             if (m >= nb) return;
+            constexpr int LINE = 128 / (int)sizeof(T);  // elements per 128-byte line
             for (int j = cc + 1 + t; j <= d; j += kNearWarps) {
-                const long long col = (long long)(m + j) * kB + lane;
-                if (col < n && CHK_TRI(sy, (long long)m * kB + col * ld, n, ld)) prefetch_l2(A.L + (long long)m * kB + col * ld);
+                const int b = m + j;
+                if (b >= nb) break;
+                const T *g = A.G + ((size_t)(j - 1) * nb + b) * kB * kB;
+                for (int e = lane * LINE; e < kB * kB; e += 32 * LINE) prefetch_l2(g + e);
             }
         };
         constexpr int PF = 16;
@@ -1034,10 +1044,11 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         }
     } else if (warp == kWZhat) {
         T *wv = S.w;
-        // row `lane` of Dinv_b in registers, loaded from L2 (the loader
-        // prefetched it 16 steps ahead) as soon as W_{b-1} is out, so that
-        // the load completes while the warp waits for step b's sums; the
-        // warp waits on no stage of the loader's
+        // W_b = Dinv_b Zf_b - sum_{j=c+1}^{d} G^(j)_b P_{b-j}: the workers post
+        // Dinv_b Zf_b and the near warps' running sum holds the G terms, so
+        // the warp only subtracts.  The first d + 1 blocks have no far part:
+        // W_b = Dinv_b V_b - (near terms), with row `lane` of Dinv_b loaded
+        // from L2 (the loader prefetched it) before the warp waits
         T drow[kB];
         auto load_drow = [&](int b) {
             using V = typename Vec16<T>::type;
@@ -1053,7 +1064,6 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
         load_drow(0);
         for (int b = 0; b < nb; ++b) {
             const long long r0 = (long long)b * kB;
-            // w = Zf_b - sum_{j=c+1}^{d} F_{b-j,b}^T P_{b-j}
             T w[KB];
             if (b > d) {
                 MW(S.f_full, b - d - 1, C::RF, b);
@@ -1063,9 +1073,14 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
                 mb_arrive(&S.f_empty[(b - d - 1) % C::RF]);
             } else {
 #pragma unroll
-                for (int q = 0; q < KB; ++q)
-                    w[q] = vin(A, sy, r0 + lane, q);
+                for (int q = 0; q < KB; ++q) w[q] = vin(A, sy, r0 + lane, q);
+                row_store<T, KB>(wv, lane, w);
+                __syncwarp();
+                lane_mv_reg<T, KB>(drow, wv, w);
+                __syncwarp();
+                if (b + 1 <= d && b + 1 < nb) load_drow(b + 1);
             }
+            if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 6] = global_ns();
             if (cc + 1 <= d && cc + 1 <= b) {
                 // the near terms, summed by the near warps (offset c + 1 holds all of them)
                 MW(S.t_full[0], b - cc - 1, C::RT, b);
@@ -1075,17 +1090,11 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
                 for (int q = 0; q < KB; ++q) w[q] -= tn[q];
             }
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 11] = global_ns();
-            row_store<T, KB>(wv, lane, w);
-            __syncwarp();
-            if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 6] = global_ns();
-            T out[KB];
-            lane_mv_reg<T, KB>(drow, wv, out);
             // W_{b - RZ}'s slot is free once the critical warp has used it
             if (b >= C::RZ) MW(S.w_empty, b - C::RZ, C::RZ, b);
-            row_store<T, KB>(S.Z[b % C::RZ], lane, out);
+            row_store<T, KB>(S.Z[b % C::RZ], lane, w);
             __syncwarp();
             mb_arrive(&S.w_full[b % C::RZ]);
-            if (b + 1 < nb) load_drow(b + 1);
             if (A.trace && lane == 0) A.trace[(size_t)b * 16 + 1] = global_ns();
         }
     } else if (warp == kWZf) {
@@ -1132,7 +1141,7 @@ __device__ void trsm_chain(const Args<T> &A, unsigned char *smem)
 // Worker warps: the far part of column block b's sum,
 //   Zf_b = V_b - sum_{r < b - d} F_{r,b}^T P_r,
 // tiles staged a few ahead (they are the factor as it entered the pass), each
-// P_r polled as tagged words, Zf_b published as tagged words.
+// P_r polled as tagged words, Dinv_b Zf_b published as tagged words.
 template <typename T, int KB>
 struct WorkerCfg {
     // staged tiles per warp: five in float, where a worker that falls a few
@@ -1236,7 +1245,15 @@ __device__ bool trsm_workers(const Args<T> &A, unsigned char *smem)
             for (int q = 0; q < KB; ++q) z[q] -= t[q];
             __syncwarp();
         }
+        // post Dinv_b Zf_b (the chain block's W warp then only subtracts):
+        // Dinv_b staged into a free tile slot, Zf_b into the P row buffer
+        stage_dense(base, A.Dinv + (size_t)b * kB * kB, lane);
+        cp_commit();
+        row_store<T, KB>(Pr, lane, z);
         cp_wait<0>();
+        __syncwarp();
+        lane_mv<T, KB>(base, Pr, z, lane);
+        __syncwarp();
         long long *zt = A.Ztag + ((size_t)b * kB + lane) * KB * TW;
 #pragma unroll
         for (int q = 0; q < KB; ++q) put_tag(zt + q * TW, z[q], ep64);
