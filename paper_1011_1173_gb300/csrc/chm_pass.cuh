@@ -1802,17 +1802,17 @@ __device__ bool sweep_segment(const Args<T> &A, const SyncArgs &sy, int b, int s
 // B along (P's columns kr .. kb - 1 hold Y), this task runs the sweep's
 // two-FMA recurrence down Y, row block by row block behind the chain, and
 // writes L~^{-T} B over Y in P (read by the solve that follows the pass).
-// One warp; lane = right-hand side.  `sm`: Aug<T, KB>::bytes of shared
-// memory.  In a fused pass a row block waits for its coefficients (and
-// P_r as tagged words); after the pass's Compute kernels it waits for
-// nothing.  Returns false if the launch is being aborted.
+// One warp of a fused pass (the host carries right-hand sides only in
+// fused passes); lane = right-hand side.  `sm`: Aug<T, KB>::bytes of shared
+// memory.  Each row block waits for its coefficients and takes P_r as
+// tagged words.  Returns false if the launch is being aborted.
 template <typename T, int KB>
 struct Aug {
     static constexpr int YS = KB + 1;  // row stride of the staged Y rows
     static constexpr size_t bytes = sizeof(T) * (size_t)kB * (YS + 2 * KB + 1);
 };
 template <typename T, int KB>
-__device__ bool aug_task(const Args<T> &A, const SyncArgs &sy, T *sm, bool fused)
+__device__ bool aug_task(const Args<T> &A, const SyncArgs &sy, T *sm)
 {
     constexpr int YS = Aug<T, KB>::YS;
     constexpr int TW = Tag<T>::words;
@@ -1830,13 +1830,8 @@ __device__ bool aug_task(const Args<T> &A, const SyncArgs &sy, T *sm, bool fused
         const long long r0 = (long long)r * kB;
         const int rows = (int)min((long long)kB, n - r0);
         T pv[KB];
-        if (fused) {
-            if (!warp_flag(sy, A.cflag + r, A.epoch, r)) return false;  // row block r's coefficients
-            if (!warp_tagged_row<T, KB>(sy, A.Ptag + (size_t)(r0 + lane) * KB * TW, ep64, pv, 256u, r)) return false;
-        } else {
-#pragma unroll
-            for (int q = 0; q < KB; ++q) pv[q] = __ldcg(A.P + (size_t)(r0 + lane) * KB + q);
-        }
+        if (!warp_flag(sy, A.cflag + r, A.epoch, r)) return false;  // row block r's coefficients
+        if (!warp_tagged_row<T, KB>(sy, A.Ptag + (size_t)(r0 + lane) * KB * TW, ep64, pv, 256u, r)) return false;
 #pragma unroll
         for (int q = 0; q < KB; ++q) Ys[lane * YS + q] = pv[q];
         if (lane < rows) {
@@ -1887,8 +1882,6 @@ __global__ void __launch_bounds__(SweepCfg<T, KB>::WARPS * 32) sweep_kernel(Args
     SweepSlot<T, KB> *slot = reinterpret_cast<SweepSlot<T, KB> *>(smem) + (size_t)warp * C::NSLOT;
     const SyncArgs sy = sync_of(A);
     if (!ws_ok<T, KB>(A, sy)) return;
-    static_assert(Aug<T, KB>::bytes <= C::NSLOT * sizeof(SweepSlot<T, KB>), "a sweep warp's slots hold the task");
-    if (take_aug<T, KB>(A) && !aug_task<T, KB>(A, sy, reinterpret_cast<T *>(slot), false)) return;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = atomicAdd(A.ctl + kCtlSweepTicket, 1);
@@ -1920,7 +1913,7 @@ __device__ void post_tasks(const Args<T> &A, const SyncArgs &sy, unsigned char *
 {
     const int lane = threadIdx.x & 31;
     static_assert(Aug<T, KB>::bytes <= WorkerCfg<T, KB>::warp_bytes, "a worker warp's shared memory holds the task");
-    if (take_aug<T, KB>(A) && !aug_task<T, KB>(A, sy, reinterpret_cast<T *>(wsmem), true)) return;
+    if (take_aug<T, KB>(A) && !aug_task<T, KB>(A, sy, reinterpret_cast<T *>(wsmem))) return;
     for (;;) {
         int tk = 0;
         if (lane == 0) tk = aborted(sy) ? (1 << 30) : atomicAdd(A.ctl + kCtlPostTicket, 1);
