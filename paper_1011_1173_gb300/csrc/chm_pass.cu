@@ -187,7 +187,9 @@ PassLayout pass_layout(long long n, int elt, int seg)
     l.ctl = x; x = al(x + pass::kCtlInts * 4);
     l.P = x; x = al(x + rows * KB * elt);
     l.Dinv = x; x = al(x + nb * 1024 * elt);
-    l.G = x; x = al(x + (size_t)pass::kMaxG * nb * 1024 * elt);
+    // G^(j) for every lookahead offset: at most 10 in float, 6 in double (clamp_d)
+    const size_t ng = elt == 8 ? 6 : pass::kMaxG;
+    l.G = x; x = al(x + ng * nb * 1024 * elt);
     l.gram = x; x = al(x + nb * KB * KB * 8);
     l.H = x; x = al(x + nb * KB * KB * 8);
     l.coef = x; x = al(x + rows * 2 * KB * elt);
