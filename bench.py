@@ -365,10 +365,16 @@ def time_host_large(L0, U, U9, stream, reps=2):
             ts.append(a.elapsed_time(b))
     chm.check(chm.status_sync(stream)[0], "host-resident status")
     n, k = L0.shape[0], U.shape[0]
+    # the device memory the host factor's modification held: the pass kernels' workspace
+    chm.config_set("path", chm.PATH_PASS)
+    try:
+        ws = chm.workspace_bytes(n, k, chm.dtype_code(L0))
+    finally:
+        chm.config_set("path", chm.PATH_AUTO)
     out = {"ms_per_modification": statistics.median(ts),
            # a factor in page-locked host memory takes the pass kernels from two vectors on
            "path": "pass" if k >= 2 or chm.path_for(n, k, chm.dtype_code(L0)) == chm.PATH_PASS else "wave",
-           "device_workspace_bytes": chm.workspace_bytes(n, k, chm.dtype_code(L0))}
+           "device_workspace_bytes": ws}
     del Lh
     return out
 
