@@ -1,6 +1,6 @@
-"""The pass kernels' restatement of Algorithm 1 (no GPU): the exact
-identities the large-factor path computes, written out in numpy in float64
-and checked against the CPU oracle's CholeskyModifyB.
+"""The kernels' restatements of Algorithm 1 (no GPU): the exact identities
+the pass kernels and the wave kernel compute, written out in numpy in
+float64 and checked against the CPU oracle's CholeskyModifyB.
 
 For a block of kb vectors V (signs sigma) applied to the factor F:
   P = F^{-T} V;  for row r the prefix Gram H_r = Sigma + sum_{i<r} p_i p_i^T,
@@ -157,3 +157,40 @@ def test_restatement_rejects_a_dropped_prefix():
     ref = cm_from_upper(F)
     assert oracle.modify_b(ref, np.ascontiguousarray(V.T), sigma)[0] == oracle.OK
     assert colscaled_err(cm_from_upper(_sweep(F, V, a2, b2, e2, dc2)), ref) > 1e-6
+
+
+def test_wave_restatement_with_row_scales_equals_modify_b():
+    """The wave kernel's restatement (no GPU): per vector (wave) v with sign
+    sigma, p = F^{-T} v for the current factor, T_0 = 1,
+    T_{i+1} = T_i + sigma p_i^2, and, with the off-diagonal of row i held
+    as S_i. = L_i. / e_i, each entry S <- S + a_i u, u <- u - b_i S with
+    a_i = sigma p_i / e_i, b_i = p_i e_i / T_{i+1} (u the column's carry
+    divided by sqrt(T_i), starting at v_j), the diagonal multiplied by
+    c_i = sqrt(T_{i+1} / T_i) and the row scale divided by it; the true
+    values e_i S_ij once after the last wave.  Checked against
+    CholeskyModifyB for several waves with mixed signs."""
+    n, k = 45, 4
+    F, V, sigma = _problem(n, k, 3131)
+    S = np.triu(F, 1).copy()   # e = 1 to start
+    diag = np.diag(F).copy()
+    e = np.ones(n)
+    for q in range(k):
+        sg = float(sigma[q])
+        Fcur = np.diag(diag) + e[:, None] * S
+        p = np.linalg.solve(Fcur.T, V[:, q])
+        T = np.concatenate(([1.0], 1.0 + np.cumsum(sg * p * p)))
+        u = V[:, q].copy()
+        for i in range(n):
+            a = sg * p[i] / e[i]
+            b = p[i] * e[i] / T[i + 1]
+            for j in range(i + 1, n):
+                S[i, j] = S[i, j] + a * u[j]
+                u[j] = u[j] - b * S[i, j]
+            c = np.sqrt(T[i + 1] / T[i])
+            diag[i] *= c
+            e[i] /= c
+    got = np.diag(diag) + e[:, None] * S
+    ref = cm_from_upper(F)
+    assert oracle.modify_b(ref, np.ascontiguousarray(V.T), sigma)[0] == oracle.OK
+    err = colscaled_err(cm_from_upper(got), ref)
+    assert err <= 1e-12, err
