@@ -61,3 +61,25 @@ def test_cpu_baseline_runs_whole_steps(dtype):
     elt = 4 if dtype == "f32" else 8
     assert cb["value"] == pytest.approx(2 * bench.alg_bytes(96, 3, elt) / per_step / 1e9)
     assert ("float32 storage" in cb["sample"]) == (dtype == "f32")
+
+
+def test_launches_per_modification_follow_the_settings():
+    """The launch count the JSON line claims: the wave kernel once per 64
+    vectors; a fused pass two launches per block of vectors (8 in float, 4 in
+    float64 by default), a six-kernel pass six."""
+    from paper_1011_1173_gb300 import chm
+    assert bench.launches_per_modification(chm.PATH_WAVE, 16) == 1
+    assert bench.launches_per_modification(chm.PATH_WAVE, 65) == 2
+    assert bench.launches_per_modification(chm.PATH_PASS, 1, "f32") == 2
+    assert bench.launches_per_modification(chm.PATH_PASS, 16, "f32") == 4
+    assert bench.launches_per_modification(chm.PATH_PASS, 16, "f64") == 8
+    chm.config_set("pass_fused", 0)
+    try:
+        assert bench.launches_per_modification(chm.PATH_PASS, 16, "f32") == 12
+    finally:
+        chm.config_set("pass_fused", 1)
+    chm.config_set("pass_kb", 16)
+    try:
+        assert bench.launches_per_modification(chm.PATH_PASS, 16, "f32") == 6
+    finally:
+        chm.config_set("pass_kb", 0)
